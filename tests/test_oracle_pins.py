@@ -1,0 +1,345 @@
+"""Pins of the oracle against facts fixed by the paper and by mathematics (CPU only).
+
+Each test checks the oracle against something other than itself: closed forms, library
+routines for special cases, invariants (symmetry, sum rules, translation / rotation invariance),
+brute force, or finite differences. Paper passages are named by equation.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+import scipy.linalg
+from scipy.spatial import cKDTree
+
+import workloads as wl
+from oracle import cohp, exact, hamiltonian, krylov, physics, pipeline
+from oracle import slater_koster as skm
+from oracle import structure
+
+SK = wl.sk_params()
+
+
+def _rot(seed):
+    q = np.random.default_rng(seed).normal(size=(3, 3))
+    Q, R = np.linalg.qr(q)
+    return Q * np.sign(np.diag(R))
+
+
+# ----------------------------------------------------------------------------- Slater-Koster
+def _block_transpose_error(sk):
+    d = np.random.default_rng(0).normal(size=(20, 3))
+    d *= (1.3 + np.random.default_rng(1).uniform(size=(20, 1))) / np.linalg.norm(d, axis=1)[:, None]
+    Hp, Sp = skm.blocks(d, sk)
+    Hm, Sm = skm.blocks(-d, sk)
+    return max(np.abs(Hm - Hp.transpose(0, 2, 1)).max(), np.abs(Sm - Sp.transpose(0, 2, 1)).max())
+
+
+def test_sk_pair_symmetry():
+    """B(R_I - R_J) = B(R_J - R_I)^T, which makes H and S symmetric (Eq. 1: H, S symmetric)."""
+    assert _block_transpose_error(SK) < 1e-14
+
+
+def test_sk_rotation_covariance():
+    """p orbitals transform as a vector: B(R d) = T B(d) T^T with T = diag(1, R)."""
+    d = np.random.default_rng(2).normal(size=(16, 3))
+    d *= 1.6 / np.linalg.norm(d, axis=1)[:, None]
+    R = _rot(3)
+    T = scipy.linalg.block_diag(1.0, R)
+    H1, S1 = skm.blocks(d @ R.T, SK)
+    H0, S0 = skm.blocks(d, SK)
+    assert np.abs(H1 - T @ H0 @ T.T).max() < 1e-13
+    assert np.abs(S1 - T @ S0 @ T.T).max() < 1e-13
+
+
+def test_sk_bond_along_z_at_r0():
+    """Bond along z at r0: the block is the integrals themselves (sigma on z, pi on x, y)."""
+    H, S = skm.blocks(np.array([[0.0, 0.0, SK.r0]]), SK)
+    for B, V in ((H[0], SK.V0), (S[0], SK.S0)):
+        assert B[0, 0] == pytest.approx(V[0], abs=1e-15)
+        assert B[0, 3] == pytest.approx(V[1], abs=1e-15)
+        assert B[3, 0] == pytest.approx(-V[1], abs=1e-15)
+        assert B[3, 3] == pytest.approx(V[2], abs=1e-15)
+        assert B[1, 1] == pytest.approx(V[3], abs=1e-15) and B[2, 2] == pytest.approx(V[3], abs=1e-15)
+        assert abs(B[0, 1]) < 1e-15 and abs(B[1, 2]) < 1e-15 and abs(B[1, 3]) < 1e-15
+
+
+def test_taper_smoothness():
+    """t = 1 below r_on, 0 above r_cut, C2 at both ends, monotone in between."""
+    assert skm.taper(SK.r_on, SK) == 1.0 and skm.taper(SK.r_cut, SK) == 0.0
+    h = 1e-4
+    for r, s in ((SK.r_on, 1.0), (SK.r_cut, -1.0)):
+        d1, d2 = skm.dtaper(r + s * h, SK), skm.dtaper(r + 2 * s * h, SK)
+        assert abs(d1) < 1e-4 and abs(d2 / d1 - 4.0) < 1e-2     # dt/dr ~ (r - r_end)^2
+    r = np.linspace(SK.r_on, SK.r_cut, 101)
+    assert np.all(np.diff(skm.taper(r, SK)) <= 0)
+    rr = np.linspace(SK.r_on + 0.01, SK.r_cut - 0.01, 17)
+    fd = (skm.taper(rr + 1e-6, SK) - skm.taper(rr - 1e-6, SK)) / 2e-6
+    assert np.abs(fd - skm.dtaper(rr, SK)).max() < 1e-6
+
+
+def test_sk_gradients_match_finite_differences():
+    d = np.random.default_rng(5).normal(size=(12, 3))
+    d *= np.linspace(1.2, 2.55, 12)[:, None] / np.linalg.norm(d, axis=1)[:, None]
+    gH, gS = skm.block_grads(d, SK)
+    h = 1e-6
+    for m in range(3):
+        e = np.zeros(3)
+        e[m] = h
+        Hp, Sp = skm.blocks(d + e, SK)
+        Hm, Sm = skm.blocks(d - e, SK)
+        assert np.abs((Hp - Hm) / (2 * h) - gH[:, m]).max() < 1e-7
+        assert np.abs((Sp - Sm) / (2 * h) - gS[:, m]).max() < 1e-7
+
+
+# ----------------------------------------------------------------------------- structure
+def test_neighbor_lists_match_kdtree():
+    w = wl.make("diamond_4096")
+    rp, ci = structure.neighbor_csr(w.pos, w.box, SK.r_cut)
+    tree = cKDTree(w.pos, boxsize=w.box)
+    ref = tree.query_ball_point(w.pos, SK.r_cut)
+    assert rp[-1] == sum(len(r) for r in ref)
+    for i in range(0, w.n_atoms, 97):
+        assert list(ci[rp[i]:rp[i + 1]]) == sorted(ref[i])
+    # perfect diamond: 1 + 4 + 12 atoms within 2.6 A, 159 within 6 A (library count)
+    pos, box = wl.diamond((8, 8, 8))
+    assert len(structure.within(pos, box, 0, SK.r_cut)) == 17
+    n6 = len(cKDTree(pos, boxsize=box).query_ball_point(pos[0], 6.0))
+    assert len(structure.cluster(pos, box, 0, 6.0)) == n6 == 159
+
+
+def test_dense_h_s_symmetric_and_s_positive_definite(diamond64):
+    H, S = hamiltonian.dense(diamond64.pos, diamond64.box, diamond64.sk)
+    assert np.abs(H - H.T).max() == 0.0 and np.abs(S - S.T).max() == 0.0
+    assert np.linalg.eigvalsh(S).min() > 0.3       # S positive definite (Eq. 1 text)
+
+
+def test_s_positive_definite_larger_systems():
+    """Lanczos lambda_min(S) for the 4096-atom system (library eigsh on the sparse S)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as sla
+    w = wl.make("diamond_4096")
+    rp, ci = structure.neighbor_csr(w.pos, w.box, SK.r_cut)
+    _, Sb = hamiltonian.bsr_values(w.pos, w.box, w.sk, rp, ci)
+    S = sp.bsr_matrix((Sb, ci, rp), shape=(4 * w.n_atoms,) * 2)
+    lam = sla.eigsh(S, k=1, which="SA", return_eigenvectors=False, tol=1e-6)[0]
+    assert lam > 0.1
+
+
+# ----------------------------------------------------------------------------- exact path
+def test_exact_matches_library_generalized_eigh(diamond64):
+    H, S = hamiltonian.dense(diamond64.pos, diamond64.box, diamond64.sk)
+    e, Y = exact.generalized_eig(H, S)
+    e_ref = scipy.linalg.eigh(H, S, eigvals_only=True)
+    assert np.abs(e - e_ref).max() < 1e-11
+    assert np.abs(Y.T @ S @ Y - np.eye(len(e))).max() < 1e-12
+    assert abs(e.sum() - np.trace(np.linalg.solve(S, H))) < 1e-9
+
+
+def test_exact_density_matrix_idempotent_at_low_temperature(diamond64):
+    """rho S rho = 2 rho when every level is full or empty (spin factor 2, Eq. 2)."""
+    H, S = hamiltonian.dense(diamond64.pos, diamond64.box, diamond64.sk)
+    e, Y = exact.generalized_eig(H, S)
+    kT = 0.01
+    mu = exact.chemical_potential(e, diamond64.n_electrons, kT)
+    rho, _ = exact.density_matrices(e, Y, mu, kT)
+    assert np.abs(rho @ S @ rho - 2.0 * rho).max() < 1e-10
+    assert abs(np.trace(rho @ S) - diamond64.n_electrons) < 1e-9
+
+
+def test_dimer_pi_levels_closed_form():
+    """Two atoms at r0 along z: pi levels (Ep +- Vpp_pi)/(1 +- Spp_pi), each twice."""
+    pos, box = wl.dimer(SK.r0)
+    H, S = hamiltonian.dense(pos, box, SK)
+    e, _ = exact.generalized_eig(H, S)
+    for val in ((SK.Ep + SK.V0[3]) / (1 + SK.S0[3]), (SK.Ep - SK.V0[3]) / (1 - SK.S0[3])):
+        assert np.sum(np.abs(e - val) < 1e-12) == 2
+    # the Krylov space of a px column is the invariant {px1, px2} pair: breakdown at nu_eff = 2
+    col = pipeline.solve_column(pos, box, SK, 0.0, 8, j=1)
+    assert col.nu_eff == 2
+    ref = sorted([(SK.Ep + SK.V0[3]) / (1 + SK.S0[3]), (SK.Ep - SK.V0[3]) / (1 - SK.S0[3])])
+    assert np.abs(np.sort(col.eps) - ref).max() < 1e-12
+
+
+# ----------------------------------------------------------------------------- Krylov path
+def _fragment():
+    """An isolated 20-atom piece of displaced diamond in a 30 A box (cluster = whole)."""
+    pos, _ = wl.diamond((2, 2, 2), sigma=0.05)
+    c = pos.mean(axis=0)
+    keep = np.argsort(np.linalg.norm(pos - c, axis=1))[:20]
+    p = pos[np.sort(keep)] - c + 15.0
+    return wl.Workload("fragment_20", p, np.full(3, 30.0), SK, r_cluster=0.0, nu=80)
+
+
+@pytest.fixture(scope="module")
+def full_subspace():
+    w = _fragment()
+    return w, pipeline.run(w), pipeline.dense_reference(w)
+
+
+def test_full_subspace_equals_exact_diagonalisation(full_subspace):
+    """P1: with the cluster = whole system and nu = M, U is square and rho is exact."""
+    w, res, ref = full_subspace
+    rp, ci = res["row_ptr"], res["col_idx"]
+    # evaluate the Krylov columns at the exact mu (mu is not unique inside the gap)
+    _, _, rho, rhoE = pipeline.assemble(w, res["columns"], ref["mu"])
+    mask = hamiltonian.bsr_to_dense(rp, ci, np.ones_like(rho)) > 0
+    assert np.abs(hamiltonian.bsr_to_dense(rp, ci, rho) - ref["rho"])[mask].max() < 1e-8
+    assert np.abs(hamiltonian.bsr_to_dense(rp, ci, rhoE) - ref["rhoE"])[mask].max() < 1e-8
+    sc = pipeline.scalars(res["columns"], ref["mu"], w.kT, w.n_electrons)
+    assert abs(sc["E_band"] - ref["E_band"]) / w.n_atoms < 1e-9
+    assert abs(sc["Omega"] - ref["Omega"]) / w.n_atoms < 1e-9
+
+
+def test_full_subspace_green_function_equals_dense_solve(full_subspace):
+    """P2: G_ij(z) = sum_k Z_ik c_k / (z - e_k) equals (zS - H)^-1 e_j (Eq. 1, b = e_j)."""
+    w, res, ref = full_subspace
+    for j in (0, 5, 41, 79):
+        col = res["columns"][j]
+        Hc, Sc = ref["H"], ref["S"]
+        kc = krylov.arnoldi_column(Hc, Sc, j, w.nu)
+        eps, V = krylov.projected_eig(kc.Hp, kc.Sp)
+        c = V.T @ kc.U[j, :]
+        Z = kc.U @ V
+        for z in (0.3 + 0.5j, -7.0 + 0.05j, 2.0 + 2.0j):
+            g = Z @ (c / (z - eps))
+            g_ref = exact.green_column(Hc, Sc, z, j)
+            assert np.abs(g - g_ref).max() <= 1e-10 * np.abs(g_ref).max()
+        assert np.abs(np.sort(col.eps) - ref["eps"]).max() < 1e-9
+
+
+def test_full_subspace_rho_symmetric(full_subspace):
+    """P4: rho = rho^T at full subspace."""
+    w, res, ref = full_subspace
+    tmap = structure.transpose_map(res["row_ptr"], res["col_idx"])
+    rho = res["rho"]
+    assert np.abs(rho - rho[tmap].transpose(0, 2, 1)).max() < 1e-10
+
+
+def test_electron_count_two_paths(diamond64):
+    """P3: N(mu) from the spectra equals Tr(rho S) from the assembled rho; both equal N_e."""
+    res = pipeline.run(diamond64)
+    _, Sb = hamiltonian.bsr_values(diamond64.pos, diamond64.box, diamond64.sk,
+                                   res["row_ptr"], res["col_idx"])
+    trace = float(np.einsum("eab,eab->", res["rho"], Sb))
+    assert abs(trace - res["N"]) < 1e-9
+    assert abs(res["N"] - diamond64.n_electrons) < 1e-6
+
+
+def test_icohp_sum_rule(diamond64):
+    """P9 (Eq. 6): sum_IJ B_IJ = E_band, for the truncated Krylov rho as well."""
+    res = pipeline.run(diamond64)
+    B, Bs, Bp = cohp.icohp(diamond64.pos, diamond64.box, diamond64.sk,
+                           res["row_ptr"], res["col_idx"], res["rho"])
+    assert abs(B.sum() - res["E_band"]) < 1e-8
+    rows = np.repeat(np.arange(diamond64.n_atoms), np.diff(res["row_ptr"]))
+    off = rows != res["col_idx"]
+    assert np.abs((Bs + Bp - B)[off]).max() < 1e-12
+
+
+def test_lanczos_special_case_s_identity(diamond64):
+    """P5: S = I makes the method Lanczos: H' tridiagonal and Gauss quadrature exact to 2nu-1."""
+    sk = dataclasses.replace(SK, S0=(0.0, 0.0, 0.0, 0.0))
+    H, _ = hamiltonian.dense(diamond64.pos, diamond64.box, sk)
+    nu = 6
+    for j in (0, 7, 201):
+        col = pipeline.solve_column(diamond64.pos, diamond64.box, sk, 0.0, nu, j)
+        assert np.abs(np.triu(col.Hp, 2)).max() < 1e-12
+        ej = np.zeros(H.shape[0])
+        ej[j] = 1.0
+        v = ej.copy()
+        for m in range(2 * nu):
+            mom = ej @ v
+            quad = np.sum(col.c ** 2 * col.eps ** m)
+            assert abs(quad - mom) <= 1e-10 * max(1.0, np.sum(np.abs(col.c ** 2 * col.eps ** m)))
+            v = H @ v
+
+
+# ----------------------------------------------------------------------------- mu, f, forces
+def test_fermi_and_omega():
+    x = np.array([-800.0, -3.0, 0.0, 2.5, 900.0])
+    f = physics.fermi(x, 0.0, 1.0)
+    assert np.all(np.isfinite(f)) and f[2] == 0.5 and f[0] == 1.0 and f[-1] == 0.0
+    assert np.abs(f + physics.fermi(-x, 0.0, 1.0) - 1.0).max() < 1e-15
+    e = np.linspace(-2, 2, 41)
+    h = 1e-6
+    dw = (physics.omega(e + h, 0.3, 0.1) - physics.omega(e - h, 0.3, 0.1)) / (2 * h)
+    assert np.abs(dw - 2.0 * physics.fermi(e, 0.3, 0.1)).max() < 1e-7
+    assert np.all(np.isfinite(physics.omega(np.array([-1e4, 1e4]), 0.0, 0.1)))
+
+
+def test_bisection_symmetric_levels():
+    # symmetric levels, half filling: mu = 0 by f(-x) = 1 - f(x); the bisection interval is
+    # 1e-13 and N'(0) ~ 1 at kT = 1, so rounding of N moves mu by ~1e-16 only
+    mu, it = physics.bisect_mu(np.array([-1.0, 1.0]), np.array([1.0, 1.0]), 2.0, 1.0)
+    assert abs(mu) < 1e-13 and it <= 100
+    with pytest.raises(physics.NoBracket):
+        physics.bisect_mu(np.array([-1.0, 1.0]), np.array([1.0, 1.0]), 5.0, 0.1)
+
+
+def test_forces_sum_to_zero_and_match_finite_differences(diamond64):
+    """P7: sum_I F_I = 0; F = -dOmega/dR at fixed mu by central differences (h = 1e-4 A)."""
+    w = diamond64
+    ref = pipeline.dense_reference(w)
+    rp, ci = structure.neighbor_csr(w.pos, w.box, w.sk.r_cut)
+    n = w.n_atoms
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    idx = np.stack([4 * rows[:, None] + np.arange(4)[None, :]] * 4, axis=2)
+    jdx = np.stack([4 * ci[:, None] + np.arange(4)[None, :]] * 4, axis=1)
+    rho = ref["rho"][idx, jdx]
+    rhoE = ref["rhoE"][idx, jdx]
+    F = physics.forces(w.pos, w.box, w.sk, rp, ci, rho, rhoE)
+    assert np.abs(F.sum(axis=0)).max() < 1e-10
+    h = 1e-4
+    for (K, m) in ((0, 0), (17, 1), (40, 2), (63, 0)):
+        om = []
+        for s in (1, -1):
+            pos = w.pos.copy()
+            pos[K, m] += s * h
+            H, S = hamiltonian.dense(pos, w.box, w.sk)
+            e, _ = exact.generalized_eig(H, S)
+            om.append(exact.grand_potential(e, ref["mu"], w.kT))
+        fd = -(om[0] - om[1]) / (2 * h)
+        assert abs(fd - F[K, m]) <= 1e-5 * max(1.0, np.abs(F).max())
+
+
+def test_band_energy_rotation_invariant():
+    """E of an isolated cluster does not depend on its orientation."""
+    pos, _ = wl.diamond((2, 2, 2), sigma=0.05)
+    pos = pos[:20]
+    box = np.full(3, 60.0)
+    c = pos.mean(axis=0)
+    es = []
+    for R in (np.eye(3), _rot(11)):
+        p = (pos - c) @ R.T + 30.0
+        H, S = hamiltonian.dense(p, box, SK)
+        e, _ = exact.generalized_eig(H, S)
+        es.append(np.sort(e))
+    assert np.abs(es[0] - es[1]).max() < 1e-11
+
+
+# ----------------------------------------------------------------------------- planted mistakes
+def test_planted_sign_error_is_caught(monkeypatch):
+    """A flipped p-s sign in the table breaks the pair-symmetry pin."""
+    orig = skm._table
+
+    def bad(u, V):
+        B = orig(u, V)
+        B[:, 1:, 0] *= -1.0
+        return B
+    monkeypatch.setattr(skm, "_table", bad)
+    assert _block_transpose_error(SK) > 1e-3
+
+
+def test_planted_missing_spin_factor_is_caught(diamond64, monkeypatch):
+    H, S = hamiltonian.dense(diamond64.pos, diamond64.box, diamond64.sk)
+    e, Y = exact.generalized_eig(H, S)
+    monkeypatch.setattr(physics, "fermi", lambda eps, mu, kT: 0.5 * (1 - np.tanh((eps - mu) / (2 * kT))) / 2)
+    mu = 0.0
+    rho, _ = exact.density_matrices(e, Y, mu, 0.01)
+    assert np.abs(rho @ S @ rho - 2.0 * rho).max() > 1e-2
+
+
+def test_planted_single_gram_schmidt_pass_changes_nothing_visible_but_orthogonality(diamond64):
+    """The S-orthonormality of the basis (what CGS2 maintains) is checked directly."""
+    col = pipeline.solve_column(diamond64.pos, diamond64.box, diamond64.sk, 0.0, 30, 9)
+    assert np.abs(col.Sp - np.eye(col.nu_eff)).max() < 1e-12
