@@ -1,0 +1,174 @@
+/*
+ * elses.h -- C ABI of the GB300 per-column Krylov Green's-function library.
+ *
+ * The library computes, for sparse real-symmetric LCAO matrices H and S (S positive definite),
+ * the Green's function G = (zS - H)^-1 column by column (Eq. 1 with b = e_j, the column index
+ * j being the parallel unit), the one-body density matrix of Eq. 2 from the Fermi-Dirac energy
+ * integral of Im G, the chemical potential by bisection (the workflow of Eq. 3), the band energy
+ * Tr(rho H) (= sum of ICOHP, Eq. 6) and the atomic forces, for a two-centre s/p tight-binding
+ * model of carbon.
+ *
+ * Conventions
+ *   Units      eV, Angstrom. All floating point is IEEE double (FP64).
+ *   Basis      N atoms, M = 4N orbitals; basis index j = 4*J + alpha, alpha = (s, px, py, pz).
+ *   Positions  double[N][3], row-major; orthorhombic periodic box; minimum-image convention
+ *              (the box must exceed 2*r_cut, and 2*r_cluster when r_cluster > 0).
+ *   Pattern    block-sparse rows (BSR) over atoms: row_ptr int32[N+1], col_idx int32[nnzb]
+ *              (ascending within a row, the diagonal block included); block e = (I, J) holds
+ *              val[e][a][b] = X_(I,a),(J,b) as double[nnzb][4][4]. The pattern is every pair with
+ *              |R_J - R_I| <= r_cut (inclusive), so it is symmetric.
+ *   Memory     Array arguments named *_dev are caller-owned DEVICE pointers (e.g. from PyTorch),
+ *              valid for the duration of the call; *_host are host pointers. Opaque handles and
+ *              the device memory behind them are owned by the library and released by
+ *              elses_system_destroy; the elses_get_* accessors copy out of that memory.
+ *   Streams    Every call takes a cudaStream_t (passed as void*; NULL = legacy default stream)
+ *              and enqueues its work on it. Calls that return host scalars synchronise that
+ *              stream before returning.
+ *   Status     0 = success; > 0 = warning (results valid); < 0 = error (outputs undefined).
+ *              elses_last_error() returns a message for the last failing call of this thread.
+ *   Threads    One system handle must not be used from two threads at once.
+ */
+#ifndef ELSES_H
+#define ELSES_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ELSES_OK                  0
+#define ELSES_WARN_BREAKDOWN      1   /* some column stopped early (invariant subspace) */
+#define ELSES_ERR_ARG            -1   /* bad argument (NULL, size, box too small, ...)   */
+#define ELSES_ERR_NOT_SPD        -2   /* a projected overlap S' failed its Cholesky      */
+#define ELSES_ERR_NONFINITE      -3   /* NaN or Inf in an input or a result              */
+#define ELSES_ERR_NO_BRACKET     -4   /* electron count not bracketed by the spectrum    */
+#define ELSES_ERR_TIMEOUT        -5   /* a bounded device-side iteration ran out         */
+#define ELSES_ERR_CUDA           -6   /* CUDA runtime error                              */
+#define ELSES_ERR_OOM            -7   /* device allocation failed                        */
+#define ELSES_ERR_NOT_IMPLEMENTED -8
+#define ELSES_ERR_STATE          -9   /* call out of order (e.g. density before columns) */
+#define ELSES_ERR_CAPACITY      -10   /* a neighbour or cluster list exceeded its bound  */
+
+/* Two-centre s/p Slater-Koster model (reading of the paper's TB-form Hamiltonian):
+ * integral x in (ss-sigma, sp-sigma, pp-sigma, pp-pi),
+ *   V_x(r) = V0[x] exp(-qH[x] (r - r0)) t(r),   S_x(r) = S0[x] exp(-qS[x] (r - r0)) t(r),
+ *   t = 1 (r <= r_on), 0 (r >= r_cut), 1 - 10s^3 + 15s^4 - 6s^5 between, s = (r-r_on)/(r_cut-r_on).
+ * On-site blocks: H = diag(Es, Ep, Ep, Ep), S = I. */
+typedef struct elses_sk {
+    double Es, Ep;
+    double V0[4], qH[4];
+    double S0[4], qS[4];
+    double r0, r_on, r_cut;
+} elses_sk;
+
+/* Method settings. nu is the Krylov dimension per column; when n_classes > 0 the dimension of
+ * a column is class_nu[c] for the first class c with cluster atoms <= class_max_atoms[c]. */
+typedef struct elses_params {
+    double r_cluster;       /* cluster radius around atom J; <= 0: the whole system          */
+    double kT;              /* Fermi-Dirac temperature (eV)                                   */
+    double n_electrons;     /* electron count for the chemical potential                      */
+    double breakdown_tol;   /* stop when beta <= tol * ||H u_n||_2 (default 1e-12)           */
+    double mu_tol;          /* bisection stops when the bracket is narrower (default 1e-13)  */
+    int    nu;              /* Krylov dimension (<= 64)                                       */
+    int    max_bisect;      /* bisection step limit (default 100)                             */
+    int    two_pass;        /* 1: memory-saving workflow of Eq. 3 (G computed twice)         */
+    int    n_classes;       /* 0..4 size classes for nu                                       */
+    int    class_max_atoms[4];
+    int    class_nu[4];
+    int    max_neighbors;   /* capacity of a neighbour row (0: default 64)                    */
+    int    max_cluster;     /* capacity of a cluster (0: default 512)                         */
+    int    schedule;        /* 0: plain (persistent CTAs, static atom order), 1: batched
+                               (persistent CTAs pulling atoms from a cluster-size-sorted queue) */
+    int    timing;          /* 1: time the kernels of each call with CUDA events (elses_stats) */
+} elses_params;
+
+/* Counters and event timings of the calls since the last build (timing = 1 for the times). */
+typedef struct elses_stats {
+    long long launches;     /* kernels launched                                              */
+    long long columns;      /* columns solved (a3-a6)                                        */
+    long long krylov_launches;
+    int bisect_steps;       /* steps of the last bisection                                   */
+    int pad;
+    double t_krylov_ms;     /* Krylov build + projection kernels (a3, a4)                    */
+    double t_eig_ms;        /* projected eigenproblem kernels (a5, a6)                       */
+    double t_bisect_ms;     /* bisection and scalar reductions (a7, a9)                      */
+    double t_density_ms;    /* density-matrix kernels (a8)                                   */
+    double t_force_ms;      /* force kernels (a10)                                           */
+} elses_stats;
+
+typedef struct elses_system_s* elses_system;
+
+/* a1 + a2: neighbour lists and clusters (periodic cell lists, brute force inside cells), then
+ * the Slater-Koster H and S on the pattern. If *sys is NULL a system is created; otherwise the
+ * existing system is rebuilt for new positions (same atom count), reusing its memory.
+ * pos_dev: double[N][3] device. box_host: double[3] host. sk, params: host structs (copied).
+ * Passage: Eq. 1 (sparse symmetric H, S) and the redundant local build of H and S
+ * (data-communication saving, item I of the computational issues). */
+int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
+                         const double* box_host, const elses_sk* sk,
+                         const elses_params* params, void* stream);
+
+/* Replace H and S by user values on the system's own pattern (double[nnzb][4][4] device).
+ * Forces need the Slater-Koster derivatives and are unavailable afterwards (ERR_STATE). */
+int elses_set_hs(elses_system sys, const double* H_dev, const double* S_dev, void* stream);
+
+/* a3-a6: per-column Krylov build, projection, projected generalized eigenproblem and spectra
+ * for columns [col_begin, col_end) (whole atoms: both multiples of 4). Keeps the spectra (and,
+ * unless two_pass, what rho needs). If n_z > 0, also writes G_ij(z) for the pattern rows i of
+ * each column j into G_dev[(e*16 + a*4 + b)*n_z + iz][2] (re, im) for block e = (I, J) holding
+ * G_(I,a),(J,b), z_host[iz] = (re, im). nu_eff_dev: optional int[M] device output.
+ * Passage: Eq. 1 and the generation of G column by column. */
+int elses_green_columns(elses_system sys, int col_begin, int col_end, int n_z,
+                        const double* z_host, double* G_dev, int* nu_eff_dev, void* stream);
+
+/* a7: chemical potential by bisection on N(mu) = sum_j sum_k 2 f(e_k - mu) d_k c_k over all
+ * columns (requires every column). Writes mu and N(mu) to host. Passage: the bisection for mu
+ * after the first calculation of G (Eq. 3 and the text after it). */
+int elses_find_mu(elses_system sys, double* mu_host, double* n_at_mu_host, void* stream);
+
+/* a8: density matrix rho_(I,a),(J,b) = 2 sum_k f(e_k - mu) Z_(I,a),k c_k of column j = 4J + b
+ * and its energy-weighted form, on the pattern (double[nnzb][4][4] device each; rhoE_dev may be
+ * NULL). In two_pass mode the columns are recomputed first. Passage: Eq. 2, Eq. 3. */
+int elses_density_matrix(elses_system sys, double mu, double* rho_dev, double* rhoE_dev,
+                         void* stream);
+
+/* a9 at a given mu: N(mu), E_band = sum 2 f g c = Tr(rho H), Omega and F_free = Omega + mu N_e
+ * (host doubles; any may be NULL). Passage: Eq. 6. */
+int elses_energies(elses_system sys, double mu, double* n_host, double* e_band_host,
+                   double* omega_host, double* f_free_host, void* stream);
+
+/* a3-a10 in one call: columns, mu, rho, energies, forces F_I = -dF_free/dR_I (double[N][3]
+ * device; may be NULL). Host outputs may be NULL. Passage: energy and force for MD from rho. */
+int elses_energy_force(elses_system sys, double* mu_host, double* e_band_host,
+                       double* f_free_host, double* forces_dev, void* stream);
+
+/* Copy-out accessors: each copies library data into caller-owned device buffers (any of which
+ * may be NULL to skip it) on `stream`; sizes are returned through the host pointers first
+ * (call once with NULL buffers to learn them). */
+int elses_get_pattern(elses_system sys, int* nnzb_host, int* row_ptr_dev, int* col_idx_dev,
+                      void* stream);                               /* int[N+1], int[nnzb]       */
+int elses_get_hs(elses_system sys, double* H_dev, double* S_dev, void* stream);
+                                                                   /* double[nnzb][4][4] each   */
+int elses_get_clusters(elses_system sys, long long* total_host, int* max_cluster_host,
+                       int* cl_ptr_dev, int* cl_idx_dev, void* stream);
+              /* int[N+1], int[total]; with r_cluster <= 0 every cluster is the whole system and
+                 only the sizes are returned                                                   */
+int elses_get_spectra(elses_system sys, int* nu_max_host, double* eps_dev, double* c_dev,
+                      double* d_dev, double* g_dev, int* nu_eff_dev, void* stream);
+              /* double[M][nu_max] each (entries k >= nu_eff[j] are zero), int[M]              */
+/* Counters and timings accumulated since the last build or elses_reset_stats. */
+int elses_get_stats(elses_system sys, elses_stats* stats_host);
+int elses_reset_stats(elses_system sys);
+
+/* Measurement utility (not part of the method): FP64 fused multiply-add throughput of the
+ * current device in GFLOP/s (2 flops per FMA), from a kernel of independent FMA chains on
+ * every SM, timed with CUDA events. */
+int elses_probe_fp64(double* gflops_host, void* stream);
+
+void elses_system_destroy(elses_system sys);
+const char* elses_last_error(void);
+int elses_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ELSES_H */

@@ -1,0 +1,148 @@
+// Internal declarations shared by the translation units of the library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace elses {
+
+struct CellGrid {
+    int nc[3];
+    double len[3];
+    double L[3];
+    int ncell;
+};
+
+// ---------------------------------------------------------------- a1 (neighbors.cu)
+void scan_exclusive(const int* in, int* out, int n, cudaStream_t st);
+void build_cells(const double* pos, int n, const CellGrid& g, int* cell_of, int* cell_count,
+                 int* cell_start, int* cursor, int* cell_atoms, cudaStream_t st);
+void count_lists(const double* pos, int n, const CellGrid& g, const int* cell_of,
+                 const int* cell_start, const int* cell_atoms, double r, int* counts,
+                 int* max_count, cudaStream_t st);
+void fill_lists(const double* pos, int n, const CellGrid& g, const int* cell_of,
+                const int* cell_start, const int* cell_atoms, double r, const int* ptr, int* idx,
+                int cap, int* status, cudaStream_t st);
+
+void check_finite(const double* x, int count, int* status, cudaStream_t st);
+int probe_fp64(double* gflops, cudaStream_t st);   // returns a cudaError_t value
+
+// ---------------------------------------------------------------- a2, a10 (sk_build.cu)
+void sk_build(const double* pos, int n, const double L[3], const SKDev& sk, const int* row_ptr,
+              const int* col_idx, int nnzb, int* row_of, int* tmap, double* H, double* S,
+              cudaStream_t st);
+void forces(const double* pos, int n, const double L[3], const SKDev& sk, const int* row_ptr,
+            const int* col_idx, const int* row_of, const int* tmap, int nnzb, const double* rho,
+            const double* rhoE, double* g_block, double* F, cudaStream_t st);
+
+// ---------------------------------------------------------------- a3, a4 (krylov.cu)
+struct KrylovArgs {
+    int n_atoms;
+    const int* row_ptr;
+    const int* col_idx;
+    const double* H;
+    const double* S;
+    const int* cl_ptr;      // nullptr: every cluster is the whole system
+    const int* cl_idx;
+    int atom_begin, atom_end;
+    const int* order;       // optional: atoms of the batch in processing order (batched form)
+    int* queue;             // optional: work counter of the persistent queue (batched form)
+    int nu_max;             // allocation stride of per-column Krylov arrays
+    int nu_default;
+    int n_classes;
+    int class_max_atoms[4];
+    int class_nu[4];
+    double breakdown_tol;
+    int na_max;             // cluster capacity rounded up to a multiple of 32
+    int deg_max;            // maximum pattern row length
+    double* scratch;        // per resident CTA: 4 warps x (U, SU) x nu_max x na_max x 4
+    double* Hp;             // [col][nu_max*(nu_max+1)/2] packed upper, batch-local col
+    double* Sp;
+    double* urow;           // [col][nu_max]: row j of U, SU, HU
+    double* surow;
+    double* hurow;
+    int* nu_eff;            // [M] global
+    double* UP;             // pattern rows of U: [(e*4 + alpha)*4 + r][nu_max], e - up_block0
+    int up_block0;
+    int* status;
+};
+size_t krylov_smem_bytes(int na_max, int deg_max);
+int krylov_blocks_per_sm(int na_max, int deg_max);
+void krylov_columns(const KrylovArgs& a, int grid, cudaStream_t st);
+
+// ---------------------------------------------------------------- a5, a6 (proj_eig.cu)
+struct EigArgs {
+    int ncols;              // batch columns
+    int col0;               // global index of the first batch column
+    int nu_max;
+    const double* Hp;
+    const double* Sp;
+    const double* urow;
+    const double* surow;
+    const double* hurow;
+    const int* nu_eff;      // [M] global
+    double* work;           // [elem][ncols_pad]
+    int ncols_pad;
+    double* eps;            // [M][nu_max] global
+    double* c;
+    double* d;
+    double* g;
+    double* V;              // [batch col][nu_max*nu_max] (row n = Krylov index, col k = eigen index)
+    int* status;
+};
+size_t eig_work_doubles(int nu_max);
+void projected_eig(const EigArgs& a, cudaStream_t st);
+
+// ---------------------------------------------------------------- a7, a9 (reduce.cu)
+struct BisectState {
+    double lo, hi, mu;
+    double n_lo, n_hi, n_mid;
+    double n_at, e_band, omega;
+    int iter, done, status, pad;
+};
+struct ReduceArgs {
+    int M;
+    int nu_max;
+    const double* eps;
+    const double* c;
+    const double* d;
+    const double* g;
+    const int* nu_eff;
+    double kT;
+    double n_electrons;
+    double tol;
+    int max_iter;
+    BisectState* state;
+    double* partials;       // [grid][4]
+    unsigned* ticket;
+};
+int reduce_grid();
+void bisect_init(const ReduceArgs& a, cudaStream_t st);      // bracket + N(lo), N(hi)
+void bisect_step(const ReduceArgs& a, cudaStream_t st);      // one bisection step (no-op when done)
+void scalars_at(const ReduceArgs& a, double mu, cudaStream_t st);  // N, E_band, Omega at mu
+
+// ---------------------------------------------------------------- a8, G(z) (density.cu)
+struct DensityArgs {
+    int atom_begin, atom_end;
+    const int* row_ptr;
+    const int* tmap;
+    int nu_max;
+    const double* eps;      // [M][nu_max] global
+    const double* c;
+    const int* nu_eff;
+    const double* V;        // batch-local columns
+    int v_col0;             // global column of V's first column
+    const double* UP;
+    int up_block0;
+    double mu, kT;
+    double* rho;
+    double* rhoE;
+    int n_z;
+    const double* z;        // device [n_z][2]
+    double* G;              // [(e*16 + a*4 + b)*n_z + iz][2]
+};
+void density_columns(const DensityArgs& a, cudaStream_t st);
+void green_columns_eval(const DensityArgs& a, cudaStream_t st);
+
+}  // namespace elses

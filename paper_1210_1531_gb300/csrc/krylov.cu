@@ -1,0 +1,419 @@
+// a3 + a4: per-column Krylov build in the S inner product and the projection H' = U^T H U,
+// S' = U^T S U, for every column j = 4J + alpha of a batch of atoms.
+//
+// The paper generates G = (zS - H)^-1 column by column (Eq. 1 with b = e_j) with a Krylov
+// ("multiple Arnoldi") solver on the local cluster of j. The reading built here (the oracle's):
+//     u_1 = e_j / sqrt(S_jj); for n = 1..nu: HU_n = H_C u_n; stop at n = nu;
+//     w = HU_n; two classical Gram-Schmidt passes h = SU^T w, w -= U h;
+//     Sw = S_C w; beta = sqrt(w^T Sw); stop if beta <= tol ||HU_n||_2; u_{n+1} = w / beta,
+// with SU_{n+1} = Sw / beta (S u_{n+1} by linearity; the oracle recomputes it by a product,
+// which agrees to rounding). H'[k][n] = u_k . HU_n and S'[k][n] = u_k . SU_n are formed for
+// k <= n as the columns appear (the oracle symmetrises full products; same values to rounding).
+//
+// GB300 layout: one CTA of 4 warps per atom J, one warp per orbital column alpha; the CTA
+// builds an ELL view of the cluster sub-matrix (atoms sorted by in-cluster degree and assigned
+// to lanes in snake order, so that lane work is balanced) in shared memory once for the 4
+// columns. Each lane owns whole atoms (4 rows); the sparse products gather the source vector
+// from shared memory and stream the 4x4 FP64 blocks (the 4 warps of a CTA read the same blocks,
+// which L1 serves). The S-inner products of CGS2 and the projection are per-lane partial sums
+// reduced by recursive halving (one addition per value). The bases U and SU stay in per-CTA
+// global scratch in [k][position][orbital] order (coalesced 32-byte rows per lane). FP64
+// everywhere; no tensor cores (the work is sparse and FP64).
+#include "internal.h"
+
+namespace elses {
+
+struct __align__(8) Ent {
+    int p4;   // 4 * (lane-slot position of the neighbour atom) = offset into a shared vector
+    int blk;  // BSR block index, -1 = padding
+};
+
+constexpr int kThreads = 32 * kWarpsPerAtom;
+
+__device__ __forceinline__ int bsearch_sorted(const int* a, int n, int v) {
+    int lo = 0, hi = n - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int x = a[mid];
+        if (x == v) return mid;
+        if (x < v) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int nu_for(const KrylovArgs& a, int n_at) {
+    for (int c = 0; c < a.n_classes; ++c)
+        if (n_at <= a.class_max_atoms[c]) return a.class_nu[c];
+    return a.nu_default;
+}
+
+__device__ __forceinline__ double dot4(const double2 a0, const double2 a1, const double2 b0, const double2 b1) {
+    return fma(a0.x, b0.x, fma(a0.y, b0.y, fma(a1.x, b1.x, a1.y * b1.y)));
+}
+
+// y = A x on the cluster (lane-owned rows; x gathered from shared memory).
+__device__ __forceinline__ void spmv(const double* __restrict__ vals, const Ent* __restrict__ ell,
+                                     const int* __restrict__ ell_off, int NS, const double* x,
+                                     double* y, int lane) {
+    for (int s = 0; s < NS; ++s) {
+        const int W = (ell_off[s + 1] - ell_off[s]) >> 5;
+        const Ent* es = ell + ell_off[s] + lane;
+        double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
+        for (int k = 0; k < W; ++k) {
+            const Ent en = es[32 * k];
+            if (en.blk >= 0) {
+                const double2* b2 = reinterpret_cast<const double2*>(vals + 16 * (size_t)en.blk);
+                const double2 a0 = __ldg(b2 + 0), a1 = __ldg(b2 + 1), a2 = __ldg(b2 + 2), a3 = __ldg(b2 + 3);
+                const double2 a4 = __ldg(b2 + 4), a5 = __ldg(b2 + 5), a6 = __ldg(b2 + 6), a7 = __ldg(b2 + 7);
+                const double2 x01 = *reinterpret_cast<const double2*>(x + en.p4);
+                const double2 x23 = *reinterpret_cast<const double2*>(x + en.p4 + 2);
+                y0 = fma(a0.x, x01.x, fma(a0.y, x01.y, fma(a1.x, x23.x, fma(a1.y, x23.y, y0))));
+                y1 = fma(a2.x, x01.x, fma(a2.y, x01.y, fma(a3.x, x23.x, fma(a3.y, x23.y, y1))));
+                y2 = fma(a4.x, x01.x, fma(a4.y, x01.y, fma(a5.x, x23.x, fma(a5.y, x23.y, y2))));
+                y3 = fma(a6.x, x01.x, fma(a6.y, x01.y, fma(a7.x, x23.x, fma(a7.y, x23.y, y3))));
+            }
+        }
+        double2* yo = reinterpret_cast<double2*>(y + 4 * (s * 32 + lane));
+        yo[0] = make_double2(y0, y1);
+        yo[1] = make_double2(y2, y3);
+    }
+}
+
+__device__ __forceinline__ void ld4(const double* p, double2& a, double2& b) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    a = q[0];
+    b = q[1];
+}
+__device__ __forceinline__ void st4(double* p, const double2 a, const double2 b) {
+    double2* q = reinterpret_cast<double2*>(p);
+    q[0] = a;
+    q[1] = b;
+}
+
+size_t krylov_smem_bytes(int na_max, int deg_max) {
+    size_t b = 0;
+    b += sizeof(double) * (size_t)kWarpsPerAtom * 3 * na_max * 4;   // u, hu/w, su per warp
+    b += sizeof(double) * (size_t)kWarpsPerAtom * kMaxNu;            // CGS coefficients
+    b += sizeof(Ent) * (size_t)na_max * deg_max;                     // ELL
+    b += sizeof(int) * (size_t)(4 * na_max + na_max / 32 + 2);       // lists
+    return (b + 15) & ~(size_t)15;
+}
+
+__global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int NA = a.na_max;
+    double* vec = reinterpret_cast<double*>(smem_raw);
+    double* hbuf = vec + (size_t)kWarpsPerAtom * 3 * NA * 4;
+    Ent* ell = reinterpret_cast<Ent*>(hbuf + kWarpsPerAtom * kMaxNu);
+    int* cl = reinterpret_cast<int*>(ell + (size_t)NA * a.deg_max);
+    int* deg = cl + NA;
+    int* pos_of = deg + NA;
+    int* atom_of_rank = pos_of + NA;
+    int* ell_off = atom_of_rank + NA;
+    __shared__ int sh_atom, sh_bad;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int PK = a.nu_max * (a.nu_max + 1) / 2;
+    const size_t warp_scratch = (size_t)2 * a.nu_max * NA * 4;
+    double* Uw = a.scratch + (size_t)blockIdx.x * kWarpsPerAtom * warp_scratch + (size_t)warp * warp_scratch;
+    double* SUw = Uw + (size_t)a.nu_max * NA * 4;
+    const int n_batch = a.atom_end - a.atom_begin;
+
+    for (int iter = 0;; ++iter) {
+        if (tid == 0) {
+            const int idx = a.queue ? atomicAdd(a.queue, 1) : blockIdx.x + iter * gridDim.x;
+            int atom = -1;
+            if (idx < n_batch) atom = a.order ? a.order[idx] : a.atom_begin + idx;
+            sh_atom = atom;
+        }
+        __syncthreads();
+        const int J = sh_atom;
+        if (J < 0) break;
+
+        // ---------------------------------------------------------------- cluster view
+        int n_at, cbase = 0;
+        if (a.cl_ptr) { cbase = a.cl_ptr[J]; n_at = a.cl_ptr[J + 1] - cbase; }
+        else n_at = a.n_atoms;
+        if (n_at > NA) {
+            if (tid == 0) flag(a.status, DEV_CAPACITY);
+            __syncthreads();
+            continue;
+        }
+        for (int q = tid; q < n_at; q += kThreads) cl[q] = a.cl_ptr ? a.cl_idx[cbase + q] : q;
+        __syncthreads();
+        for (int q = tid; q < n_at; q += kThreads) {
+            const int A = cl[q];
+            int cnt = 0;
+            for (int e = a.row_ptr[A]; e < a.row_ptr[A + 1]; ++e) cnt += bsearch_sorted(cl, n_at, a.col_idx[e]) >= 0;
+            deg[q] = cnt;
+        }
+        __syncthreads();
+        const int NS = (n_at + 31) >> 5;
+        for (int q = tid; q < NS * 32; q += kThreads) {
+            int rank = q;   // ranks >= n_at are empty positions
+            if (q < n_at) {
+                const int dq = deg[q];
+                rank = 0;
+                for (int b = 0; b < n_at; ++b) {
+                    const int db = deg[b];
+                    rank += (db > dq) || (db == dq && b < q);
+                }
+            }
+            const int s = rank >> 5;
+            int l = rank & 31;
+            if (s & 1) l = 31 - l;
+            if (q < n_at) pos_of[q] = s * 32 + l;
+            atom_of_rank[rank] = q < n_at ? q : -1 - (s * 32 + l);   // empty: encode its position
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int off = 0;
+            for (int s = 0; s < NS; ++s) {
+                ell_off[s] = off;
+                off += 32 * deg[atom_of_rank[s * 32]];
+            }
+            ell_off[NS] = off;
+            sh_bad = off > NA * a.deg_max;
+        }
+        __syncthreads();
+        if (sh_bad) {
+            if (tid == 0) flag(a.status, DEV_CAPACITY);
+            __syncthreads();
+            continue;
+        }
+        for (int rank = tid; rank < NS * 32; rank += kThreads) {
+            const int q = atom_of_rank[rank];
+            const int p = q >= 0 ? pos_of[q] : -1 - q;
+            const int s = p >> 5, l = p & 31;
+            const int W = (ell_off[s + 1] - ell_off[s]) >> 5;
+            Ent* col = ell + ell_off[s] + l;
+            int k = 0;
+            if (q >= 0) {
+                const int A = cl[q];
+                for (int e = a.row_ptr[A]; e < a.row_ptr[A + 1]; ++e) {
+                    const int b = bsearch_sorted(cl, n_at, a.col_idx[e]);
+                    if (b >= 0) col[32 * (k++)] = Ent{4 * pos_of[b], e};
+                }
+            }
+            for (; k < W; ++k) col[32 * k] = Ent{0, -1};
+        }
+        __syncthreads();
+
+        // ---------------------------------------------------------------- column alpha = warp
+        do {
+            const int alpha = warp;
+            const int j = 4 * J + alpha;
+            const int col = j - 4 * a.atom_begin;
+            const int NP = NS * 32;
+            const int nu = min(nu_for(a, n_at), a.nu_max);
+            const int aJ = bsearch_sorted(cl, n_at, J);
+            double* A = vec + (size_t)(warp * 3) * NA * 4;
+            double* B = A + (size_t)NA * 4;
+            double* C = B + (size_t)NA * 4;
+            double* h = hbuf + warp * kMaxNu;
+            int eJJ = -1;
+            for (int e = a.row_ptr[J]; e < a.row_ptr[J + 1]; ++e)
+                if (a.col_idx[e] == J) eJJ = e;
+            const double sjj = eJJ >= 0 ? a.S[16 * (size_t)eJJ + 5 * alpha] : -1.0;
+            if (aJ < 0 || !(sjj > 0.0)) {   // no diagonal block or S_jj <= 0: bad input
+                if (lane == 0) { flag(a.status, DEV_ARG); a.nu_eff[j] = 0; }
+                break;   // leaves this warp's column (do-while below); the CTA barrier follows
+            }
+            const int jp = 4 * pos_of[aJ] + alpha;
+
+            for (int q = lane; q < NP * 4; q += 32) A[q] = 0.0;
+            __syncwarp();
+            if (lane == 0) A[jp] = 1.0 / sqrt(sjj);
+            __syncwarp();
+            spmv(a.S, ell, ell_off, NS, A, C, lane);
+            for (int s = 0; s < NS; ++s) {
+                const int p = s * 32 + lane;
+                double2 x0, x1;
+                ld4(A + 4 * p, x0, x1);
+                st4(Uw + 4 * (size_t)p, x0, x1);
+                ld4(C + 4 * p, x0, x1);
+                st4(SUw + 4 * (size_t)p, x0, x1);
+            }
+            __syncwarp();
+
+            int nu_eff = nu;
+            for (int n = 0; n < nu; ++n) {
+                spmv(a.H, ell, ell_off, NS, A, B, lane);
+                __syncwarp();
+                if (lane == 0) {
+                    a.urow[(size_t)col * a.nu_max + n] = A[jp];
+                    a.surow[(size_t)col * a.nu_max + n] = C[jp];
+                    a.hurow[(size_t)col * a.nu_max + n] = B[jp];
+                }
+                // pass A: H'[k][n], S'[k][n] and the first CGS coefficients, k <= n
+                double hh = 0.0;
+                for (int k0 = 0; k0 <= n; k0 += 10) {
+                    double acc[32];
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) acc[q] = 0.0;
+                    for (int s = 0; s < NS; ++s) {
+                        const int p = s * 32 + lane;
+                        double2 hu0, hu1, su0, su1;
+                        ld4(B + 4 * p, hu0, hu1);
+                        ld4(C + 4 * p, su0, su1);
+                        if (k0 == 0) acc[30] += dot4(hu0, hu1, hu0, hu1);
+#pragma unroll
+                        for (int kk = 0; kk < 10; ++kk) {
+                            const int k = k0 + kk;
+                            if (k <= n) {
+                                double2 u0, u1, v0, v1;
+                                ld4(Uw + 4 * ((size_t)k * NP + p), u0, u1);
+                                ld4(SUw + 4 * ((size_t)k * NP + p), v0, v1);
+                                acc[kk] += dot4(u0, u1, hu0, hu1);
+                                acc[10 + kk] += dot4(u0, u1, su0, su1);
+                                acc[20 + kk] += dot4(v0, v1, hu0, hu1);
+                            }
+                        }
+                    }
+                    const double r = warp_sum32(acc);
+                    const int kk = lane % 10, kind = lane / 10, k = k0 + kk;
+                    if (lane < 30 && k <= n) {
+                        const size_t pk = (size_t)col * PK + k + (size_t)n * (n + 1) / 2;
+                        if (kind == 0) a.Hp[pk] = r;
+                        else if (kind == 1) a.Sp[pk] = r;
+                        else h[k] = r;
+                    }
+                    if (k0 == 0) hh = __shfl_sync(0xffffffffu, r, 30);
+                }
+                if (n == nu - 1) break;
+                __syncwarp();
+                // sweep B: w = hu - U h (first pass), then the second-pass coefficients SU^T w
+                double acc2[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) acc2[q] = 0.0;
+                for (int s = 0; s < NS; ++s) {
+                    const int p = s * 32 + lane;
+                    double2 w0, w1;
+                    ld4(B + 4 * p, w0, w1);
+                    for (int k = 0; k <= n; ++k) {
+                        const double hk = h[k];
+                        double2 u0, u1;
+                        ld4(Uw + 4 * ((size_t)k * NP + p), u0, u1);
+                        w0.x = fma(-u0.x, hk, w0.x); w0.y = fma(-u0.y, hk, w0.y);
+                        w1.x = fma(-u1.x, hk, w1.x); w1.y = fma(-u1.y, hk, w1.y);
+                    }
+                    st4(B + 4 * p, w0, w1);
+#pragma unroll
+                    for (int kk = 0; kk < 32; ++kk) {
+                        if (kk <= n) {
+                            double2 v0, v1;
+                            ld4(SUw + 4 * ((size_t)kk * NP + p), v0, v1);
+                            acc2[kk] += dot4(v0, v1, w0, w1);
+                        }
+                    }
+                }
+                double r2 = warp_sum32(acc2);
+                __syncwarp();
+                if (lane <= n) h[lane] = r2;
+                if (n >= 32) {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) acc2[q] = 0.0;
+                    for (int s = 0; s < NS; ++s) {
+                        const int p = s * 32 + lane;
+                        double2 w0, w1;
+                        ld4(B + 4 * p, w0, w1);
+#pragma unroll
+                        for (int kk = 0; kk < 32; ++kk) {
+                            if (32 + kk <= n) {
+                                double2 v0, v1;
+                                ld4(SUw + 4 * ((size_t)(32 + kk) * NP + p), v0, v1);
+                                acc2[kk] += dot4(v0, v1, w0, w1);
+                            }
+                        }
+                    }
+                    r2 = warp_sum32(acc2);
+                    if (32 + lane <= n) h[32 + lane] = r2;
+                }
+                __syncwarp();
+                // sweep C: w -= U h (second pass)
+                for (int s = 0; s < NS; ++s) {
+                    const int p = s * 32 + lane;
+                    double2 w0, w1;
+                    ld4(B + 4 * p, w0, w1);
+                    for (int k = 0; k <= n; ++k) {
+                        const double hk = h[k];
+                        double2 u0, u1;
+                        ld4(Uw + 4 * ((size_t)k * NP + p), u0, u1);
+                        w0.x = fma(-u0.x, hk, w0.x); w0.y = fma(-u0.y, hk, w0.y);
+                        w1.x = fma(-u1.x, hk, w1.x); w1.y = fma(-u1.y, hk, w1.y);
+                    }
+                    st4(B + 4 * p, w0, w1);
+                }
+                __syncwarp();
+                // Sw and beta
+                spmv(a.S, ell, ell_off, NS, B, C, lane);
+                double part = 0.0;
+                for (int s = 0; s < NS; ++s) {
+                    const int p = s * 32 + lane;
+                    double2 w0, w1, v0, v1;
+                    ld4(B + 4 * p, w0, w1);
+                    ld4(C + 4 * p, v0, v1);
+                    part += dot4(w0, w1, v0, v1);
+                }
+                const double beta2 = warp_sum(part);
+                if (!(beta2 == beta2)) {   // NaN
+                    if (lane == 0) flag(a.status, DEV_NONFINITE);
+                    nu_eff = n + 1;
+                    break;
+                }
+                const double beta = sqrt(fmax(beta2, 0.0));
+                if (beta <= a.breakdown_tol * sqrt(hh)) {
+                    nu_eff = n + 1;
+                    break;
+                }
+                const double inv = 1.0 / beta;
+                for (int s = 0; s < NS; ++s) {
+                    const int p = s * 32 + lane;
+                    double2 w0, w1, v0, v1;
+                    ld4(B + 4 * p, w0, w1);
+                    ld4(C + 4 * p, v0, v1);
+                    w0.x *= inv; w0.y *= inv; w1.x *= inv; w1.y *= inv;
+                    v0.x *= inv; v0.y *= inv; v1.x *= inv; v1.y *= inv;
+                    st4(A + 4 * p, w0, w1);
+                    st4(C + 4 * p, v0, v1);
+                    st4(Uw + 4 * ((size_t)(n + 1) * NP + p), w0, w1);
+                    st4(SUw + 4 * ((size_t)(n + 1) * NP + p), v0, v1);
+                }
+                __syncwarp();
+            }
+            if (lane == 0) {
+                a.nu_eff[j] = nu_eff;
+                if (nu_eff < nu) flag(a.status, DEV_BREAKDOWN);
+            }
+            __syncwarp();
+            // pattern rows of U for rho / G: blocks e = (J, I) of row J, orbital r of atom I
+            if (a.UP) {
+                const int e0 = a.row_ptr[J], ne = a.row_ptr[J + 1] - e0;
+                for (int q = lane; q < ne * 4; q += 32) {
+                    const int e = e0 + (q >> 2), r = q & 3;
+                    const int b = bsearch_sorted(cl, n_at, a.col_idx[e]);
+                    const int p = pos_of[b];
+                    double* out = a.UP + ((size_t)((e - a.up_block0) * 4 + alpha) * 4 + r) * a.nu_max;
+                    for (int k = 0; k < nu_eff; ++k) out[k] = Uw[4 * ((size_t)k * NP + p) + r];
+                }
+            }
+        } while (0);
+        __syncthreads();
+    }
+}
+
+int krylov_blocks_per_sm(int na_max, int deg_max) {
+    const size_t smem = krylov_smem_bytes(na_max, deg_max);
+    cudaFuncSetAttribute(k_krylov, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_krylov, kThreads, smem);
+    return nb;
+}
+
+void krylov_columns(const KrylovArgs& a, int grid, cudaStream_t st) {
+    const size_t smem = krylov_smem_bytes(a.na_max, a.deg_max);
+    cudaFuncSetAttribute(k_krylov, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_krylov<<<grid, kThreads, smem, st>>>(a);
+}
+
+}  // namespace elses

@@ -1,0 +1,183 @@
+// a7: chemical potential by bisection; a9: N(mu), E_band, Omega at a given mu.
+//
+// With the poles e_k and weights of every column, the electron count is
+//     N(mu) = Tr(rho S) = sum_j sum_k 2 f(e_k - mu) d_k c_k,   f(x) = 1 / (1 + exp(x / kT)),
+// and mu is found "in the bisection method" after the first calculation of G (Eq. 3 and the
+// text after it). Reading: bracket [min e - 40 kT, max e + 40 kT]; each step replaces lo by mid
+// when N(mid) < N_e, else hi; stop when hi - lo < tol or after max_iter steps; mu = (lo+hi)/2.
+// E_band = sum 2 f g c = Tr(rho H) (Eq. 6); Omega = sum d c w(e), w = -2 kT ln(1 + e^{-(e-mu)/kT}).
+//
+// Every evaluation is one grid-wide reduction in a fixed order (per-thread column strides, a
+// fixed block tree, then the block partials summed in index order by the last block to finish,
+// found with an atomic ticket -- no thread ever waits on another block). The bracket lives in
+// device memory and each bisection launch reads and updates it, so the whole search is a fixed
+// sequence of launches with no host round trip; launches after convergence return at once.
+#include "internal.h"
+
+namespace elses {
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double fermi(double x) {   // x = (e - mu) / kT
+    if (x > 0.0) {
+        const double t = exp(-x);
+        return t / (1.0 + t);
+    }
+    return 1.0 / (1.0 + exp(x));
+}
+
+__device__ __forceinline__ double omega_w(double e, double mu, double kT) {
+    const double x = (e - mu) / kT;
+    if (x >= 0.0) return -2.0 * kT * log1p(exp(-x));
+    return 2.0 * (x * kT) - 2.0 * kT * log1p(exp(x));
+}
+
+int reduce_grid() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return 2 * (sms > 0 ? sms : 1);
+}
+
+template <int NV>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* partials, int nv_stride) {
+    __shared__ double sh[NV][kRedThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double x = warp_sum(v[q]);
+        if (lane == 0) sh[q][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double s = 0.0;
+            for (int i = 0; i < kRedThreads / 32; ++i) s += sh[q][i];
+            partials[(size_t)blockIdx.x * nv_stride + q] = s;
+        }
+    }
+}
+
+// Returns true in thread 0 of the last block to finish (after all partials are visible).
+__device__ __forceinline__ bool last_block(unsigned* ticket) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    return is_last && threadIdx.x == 0;
+}
+
+__global__ void k_bracket(const ReduceArgs a) {
+    double mn = 1e300, mx = -1e300;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.M; j += gridDim.x * blockDim.x) {
+        const int nu = a.nu_eff[j];
+        for (int k = 0; k < nu; ++k) {
+            const double e = a.eps[(size_t)j * a.nu_max + k];
+            mn = fmin(mn, e);
+            mx = fmax(mx, e);
+        }
+    }
+    __shared__ double smn[kRedThreads], smx[kRedThreads];
+    smn[threadIdx.x] = mn;
+    smx[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            smn[threadIdx.x] = fmin(smn[threadIdx.x], smn[threadIdx.x + o]);
+            smx[threadIdx.x] = fmax(smx[threadIdx.x], smx[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a.partials[4 * (size_t)blockIdx.x] = smn[0];
+        a.partials[4 * (size_t)blockIdx.x + 1] = smx[0];
+    }
+    if (last_block(a.ticket)) {
+        double lo = 1e300, hi = -1e300;
+        for (int b = 0; b < gridDim.x; ++b) {
+            lo = fmin(lo, __ldcg(a.partials + 4 * (size_t)b));
+            hi = fmax(hi, __ldcg(a.partials + 4 * (size_t)b + 1));
+        }
+        BisectState* s = a.state;
+        s->lo = lo - 40.0 * a.kT;
+        s->hi = hi + 40.0 * a.kT;
+        s->iter = 0;
+        s->done = (a.max_iter <= 0) || !(s->hi - s->lo >= a.tol);
+        s->status = (lo <= hi && isfinite(lo) && isfinite(hi)) ? 0 : DEV_NONFINITE;
+        s->mu = 0.5 * (s->lo + s->hi);
+        *a.ticket = 0u;
+    }
+}
+
+// mode 0: N(lo); 1: N(hi) and the bracket check; 2: one bisection step; 3: scalars at mu_in.
+__global__ void k_count(const ReduceArgs a, int mode, double mu_in) {
+    BisectState* s = a.state;
+    double x;
+    if (mode == 2) {
+        if (s->done) return;
+        x = 0.5 * (s->lo + s->hi);
+    } else if (mode == 0) x = s->lo;
+    else if (mode == 1) x = s->hi;
+    else x = mu_in;
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.M; j += gridDim.x * blockDim.x) {
+        const int nu = a.nu_eff[j];
+        const size_t b = (size_t)j * a.nu_max;
+        for (int k = 0; k < nu; ++k) {
+            const double e = a.eps[b + k], cc = a.c[b + k];
+            const double f2 = 2.0 * fermi((e - x) / a.kT);
+            v[0] += f2 * a.d[b + k] * cc;
+            if (mode == 3) {
+                v[1] += f2 * a.g[b + k] * cc;
+                v[2] += a.d[b + k] * cc * omega_w(e, x, a.kT);
+            }
+        }
+    }
+    block_reduce_store<3>(v, a.partials, 4);
+    if (last_block(a.ticket)) {
+        double N = 0.0, E = 0.0, Om = 0.0;
+        for (int b = 0; b < gridDim.x; ++b) {
+            N += __ldcg(a.partials + 4 * (size_t)b);
+            E += __ldcg(a.partials + 4 * (size_t)b + 1);
+            Om += __ldcg(a.partials + 4 * (size_t)b + 2);
+        }
+        if (mode == 0) s->n_lo = N;
+        else if (mode == 1) {
+            s->n_hi = N;
+            if (!(s->n_lo < a.n_electrons && a.n_electrons <= N)) {
+                s->status |= DEV_NO_BRACKET;
+                s->done = 1;
+            }
+        } else if (mode == 2) {
+            if (N < a.n_electrons) s->lo = x; else s->hi = x;
+            s->n_mid = N;
+            s->iter += 1;
+            if (s->iter >= a.max_iter || !(s->hi - s->lo >= a.tol)) s->done = 1;
+            s->mu = 0.5 * (s->lo + s->hi);
+        } else {
+            s->n_at = N;
+            s->e_band = E;
+            s->omega = Om;
+        }
+        *a.ticket = 0u;
+    }
+}
+
+void bisect_init(const ReduceArgs& a, cudaStream_t st) {
+    const int G = reduce_grid();
+    k_bracket<<<G, kRedThreads, 0, st>>>(a);
+    k_count<<<G, kRedThreads, 0, st>>>(a, 0, 0.0);
+    k_count<<<G, kRedThreads, 0, st>>>(a, 1, 0.0);
+}
+
+void bisect_step(const ReduceArgs& a, cudaStream_t st) {
+    k_count<<<reduce_grid(), kRedThreads, 0, st>>>(a, 2, 0.0);
+}
+
+void scalars_at(const ReduceArgs& a, double mu, cudaStream_t st) {
+    k_count<<<reduce_grid(), kRedThreads, 0, st>>>(a, 3, mu);
+}
+
+}  // namespace elses

@@ -1,0 +1,813 @@
+// Host runtime of the C ABI (include/elses.h): system handle, memory, launch sequencing.
+//
+// Order of one energy + force evaluation (the memory-saving workflow of Eq. 3 when two_pass,
+// otherwise the per-column quantities of the first pass are kept and reused):
+//   build_clusters : cells -> neighbour CSR -> cluster CSR -> Slater-Koster H, S   (a1, a2)
+//   green_columns  : batches of atoms: Krylov build + projection (one CTA per atom), then the
+//                    projected eigenproblem (one thread per column)                  (a3-a6)
+//   find_mu        : device-resident bisection, one launch per step                  (a7)
+//   density_matrix : rho, rhoE on the pattern                                        (a8)
+//   energies       : N, E_band, Omega, F_free                                        (a9)
+//   forces         : per-block gradient contraction, per-atom sums                   (a10)
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace elses;
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(x)                                                                        \
+    do {                                                                                   \
+        cudaError_t e_ = (x);                                                              \
+        if (e_ != cudaSuccess) return fail(ELSES_ERR_CUDA, "%s: %s", #x, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define TRY(x)                     \
+    do {                           \
+        int r_ = (x);              \
+        if (r_ < 0) return r_;     \
+    } while (0)
+
+template <class T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t cap = 0;
+    int ensure(size_t n) {
+        if (n <= cap && p) return 0;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = std::max<size_t>(n, 1);
+        if (cudaMalloc(&p, want * sizeof(T)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ELSES_ERR_OOM, "device allocation of %zu bytes failed", want * sizeof(T));
+        }
+        cap = want;
+        return 0;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+struct elses_system_s {
+    int n = 0, M = 0;
+    double box[3] = {0, 0, 0};
+    elses_sk sk{};
+    elses_params p{};
+    SKDev skd{};
+    int num_sms = 0;
+    CellGrid grid{};
+    bool user_hs = false;
+
+    DevBuf<double> pos;
+    DevBuf<int> cell_of, cell_count, cell_start, cursor, cell_atoms;
+    DevBuf<int> row_cnt, row_ptr, col_idx, row_of, tmap;
+    DevBuf<int> cl_cnt, cl_ptr, cl_idx;
+    DevBuf<int> counters;   // [0] max neighbours, [1] max cluster, [2] status, [3] queue
+    DevBuf<double> H, S;
+    int nnzb = 0, max_nb = 0, max_cl = 0;
+    long long cl_total = 0;
+    std::vector<int> h_row_ptr;
+
+    int nu_max = 0, na_max = 0, k3_grid = 0, batch_atoms = 0;
+    DevBuf<double> kscratch, Hp, Sp, urow, surow, hurow, eigwork;
+    DevBuf<double> eps, cc, dd, gg, V, UP, Vb, UPb;
+    DevBuf<int> nu_eff, order;
+    DevBuf<double> rho, rhoE, gblock;
+    DevBuf<double> partials, zbuf;
+    DevBuf<BisectState> bstate;
+    DevBuf<unsigned> ticket;
+    std::vector<char> atom_done;
+    long long atoms_done = 0;
+
+    elses_stats stats{};
+    double mu = 0.0;
+    bool have_mu = false;
+
+    // CUDA-event timing of kernel groups (params.timing = 1)
+    struct EvPair { cudaEvent_t a, b; int cat; };
+    std::vector<EvPair> pending;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t ev() {
+        cudaEvent_t e;
+        if (!pool.empty()) { e = pool.back(); pool.pop_back(); }
+        else cudaEventCreate(&e);
+        return e;
+    }
+    void tic(int cat, cudaStream_t st) {
+        if (!p.timing) return;
+        EvPair q{ev(), ev(), cat};
+        cudaEventRecord(q.a, st);
+        pending.push_back(q);
+    }
+    void toc(cudaStream_t st) {
+        if (!p.timing || pending.empty()) return;
+        cudaEventRecord(pending.back().b, st);
+    }
+    void collect() {   // after a synchronisation of the stream
+        for (auto& q : pending) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+                double* t = &stats.t_krylov_ms;
+                t[q.cat] += ms;
+            }
+            pool.push_back(q.a);
+            pool.push_back(q.b);
+        }
+        pending.clear();
+        cudaGetLastError();
+    }
+    ~elses_system_s() {
+        for (auto& q : pending) { pool.push_back(q.a); pool.push_back(q.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+enum { T_KRYLOV = 0, T_EIG = 1, T_BISECT = 2, T_DENSITY = 3, T_FORCE = 4 };
+
+namespace {
+
+int nu_of_params(const elses_params& p) {
+    int m = p.nu;
+    for (int c = 0; c < p.n_classes; ++c) m = std::max(m, p.class_nu[c]);
+    return m;
+}
+
+int check_status(elses_system s, cudaStream_t st, bool allow_breakdown_warning = true) {
+    int h = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h, s->counters.p + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY(cudaGetLastError());
+    s->collect();
+    if (h & DEV_CAPACITY) return fail(ELSES_ERR_CAPACITY, "a neighbour or cluster list exceeded its capacity");
+    if (h & DEV_NOT_SPD) return fail(ELSES_ERR_NOT_SPD, "projected overlap S' is not positive definite");
+    if (h & DEV_NONFINITE) return fail(ELSES_ERR_NONFINITE, "non-finite value in the Krylov build");
+    if (h & DEV_TIMEOUT) return fail(ELSES_ERR_TIMEOUT, "projected eigensolver did not converge");
+    if (h & DEV_ARG) return fail(ELSES_ERR_ARG, "invalid device-side argument");
+    if ((h & DEV_BREAKDOWN) && allow_breakdown_warning) return ELSES_WARN_BREAKDOWN;
+    return ELSES_OK;
+}
+
+int clear_status(elses_system s, cudaStream_t st) {
+    CUDA_TRY(cudaMemsetAsync(s->counters.p + 2, 0, sizeof(int), st));
+    return 0;
+}
+
+// Column storage, Krylov launch shape and batch buffers for the current sizes.
+int prepare_columns(elses_system s) {
+    s->nu_max = nu_of_params(s->p);
+    s->na_max = ((s->max_cl + 31) / 32) * 32;
+    const int nm = s->nu_max;
+    const size_t smem = krylov_smem_bytes(s->na_max, s->max_nb);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if ((int)smem > smem_optin)
+        return fail(ELSES_ERR_CAPACITY, "cluster of %d atoms needs %zu B of shared memory (max %d)",
+                    s->max_cl, smem, smem_optin);
+    int bps = krylov_blocks_per_sm(s->na_max, s->max_nb);
+    if (bps < 1) return fail(ELSES_ERR_CAPACITY, "Krylov kernel cannot be resident (smem %zu B)", smem);
+    s->k3_grid = s->num_sms * bps;
+    s->k3_grid = std::min(s->k3_grid, std::max(1, s->n));
+    const size_t per_cta = (size_t)kWarpsPerAtom * 2 * nm * s->na_max * 4;
+    TRY(s->kscratch.ensure(per_cta * s->k3_grid));
+    // batch of atoms for the Krylov -> eigensolver hand-off
+    const size_t PK = (size_t)nm * (nm + 1) / 2;
+    const size_t per_col = 2 * PK + 3 * (size_t)nm + eig_work_doubles(nm);
+    size_t cols = std::max<size_t>(128, (size_t)(1u << 29) / (per_col * sizeof(double)));   // ~512 MB
+    s->batch_atoms = (int)std::min<size_t>((size_t)s->n, std::max<size_t>(32, cols / 4));
+    const size_t bc = 4 * (size_t)s->batch_atoms;
+    const size_t bc_pad = ((bc + 31) / 32) * 32;
+    TRY(s->Hp.ensure(bc * PK));
+    TRY(s->Sp.ensure(bc * PK));
+    TRY(s->urow.ensure(bc * nm));
+    TRY(s->surow.ensure(bc * nm));
+    TRY(s->hurow.ensure(bc * nm));
+    TRY(s->eigwork.ensure(bc_pad * eig_work_doubles(nm)));
+    const size_t M = s->M;
+    TRY(s->eps.ensure(M * nm));
+    TRY(s->cc.ensure(M * nm));
+    TRY(s->dd.ensure(M * nm));
+    TRY(s->gg.ensure(M * nm));
+    TRY(s->nu_eff.ensure(M));
+    if (!s->p.two_pass) {
+        TRY(s->V.ensure(M * nm * nm));
+        TRY(s->UP.ensure((size_t)s->nnzb * 16 * nm));
+    } else {
+        int maxblk = 0;
+        for (int b = 0; b < s->n; b += s->batch_atoms) {
+            const int e = std::min(s->n, b + s->batch_atoms);
+            maxblk = std::max(maxblk, s->h_row_ptr[e] - s->h_row_ptr[b]);
+        }
+        TRY(s->Vb.ensure(bc * nm * nm));
+        TRY(s->UPb.ensure((size_t)maxblk * 16 * nm));
+    }
+    TRY(s->rho.ensure((size_t)s->nnzb * 16));
+    TRY(s->rhoE.ensure((size_t)s->nnzb * 16));
+    TRY(s->gblock.ensure((size_t)s->nnzb * 3));
+    TRY(s->partials.ensure(4 * (size_t)reduce_grid()));
+    TRY(s->bstate.ensure(1));
+    TRY(s->ticket.ensure(1));
+    CUDA_TRY(cudaMemset(s->ticket.p, 0, sizeof(unsigned)));
+    s->atom_done.assign(s->n, 0);
+    s->atoms_done = 0;
+    s->have_mu = false;
+    return 0;
+}
+
+// Krylov build + projected eigenproblem for atoms [b, e). Writes V and UP either to the stored
+// arrays or to the batch buffers (two-pass), returning the pointers used.
+int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_col0,
+              double** UP_out, int* up_block0, cudaStream_t st, bool need_rows = true) {
+    const int nm = s->nu_max;
+    KrylovArgs ka{};
+    ka.n_atoms = s->n;
+    ka.row_ptr = s->row_ptr.p;
+    ka.col_idx = s->col_idx.p;
+    ka.H = s->H.p;
+    ka.S = s->S.p;
+    ka.cl_ptr = s->p.r_cluster > 0 ? s->cl_ptr.p : nullptr;
+    ka.cl_idx = s->p.r_cluster > 0 ? s->cl_idx.p : nullptr;
+    ka.atom_begin = b;
+    ka.atom_end = e;
+    ka.nu_max = nm;
+    ka.nu_default = s->p.nu;
+    ka.n_classes = s->p.n_classes;
+    for (int c = 0; c < 4; ++c) {
+        ka.class_max_atoms[c] = s->p.class_max_atoms[c];
+        ka.class_nu[c] = s->p.class_nu[c];
+    }
+    ka.breakdown_tol = s->p.breakdown_tol;
+    ka.na_max = s->na_max;
+    ka.deg_max = s->max_nb;
+    ka.scratch = s->kscratch.p;
+    ka.Hp = s->Hp.p;
+    ka.Sp = s->Sp.p;
+    ka.urow = s->urow.p;
+    ka.surow = s->surow.p;
+    ka.hurow = s->hurow.p;
+    ka.nu_eff = s->nu_eff.p;
+    ka.status = s->counters.p + 2;
+    if (stored) {
+        ka.UP = s->UP.p;
+        ka.up_block0 = 0;
+    } else {
+        ka.UP = s->UPb.p;
+        ka.up_block0 = s->h_row_ptr[b];
+    }
+    if (!need_rows) ka.UP = nullptr;
+    if (s->p.schedule == 1) {
+        // batched form: persistent CTAs pull atoms from a queue ordered by cluster size
+        CUDA_TRY(cudaMemsetAsync(s->counters.p + 3, 0, sizeof(int), st));
+        ka.queue = s->counters.p + 3;
+        ka.order = s->order.p ? s->order.p + b : nullptr;
+    }
+    const int grid = std::min(s->k3_grid, e - b);
+    s->tic(T_KRYLOV, st);
+    krylov_columns(ka, grid, st);
+    s->toc(st);
+    s->stats.launches++;
+    s->stats.krylov_launches++;
+
+    EigArgs ea{};
+    ea.ncols = 4 * (e - b);
+    ea.col0 = 4 * b;
+    ea.nu_max = nm;
+    ea.Hp = s->Hp.p;
+    ea.Sp = s->Sp.p;
+    ea.urow = s->urow.p;
+    ea.surow = s->surow.p;
+    ea.hurow = s->hurow.p;
+    ea.nu_eff = s->nu_eff.p;
+    ea.work = s->eigwork.p;
+    ea.ncols_pad = ((4 * s->batch_atoms + 31) / 32) * 32;
+    ea.eps = s->eps.p;
+    ea.c = s->cc.p;
+    ea.d = s->dd.p;
+    ea.g = s->gg.p;
+    ea.V = stored ? s->V.p + (size_t)4 * b * nm * nm : s->Vb.p;
+    ea.status = s->counters.p + 2;
+    s->tic(T_EIG, st);
+    projected_eig(ea, st);
+    s->toc(st);
+    s->stats.launches++;
+    s->stats.columns += 4LL * (e - b);
+    *V_out = ea.V;
+    *v_col0 = 4 * b;
+    *UP_out = ka.UP;
+    *up_block0 = ka.up_block0;
+    return 0;
+}
+
+int check_built(elses_system s) {
+    if (!s) return fail(ELSES_ERR_ARG, "null system");
+    if (s->n <= 0 || !s->H.p) return fail(ELSES_ERR_STATE, "system not built");
+    return 0;
+}
+
+ReduceArgs reduce_args(elses_system s) {
+    ReduceArgs r{};
+    r.M = s->M;
+    r.nu_max = s->nu_max;
+    r.eps = s->eps.p;
+    r.c = s->cc.p;
+    r.d = s->dd.p;
+    r.g = s->gg.p;
+    r.nu_eff = s->nu_eff.p;
+    r.kT = s->p.kT;
+    r.n_electrons = s->p.n_electrons;
+    r.tol = s->p.mu_tol;
+    r.max_iter = s->p.max_bisect;
+    r.state = s->bstate.p;
+    r.partials = s->partials.p;
+    r.ticket = s->ticket.p;
+    return r;
+}
+
+DensityArgs density_args(elses_system s, double mu, double* rho, double* rhoE) {
+    DensityArgs d{};
+    d.row_ptr = s->row_ptr.p;
+    d.tmap = s->tmap.p;
+    d.nu_max = s->nu_max;
+    d.eps = s->eps.p;
+    d.c = s->cc.p;
+    d.nu_eff = s->nu_eff.p;
+    d.mu = mu;
+    d.kT = s->p.kT;
+    d.rho = rho;
+    d.rhoE = rhoE;
+    return d;
+}
+
+}  // namespace
+
+extern "C" {
+
+int elses_version(void) { return 1; }
+
+const char* elses_last_error(void) { return g_err.c_str(); }
+
+void elses_system_destroy(elses_system s) {
+    if (!s) return;
+    DevBuf<double>* dbs[] = {&s->pos, &s->H, &s->S, &s->kscratch, &s->Hp, &s->Sp, &s->urow,
+                             &s->surow, &s->hurow, &s->eigwork, &s->eps, &s->cc, &s->dd, &s->gg,
+                             &s->V, &s->UP, &s->Vb, &s->UPb, &s->rho, &s->rhoE, &s->gblock,
+                             &s->partials, &s->zbuf};
+    for (auto* b : dbs) b->release();
+    DevBuf<int>* ibs[] = {&s->cell_of, &s->cell_count, &s->cell_start, &s->cursor, &s->cell_atoms,
+                          &s->row_cnt, &s->row_ptr, &s->col_idx, &s->row_of, &s->tmap, &s->cl_cnt,
+                          &s->cl_ptr, &s->cl_idx, &s->counters, &s->nu_eff, &s->order};
+    for (auto* b : ibs) b->release();
+    s->bstate.release();
+    s->ticket.release();
+    delete s;
+}
+
+int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
+                         const double* box_host, const elses_sk* sk, const elses_params* params,
+                         void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!sys || !pos_dev || !box_host || !sk || !params) return fail(ELSES_ERR_ARG, "null argument");
+    if (n_atoms <= 0) return fail(ELSES_ERR_ARG, "n_atoms must be positive");
+    elses_params p = *params;
+    if (p.breakdown_tol <= 0) p.breakdown_tol = 1e-12;
+    if (p.mu_tol <= 0) p.mu_tol = 1e-13;
+    if (p.max_bisect <= 0) p.max_bisect = 100;
+    if (p.max_neighbors <= 0) p.max_neighbors = 64;
+    if (p.max_cluster <= 0) p.max_cluster = 512;
+    if (p.nu < 1 || p.nu > kMaxNu) return fail(ELSES_ERR_ARG, "nu must be in [1, %d]", kMaxNu);
+    if (p.n_classes < 0 || p.n_classes > 4) return fail(ELSES_ERR_ARG, "n_classes must be in [0, 4]");
+    for (int c = 0; c < p.n_classes; ++c)
+        if (p.class_nu[c] < 1 || p.class_nu[c] > kMaxNu) return fail(ELSES_ERR_ARG, "class_nu out of range");
+    if (!(p.kT > 0)) return fail(ELSES_ERR_ARG, "kT must be positive");
+    if (!(sk->r_cut > sk->r_on) || !(sk->r_on > 0)) return fail(ELSES_ERR_ARG, "need 0 < r_on < r_cut");
+    for (int d = 0; d < 3; ++d) {
+        if (!(box_host[d] > 2.0 * sk->r_cut)) return fail(ELSES_ERR_ARG, "box must exceed 2*r_cut");
+        if (p.r_cluster > 0 && !(box_host[d] > 2.0 * p.r_cluster))
+            return fail(ELSES_ERR_ARG, "box must exceed 2*r_cluster");
+    }
+    if (p.r_cluster > 0 && p.r_cluster < sk->r_cut)
+        return fail(ELSES_ERR_ARG, "r_cluster must be >= r_cut (the pattern rows lie in the cluster)");
+    elses_system s = *sys;
+    if (s && s->n != n_atoms) return fail(ELSES_ERR_ARG, "rebuild with a different atom count");
+    if (!s) {
+        s = new elses_system_s();
+        *sys = s;
+    }
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    s->n = n_atoms;
+    s->M = 4 * n_atoms;
+    std::memcpy(s->box, box_host, sizeof s->box);
+    s->sk = *sk;
+    s->p = p;
+    s->user_hs = false;
+    s->skd.Es = sk->Es;
+    s->skd.Ep = sk->Ep;
+    for (int x = 0; x < 4; ++x) {
+        s->skd.V0[x] = sk->V0[x];
+        s->skd.qH[x] = sk->qH[x];
+        s->skd.S0[x] = sk->S0[x];
+        s->skd.qS[x] = sk->qS[x];
+    }
+    s->skd.r0 = sk->r0;
+    s->skd.r_on = sk->r_on;
+    s->skd.r_cut = sk->r_cut;
+    s->collect();
+    s->stats = elses_stats{};
+    const int n = n_atoms;
+    TRY(s->pos.ensure(3 * (size_t)n));
+    CUDA_TRY(cudaMemcpyAsync(s->pos.p, pos_dev, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st));
+    TRY(s->counters.ensure(8));
+    CUDA_TRY(cudaMemsetAsync(s->counters.p, 0, sizeof(int) * 8, st));
+    check_finite(s->pos.p, 3 * n, s->counters.p + 2, st);
+    s->stats.launches++;
+    {
+        int h = 0;
+        CUDA_TRY(cudaMemcpyAsync(&h, s->counters.p + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        if (h) return fail(ELSES_ERR_NONFINITE, "positions contain NaN or Inf");
+    }
+
+    // cell grid with edges >= r_cut
+    CellGrid& g = s->grid;
+    g.ncell = 1;
+    for (int d = 0; d < 3; ++d) {
+        g.L[d] = box_host[d];
+        g.nc[d] = std::max(1, std::min(256, (int)std::floor(box_host[d] / sk->r_cut)));
+        g.len[d] = box_host[d] / g.nc[d];
+        g.ncell *= g.nc[d];
+    }
+    TRY(s->cell_of.ensure(n));
+    TRY(s->cell_count.ensure(g.ncell));
+    TRY(s->cell_start.ensure(g.ncell + 1));
+    TRY(s->cursor.ensure(g.ncell));
+    TRY(s->cell_atoms.ensure(n));
+    build_cells(s->pos.p, n, g, s->cell_of.p, s->cell_count.p, s->cell_start.p, s->cursor.p,
+                s->cell_atoms.p, st);
+    s->stats.launches += 4;
+
+    // neighbour pattern
+    TRY(s->row_cnt.ensure(n));
+    TRY(s->row_ptr.ensure(n + 1));
+    count_lists(s->pos.p, n, g, s->cell_of.p, s->cell_start.p, s->cell_atoms.p, sk->r_cut,
+                s->row_cnt.p, s->counters.p + 0, st);
+    scan_exclusive(s->row_cnt.p, s->row_ptr.p, n, st);
+    s->stats.launches += 2;
+    int hc[2] = {0, 0};
+    CUDA_TRY(cudaMemcpyAsync(&hc[0], s->counters.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    s->h_row_ptr.resize(n + 1);
+    CUDA_TRY(cudaMemcpyAsync(s->h_row_ptr.data(), s->row_ptr.p, sizeof(int) * (n + 1),
+                             cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    s->max_nb = hc[0];
+    s->nnzb = s->h_row_ptr[n];
+    if (s->max_nb > p.max_neighbors)
+        return fail(ELSES_ERR_CAPACITY, "an atom has %d neighbours (max_neighbors %d)", s->max_nb, p.max_neighbors);
+    TRY(s->col_idx.ensure(s->nnzb));
+    TRY(s->row_of.ensure(s->nnzb));
+    TRY(s->tmap.ensure(s->nnzb));
+    fill_lists(s->pos.p, n, g, s->cell_of.p, s->cell_start.p, s->cell_atoms.p, sk->r_cut,
+               s->row_ptr.p, s->col_idx.p, p.max_neighbors, s->counters.p + 2, st);
+    s->stats.launches++;
+
+    // clusters
+    if (p.r_cluster > 0) {
+        TRY(s->cl_cnt.ensure(n));
+        TRY(s->cl_ptr.ensure(n + 1));
+        count_lists(s->pos.p, n, g, s->cell_of.p, s->cell_start.p, s->cell_atoms.p, p.r_cluster,
+                    s->cl_cnt.p, s->counters.p + 1, st);
+        scan_exclusive(s->cl_cnt.p, s->cl_ptr.p, n, st);
+        s->stats.launches += 2;
+        int tot = 0;
+        CUDA_TRY(cudaMemcpyAsync(&hc[1], s->counters.p + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(&tot, s->cl_ptr.p + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        s->max_cl = hc[1];
+        s->cl_total = tot;
+        if (s->max_cl > p.max_cluster)
+            return fail(ELSES_ERR_CAPACITY, "a cluster has %d atoms (max_cluster %d)", s->max_cl, p.max_cluster);
+        TRY(s->cl_idx.ensure(std::max(1, tot)));
+        fill_lists(s->pos.p, n, g, s->cell_of.p, s->cell_start.p, s->cell_atoms.p, p.r_cluster,
+                   s->cl_ptr.p, s->cl_idx.p, p.max_cluster, s->counters.p + 2, st);
+        s->stats.launches++;
+    } else {
+        if (n > p.max_cluster)
+            return fail(ELSES_ERR_CAPACITY, "whole-system cluster of %d atoms exceeds max_cluster %d", n, p.max_cluster);
+        s->max_cl = n;
+        s->cl_total = (long long)n * n;
+    }
+
+    // Slater-Koster H and S
+    TRY(s->H.ensure((size_t)s->nnzb * 16));
+    TRY(s->S.ensure((size_t)s->nnzb * 16));
+    sk_build(s->pos.p, n, s->box, s->skd, s->row_ptr.p, s->col_idx.p, s->nnzb, s->row_of.p, s->tmap.p,
+             s->H.p, s->S.p, st);
+    s->stats.launches += 2;
+    TRY(check_status(s, st));
+    TRY(prepare_columns(s));
+    // queue order for the batched form: largest clusters first inside each batch
+    if (p.schedule == 1 && p.r_cluster > 0) {
+        std::vector<int> cnt(n), hptr(n + 1);
+        CUDA_TRY(cudaMemcpy(hptr.data(), s->cl_ptr.p, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost));
+        std::vector<int> ord(n);
+        for (int b = 0; b < n; b += s->batch_atoms) {
+            const int e = std::min(n, b + s->batch_atoms);
+            for (int i = b; i < e; ++i) ord[i] = i;
+            std::stable_sort(ord.begin() + b, ord.begin() + e, [&](int x, int y) {
+                return hptr[x + 1] - hptr[x] > hptr[y + 1] - hptr[y];
+            });
+        }
+        TRY(s->order.ensure(n));
+        CUDA_TRY(cudaMemcpy(s->order.p, ord.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    }
+    return ELSES_OK;
+}
+
+int elses_set_hs(elses_system s, const double* H_dev, const double* S_dev, void* stream) {
+    TRY(check_built(s));
+    if (!H_dev || !S_dev) return fail(ELSES_ERR_ARG, "null H or S");
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(s->H.p, H_dev, sizeof(double) * 16 * s->nnzb, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(s->S.p, S_dev, sizeof(double) * 16 * s->nnzb, cudaMemcpyDeviceToDevice, st));
+    s->user_hs = true;
+    s->atom_done.assign(s->n, 0);
+    s->atoms_done = 0;
+    s->have_mu = false;
+    return ELSES_OK;
+}
+
+int elses_green_columns(elses_system s, int col_begin, int col_end, int n_z, const double* z_host,
+                        double* G_dev, int* nu_eff_dev, void* stream) {
+    TRY(check_built(s));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (col_begin < 0 || col_end > s->M || col_begin > col_end || col_begin % 4 || col_end % 4)
+        return fail(ELSES_ERR_ARG, "column range must be whole atoms inside [0, M)");
+    if (n_z < 0 || (n_z > 0 && (!z_host || !G_dev))) return fail(ELSES_ERR_ARG, "bad z / G arguments");
+    TRY(clear_status(s, st));
+    if (n_z > 0) {
+        TRY(s->zbuf.ensure(2 * (size_t)n_z));
+        CUDA_TRY(cudaMemcpyAsync(s->zbuf.p, z_host, sizeof(double) * 2 * n_z, cudaMemcpyHostToDevice, st));
+    }
+    const int a0 = col_begin / 4, a1 = col_end / 4;
+    const bool stored = !s->p.two_pass;
+    for (int b = a0; b < a1; b += s->batch_atoms) {
+        const int e = std::min(a1, b + s->batch_atoms);
+        double* V;
+        double* UP;
+        int v0, u0;
+        // first calculation of G in the two-pass workflow keeps only the spectra
+        TRY(run_batch(s, b, e, stored, &V, &v0, &UP, &u0, st, stored || n_z > 0));
+        if (n_z > 0) {
+            DensityArgs d = density_args(s, 0.0, nullptr, nullptr);
+            d.atom_begin = b;
+            d.atom_end = e;
+            d.V = V;
+            d.v_col0 = v0;
+            d.UP = UP;
+            d.up_block0 = u0;
+            d.n_z = n_z;
+            d.z = s->zbuf.p;
+            d.G = G_dev;
+            green_columns_eval(d, st);
+            s->stats.launches++;
+        }
+        for (int a = b; a < e; ++a)
+            if (!s->atom_done[a]) { s->atom_done[a] = 1; s->atoms_done++; }
+    }
+    if (nu_eff_dev && a1 > a0)
+        CUDA_TRY(cudaMemcpyAsync(nu_eff_dev + col_begin, s->nu_eff.p + col_begin,
+                                 sizeof(int) * (col_end - col_begin), cudaMemcpyDeviceToDevice, st));
+    s->have_mu = false;
+    return check_status(s, st);
+}
+
+int elses_find_mu(elses_system s, double* mu_host, double* n_at_mu_host, void* stream) {
+    TRY(check_built(s));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (s->atoms_done != s->n) return fail(ELSES_ERR_STATE, "find_mu needs every column (call green_columns first)");
+    ReduceArgs r = reduce_args(s);
+    s->tic(T_BISECT, st);
+    bisect_init(r, st);
+    s->stats.launches += 3;
+    for (int it = 0; it < s->p.max_bisect; ++it) bisect_step(r, st);
+    s->stats.launches += s->p.max_bisect;
+    s->toc(st);
+    BisectState h{};
+    CUDA_TRY(cudaMemcpyAsync(&h, s->bstate.p, sizeof h, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    s->collect();
+    s->stats.bisect_steps = h.iter;
+    if (h.status & DEV_NONFINITE) return fail(ELSES_ERR_NONFINITE, "non-finite poles");
+    if (h.status & DEV_NO_BRACKET)
+        return fail(ELSES_ERR_NO_BRACKET, "N(lo)=%.17g N(hi)=%.17g do not bracket N_e=%.17g", h.n_lo, h.n_hi,
+                    s->p.n_electrons);
+    s->mu = h.mu;
+    s->have_mu = true;
+    if (mu_host) *mu_host = h.mu;
+    if (n_at_mu_host) {
+        s->tic(T_BISECT, st);
+        scalars_at(r, h.mu, st);
+        s->toc(st);
+        s->stats.launches++;
+        CUDA_TRY(cudaMemcpyAsync(&h, s->bstate.p, sizeof h, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        s->collect();
+        *n_at_mu_host = h.n_at;
+    }
+    return ELSES_OK;
+}
+
+static int density_impl(elses_system s, double mu, double* rho, double* rhoE, cudaStream_t st) {
+    if (s->atoms_done != s->n) return fail(ELSES_ERR_STATE, "density_matrix needs every column");
+    TRY(clear_status(s, st));
+    if (!s->p.two_pass) {
+        DensityArgs d = density_args(s, mu, rho, rhoE);
+        d.atom_begin = 0;
+        d.atom_end = s->n;
+        d.V = s->V.p;
+        d.v_col0 = 0;
+        d.UP = s->UP.p;
+        d.up_block0 = 0;
+        s->tic(T_DENSITY, st);
+        density_columns(d, st);
+        s->toc(st);
+        s->stats.launches++;
+    } else {
+        // second calculation of G (Eq. 3): recompute every batch, then its rho columns
+        for (int b = 0; b < s->n; b += s->batch_atoms) {
+            const int e = std::min(s->n, b + s->batch_atoms);
+            double* V;
+            double* UP;
+            int v0, u0;
+            TRY(run_batch(s, b, e, false, &V, &v0, &UP, &u0, st));
+            DensityArgs d = density_args(s, mu, rho, rhoE);
+            d.atom_begin = b;
+            d.atom_end = e;
+            d.V = V;
+            d.v_col0 = v0;
+            d.UP = UP;
+            d.up_block0 = u0;
+            s->tic(T_DENSITY, st);
+            density_columns(d, st);
+            s->toc(st);
+            s->stats.launches++;
+        }
+    }
+    return 0;
+}
+
+int elses_density_matrix(elses_system s, double mu, double* rho_dev, double* rhoE_dev, void* stream) {
+    TRY(check_built(s));
+    if (!rho_dev) return fail(ELSES_ERR_ARG, "null rho");
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(density_impl(s, mu, rho_dev, rhoE_dev, st));
+    return check_status(s, st);
+}
+
+int elses_energies(elses_system s, double mu, double* n_host, double* e_band_host, double* omega_host,
+                   double* f_free_host, void* stream) {
+    TRY(check_built(s));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (s->atoms_done != s->n) return fail(ELSES_ERR_STATE, "energies need every column");
+    ReduceArgs r = reduce_args(s);
+    s->tic(T_BISECT, st);
+    scalars_at(r, mu, st);
+    s->toc(st);
+    s->stats.launches++;
+    BisectState h{};
+    CUDA_TRY(cudaMemcpyAsync(&h, s->bstate.p, sizeof h, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    s->collect();
+    if (n_host) *n_host = h.n_at;
+    if (e_band_host) *e_band_host = h.e_band;
+    if (omega_host) *omega_host = h.omega;
+    if (f_free_host) *f_free_host = h.omega + mu * s->p.n_electrons;
+    return ELSES_OK;
+}
+
+int elses_energy_force(elses_system s, double* mu_host, double* e_band_host, double* f_free_host,
+                       double* forces_dev, void* stream) {
+    TRY(check_built(s));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (forces_dev && s->user_hs) return fail(ELSES_ERR_STATE, "forces need the Slater-Koster H, S");
+    int warn = elses_green_columns(s, 0, s->M, 0, nullptr, nullptr, nullptr, stream);
+    if (warn < 0) return warn;
+    double mu = 0.0;
+    TRY(elses_find_mu(s, &mu, nullptr, stream));
+    TRY(density_impl(s, mu, s->rho.p, s->rhoE.p, st));
+    ReduceArgs r = reduce_args(s);
+    s->tic(T_BISECT, st);
+    scalars_at(r, mu, st);
+    s->toc(st);
+    s->stats.launches++;
+    if (forces_dev) {
+        s->tic(T_FORCE, st);
+        forces(s->pos.p, s->n, s->box, s->skd, s->row_ptr.p, s->col_idx.p, s->row_of.p, s->tmap.p, s->nnzb,
+               s->rho.p, s->rhoE.p, s->gblock.p, forces_dev, st);
+        s->toc(st);
+        s->stats.launches += 2;
+    }
+    BisectState h{};
+    CUDA_TRY(cudaMemcpyAsync(&h, s->bstate.p, sizeof h, cudaMemcpyDeviceToHost, st));
+    int rc = check_status(s, st);
+    if (rc < 0) return rc;
+    if (mu_host) *mu_host = mu;
+    if (e_band_host) *e_band_host = h.e_band;
+    if (f_free_host) *f_free_host = h.omega + mu * s->p.n_electrons;
+    return warn > 0 ? warn : rc;
+}
+
+int elses_get_pattern(elses_system s, int* nnzb_host, int* row_ptr_dev, int* col_idx_dev, void* stream) {
+    TRY(check_built(s));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (nnzb_host) *nnzb_host = s->nnzb;
+    if (row_ptr_dev)
+        CUDA_TRY(cudaMemcpyAsync(row_ptr_dev, s->row_ptr.p, sizeof(int) * (s->n + 1), cudaMemcpyDeviceToDevice, st));
+    if (col_idx_dev)
+        CUDA_TRY(cudaMemcpyAsync(col_idx_dev, s->col_idx.p, sizeof(int) * s->nnzb, cudaMemcpyDeviceToDevice, st));
+    return ELSES_OK;
+}
+
+int elses_get_hs(elses_system s, double* H_dev, double* S_dev, void* stream) {
+    TRY(check_built(s));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (H_dev) CUDA_TRY(cudaMemcpyAsync(H_dev, s->H.p, sizeof(double) * 16 * s->nnzb, cudaMemcpyDeviceToDevice, st));
+    if (S_dev) CUDA_TRY(cudaMemcpyAsync(S_dev, s->S.p, sizeof(double) * 16 * s->nnzb, cudaMemcpyDeviceToDevice, st));
+    return ELSES_OK;
+}
+
+int elses_get_clusters(elses_system s, long long* total_host, int* max_cluster_host, int* cl_ptr_dev,
+                       int* cl_idx_dev, void* stream) {
+    TRY(check_built(s));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (total_host) *total_host = s->cl_total;
+    if (max_cluster_host) *max_cluster_host = s->max_cl;
+    if (s->p.r_cluster > 0) {
+        if (cl_ptr_dev)
+            CUDA_TRY(cudaMemcpyAsync(cl_ptr_dev, s->cl_ptr.p, sizeof(int) * (s->n + 1), cudaMemcpyDeviceToDevice, st));
+        if (cl_idx_dev)
+            CUDA_TRY(cudaMemcpyAsync(cl_idx_dev, s->cl_idx.p, sizeof(int) * s->cl_total, cudaMemcpyDeviceToDevice, st));
+    }
+    return ELSES_OK;
+}
+
+int elses_get_spectra(elses_system s, int* nu_max_host, double* eps_dev, double* c_dev, double* d_dev,
+                      double* g_dev, int* nu_eff_dev, void* stream) {
+    TRY(check_built(s));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double) * (size_t)s->M * s->nu_max;
+    if (nu_max_host) *nu_max_host = s->nu_max;
+    if (eps_dev) CUDA_TRY(cudaMemcpyAsync(eps_dev, s->eps.p, bytes, cudaMemcpyDeviceToDevice, st));
+    if (c_dev) CUDA_TRY(cudaMemcpyAsync(c_dev, s->cc.p, bytes, cudaMemcpyDeviceToDevice, st));
+    if (d_dev) CUDA_TRY(cudaMemcpyAsync(d_dev, s->dd.p, bytes, cudaMemcpyDeviceToDevice, st));
+    if (g_dev) CUDA_TRY(cudaMemcpyAsync(g_dev, s->gg.p, bytes, cudaMemcpyDeviceToDevice, st));
+    if (nu_eff_dev) CUDA_TRY(cudaMemcpyAsync(nu_eff_dev, s->nu_eff.p, sizeof(int) * s->M, cudaMemcpyDeviceToDevice, st));
+    return ELSES_OK;
+}
+
+int elses_get_stats(elses_system s, elses_stats* out) {
+    if (!s || !out) return fail(ELSES_ERR_ARG, "null argument");
+    *out = s->stats;
+    return ELSES_OK;
+}
+
+int elses_reset_stats(elses_system s) {
+    if (!s) return fail(ELSES_ERR_ARG, "null system");
+    s->collect();
+    s->stats = elses_stats{};
+    return ELSES_OK;
+}
+
+int elses_probe_fp64(double* gflops_host, void* stream) {
+    if (!gflops_host) return fail(ELSES_ERR_ARG, "null output");
+    double g = 0.0;
+    const int rc = probe_fp64(&g, (cudaStream_t)stream);
+    if (rc != 0) return fail(ELSES_ERR_CUDA, "fp64 probe failed: %s", cudaGetErrorString((cudaError_t)rc));
+    *gflops_host = g;
+    return ELSES_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,294 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle, on seeded synthetic systems.
+
+Gates: |delta rho_ij| <= 1e-10 and |delta E|/atom <= 1e-9 eV against the same-algorithm oracle;
+exact diagonalisation at full subspace to 1e-8; finite-difference forces to 1e-5 relative;
+bit-exact neighbour, cluster and pattern lists. mu is not unique when it falls in a gap (N(mu)
+is flat there), so the GPU's mu is checked for validity (the oracle's N at that mu is N_e) and
+rho is compared with the oracle evaluated at the GPU's mu.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as wl
+from oracle import exact, hamiltonian, physics, pipeline, structure
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eg():
+    return gu.library()
+
+
+# ----------------------------------------------------------------------------- 64-atom diamond
+@pytest.fixture(scope="module")
+def d64(eg):
+    w = wl.make("diamond_64")
+    sysg = eg.system_for(w)
+    mu, e_band, f_free, F = sysg.energy_force()
+    rho, rhoE = sysg.density_matrix(mu)
+    rp, ci = sysg.pattern()
+    out = dict(w=w, sys=sysg, mu=mu, e_band=e_band, f_free=f_free, F=gu.to_np(F), rho=gu.to_np(rho),
+               rhoE=gu.to_np(rhoE), rp=gu.to_np(rp), ci=gu.to_np(ci), spectra={k: gu.to_np(v) for k, v in sysg.spectra().items()})
+    out["oracle_cols"] = pipeline.columns(w)
+    return out
+
+
+def test_pattern_is_bit_exact(d64):
+    rp, ci = structure.neighbor_csr(d64["w"].pos, d64["w"].box, d64["w"].sk.r_cut)
+    assert np.array_equal(rp, d64["rp"]) and np.array_equal(ci, d64["ci"])
+
+
+def test_hs_blocks_match(d64):
+    H, S = d64["sys"].hs()
+    Ho, So = hamiltonian.bsr_values(d64["w"].pos, d64["w"].box, d64["w"].sk, d64["rp"], d64["ci"])
+    assert np.abs(gu.to_np(H) - Ho).max() < 1e-13
+    assert np.abs(gu.to_np(S) - So).max() < 1e-14
+
+
+def test_mu_is_a_valid_root(d64):
+    w = d64["w"]
+    N = pipeline.scalars(d64["oracle_cols"], d64["mu"], w.kT, w.n_electrons)["N"]
+    assert abs(N - w.n_electrons) < 1e-8
+
+
+def test_rho_all_columns(d64):
+    w = d64["w"]
+    cols = d64["oracle_cols"]
+    _, _, rho_o, rhoE_o = pipeline.assemble(w, cols, d64["mu"])
+    assert np.abs(d64["rho"] - rho_o).max() <= gu.RHO_TOL
+    assert np.abs(d64["rhoE"] - rhoE_o).max() <= 10 * gu.RHO_TOL
+
+
+def test_energies(d64):
+    w = d64["w"]
+    sc = pipeline.scalars(d64["oracle_cols"], d64["mu"], w.kT, w.n_electrons)
+    assert abs(d64["e_band"] - sc["E_band"]) / w.n_atoms <= gu.E_TOL_PER_ATOM
+    assert abs(d64["f_free"] - sc["F_free"]) / w.n_atoms <= gu.E_TOL_PER_ATOM
+    e = d64["sys"].energies(d64["mu"])
+    assert abs(e["N"] - w.n_electrons) < 1e-8
+
+
+def test_spectra_invariants(d64):
+    sp = d64["spectra"]
+    for col in d64["oracle_cols"]:
+        j = col.j
+        nu = int(sp["nu_eff"][j])
+        assert nu == col.nu_eff
+        assert np.abs(sp["eps"][j, :nu] - col.eps).max() < 1e-9
+        mg = gu.spectral_moments(sp["eps"][j], sp["c"][j] * sp["d"][j], nu)
+        mo = gu.spectral_moments(col.eps, col.c * col.d, nu)
+        assert np.abs(mg - mo).max() <= 1e-9 * np.maximum(1.0, np.abs(mo)).max()
+        mg = gu.spectral_moments(sp["eps"][j], sp["c"][j] * sp["g"][j], nu)
+        mo = gu.spectral_moments(col.eps, col.c * col.g, nu)
+        assert np.abs(mg - mo).max() <= 1e-9 * np.maximum(1.0, np.abs(mo)).max()
+
+
+def test_forces_match_oracle_and_sum_to_zero(d64):
+    w = d64["w"]
+    _, _, rho_o, rhoE_o = pipeline.assemble(w, d64["oracle_cols"], d64["mu"])
+    F_o = physics.forces(w.pos, w.box, w.sk, d64["rp"], d64["ci"], rho_o, rhoE_o)
+    assert np.abs(d64["F"] - F_o).max() <= 1e-8 * max(1.0, np.abs(F_o).max())
+    assert np.abs(d64["F"].sum(axis=0)).max() < 1e-9
+
+
+def test_green_function_on_pattern(eg, d64):
+    w = d64["w"]
+    zs = [0.5 + 0.3j, -6.0 + 0.05j]
+    G = gu.to_np(d64["sys"].green_columns(z=zs))
+    rp, ci = d64["rp"], d64["ci"]
+    for col in d64["oracle_cols"][::37]:
+        Z = col.UP @ col.V
+        J, alpha = divmod(col.j, 4)
+        for iz, z in enumerate(zs):
+            g_o = (Z @ (col.c / (z - col.eps))).reshape(-1, 4)
+            for p, I in enumerate(col.pattern):
+                row = ci[rp[I]:rp[I + 1]]
+                e = rp[I] + int(np.searchsorted(row, J))
+                assert np.abs(G[e, :, alpha, iz] - g_o[p]).max() <= 1e-10 * max(1.0, np.abs(g_o).max())
+
+
+def test_deterministic_repeat(eg, d64):
+    sysg = d64["sys"]
+    mu, e_band, f_free, F = sysg.energy_force()
+    assert mu == d64["mu"] and e_band == d64["e_band"] and f_free == d64["f_free"]
+    assert np.array_equal(gu.to_np(F), d64["F"])
+
+
+def test_two_pass_equals_stored(eg, d64):
+    """Workflow invariance (the memory-saving workflow does not change the results, Eq. 3)."""
+    w = d64["w"]
+    s2 = eg.system_for(w, two_pass=True)
+    mu, e_band, f_free, F = s2.energy_force()
+    rho, rhoE = s2.density_matrix(mu)
+    assert mu == d64["mu"] and e_band == d64["e_band"]
+    assert np.array_equal(gu.to_np(rho), d64["rho"]) and np.array_equal(gu.to_np(F), d64["F"])
+
+
+def test_batched_schedule_equals_plain(eg, d64):
+    s2 = eg.system_for(d64["w"], schedule=1)
+    mu, e_band, _, F = s2.energy_force()
+    assert mu == d64["mu"] and e_band == d64["e_band"] and np.array_equal(gu.to_np(F), d64["F"])
+
+
+# ----------------------------------------------------------------------------- full subspace
+@pytest.fixture(scope="module")
+def full(eg):
+    w = gu.fragment(16)                 # M = 64 = nu: the Krylov space is the whole space
+    sysg = eg.system_for(w)
+    sysg.green_columns()
+    ref = pipeline.dense_reference(w)
+    return w, sysg, ref
+
+
+def test_full_subspace_equals_exact_diagonalisation(full):
+    w, sysg, ref = full
+    rho, rhoE = sysg.density_matrix(ref["mu"])
+    rp, ci = sysg.pattern()
+    rp, ci = gu.to_np(rp), gu.to_np(ci)
+    rho_d = hamiltonian.bsr_to_dense(rp, ci, gu.to_np(rho))
+    mask = hamiltonian.bsr_to_dense(rp, ci, np.ones((len(ci), 4, 4))) > 0
+    assert np.abs(rho_d - ref["rho"])[mask].max() < 1e-8
+    rhoE_d = hamiltonian.bsr_to_dense(rp, ci, gu.to_np(rhoE))
+    assert np.abs(rhoE_d - ref["rhoE"])[mask].max() < 1e-8
+    e = sysg.energies(ref["mu"])
+    assert abs(e["E_band"] - ref["E_band"]) / w.n_atoms < 1e-9
+
+
+def test_full_subspace_green_function_equals_dense_solve(full):
+    w, sysg, ref = full
+    zs = [0.3 + 0.5j, -7.0 + 0.05j]
+    G = gu.to_np(sysg.green_columns(z=zs))
+    rp, ci = (gu.to_np(t) for t in sysg.pattern())
+    for j in (0, 13, 42, 63):
+        J, alpha = divmod(j, 4)
+        for iz, z in enumerate(zs):
+            g_ref = exact.green_column(ref["H"], ref["S"], z, j)
+            for I in range(w.n_atoms):
+                row = ci[rp[I]:rp[I + 1]]
+                k = np.searchsorted(row, J)
+                if k < len(row) and row[k] == J:
+                    e = rp[I] + k
+                    assert np.abs(G[e, :, alpha, iz] - g_ref[4 * I:4 * I + 4]).max() <= 1e-10 * np.abs(g_ref).max()
+
+
+def test_full_subspace_forces_match_finite_differences(eg, full):
+    """HF forces are the exact gradient at full subspace: compare with central differences of
+    Omega at fixed mu (h = 1e-4 A), each side evaluated by the GPU path."""
+    w = full[0]
+    s = eg.system_for(w)
+    mu, _, _, F = s.energy_force()
+    F = gu.to_np(F)
+    h = 1e-4
+    scale = max(1.0, np.abs(F).max())
+    for (K, m) in ((0, 0), (5, 1), (11, 2)):
+        om = []
+        for sgn in (1, -1):
+            pos = w.pos.copy()
+            pos[K, m] += sgn * h
+            t = eg.System(torch.tensor(pos, device="cuda"), w.box, w.sk, w.r_cluster, w.nu, w.kT,
+                          w.n_electrons)
+            t.green_columns()
+            om.append(t.energies(mu)["Omega"])
+            t.close()
+        fd = -(om[0] - om[1]) / (2 * h)
+        assert abs(fd - F[K, m]) <= 1e-5 * scale
+    assert np.abs(F.sum(axis=0)).max() < 1e-9
+
+
+# ----------------------------------------------------------------------------- larger systems
+def _sampled_parity(eg, w, n_cols, **kw):
+    sysg = eg.system_for(w, **kw)
+    mu, e_band, f_free, F = sysg.energy_force()
+    rho, rhoE = sysg.density_matrix(mu)
+    rp, ci = (gu.to_np(t) for t in sysg.pattern())
+    cols = wl.sample_columns(4 * w.n_atoms, n_cols)
+    oc = gu.oracle_rho_columns(w, cols, mu)
+    dr, dE = gu.max_rho_diff(gu.to_np(rho), gu.to_np(rhoE), rp, ci, oc)
+    sp = {k: gu.to_np(v) for k, v in sysg.spectra().items()}
+    for j, (_, _, _, col) in oc.items():
+        assert int(sp["nu_eff"][j]) == col.nu_eff
+        assert np.abs(sp["eps"][j, :col.nu_eff] - col.eps).max() < 1e-9
+    # per-column band energy and electron count at the GPU's mu
+    f2 = lambda e: 2.0 * physics.fermi(e, mu, w.kT)
+    for j, (_, _, _, col) in list(oc.items())[:16]:
+        nu = col.nu_eff
+        Eg = np.sum(f2(sp["eps"][j, :nu]) * sp["g"][j, :nu] * sp["c"][j, :nu])
+        Eo = np.sum(f2(col.eps) * col.g * col.c)
+        assert abs(Eg - Eo) <= 1e-9
+    return dict(sys=sysg, mu=mu, dr=dr, dE=dE, F=gu.to_np(F), rp=rp, ci=ci)
+
+
+def test_diamond4096_sampled_columns(eg):
+    w = wl.make("diamond_4096")
+    r = _sampled_parity(eg, w, 48)
+    assert r["dr"] <= gu.RHO_TOL and r["dE"] <= 10 * gu.RHO_TOL
+    rp, ci = structure.neighbor_csr(w.pos, w.box, w.sk.r_cut)
+    assert np.array_equal(rp, r["rp"]) and np.array_equal(ci, r["ci"])
+    cp, cidx, mx = r["sys"].clusters()
+    cp, cidx = gu.to_np(cp), gu.to_np(cidx)
+    for J in wl.sample_columns(w.n_atoms, 64):
+        assert np.array_equal(cidx[cp[J]:cp[J + 1]], structure.cluster(w.pos, w.box, J, w.r_cluster))
+    assert abs(r["F"].sum(axis=0)).max() < 1e-8
+
+
+def test_diamond4096_batched_equals_plain(eg):
+    w = wl.make("diamond_4096")
+    a = eg.system_for(w, schedule=0)
+    b = eg.system_for(w, schedule=1)
+    ra, rb = a.energy_force(), b.energy_force()
+    assert ra[0] == rb[0] and ra[1] == rb[1] and np.array_equal(gu.to_np(ra[3]), gu.to_np(rb[3]))
+
+
+def test_composite_sampled_columns(eg):
+    w = wl.make("composite_32768")
+    r = _sampled_parity(eg, w, 32, schedule=1)
+    assert r["dr"] <= gu.RHO_TOL and r["dE"] <= 10 * gu.RHO_TOL
+    nu_eff = gu.to_np(r["sys"].spectra()["nu_eff"])
+    assert set(np.unique(nu_eff)) <= {20, 30, 40}
+
+
+@pytest.mark.slow
+def test_amorphous_1m_sampled_columns(eg):
+    w = wl.make("amorphous_1m")
+    r = _sampled_parity(eg, w, 16, schedule=1)
+    assert r["dr"] <= gu.RHO_TOL and r["dE"] <= 10 * gu.RHO_TOL
+    assert abs(r["F"].sum(axis=0)).max() < 1e-6
+
+
+# ----------------------------------------------------------------------------- edge cases
+def test_dimer_breakdown_warning(eg):
+    pos, box = wl.dimer(wl.sk_params().r0)
+    s = eg.System(torch.tensor(pos, device="cuda"), box, wl.sk_params(), 0.0, 8, 0.1, 8.0)
+    assert s.green_columns() == eg.WARN_BREAKDOWN
+    nu = gu.to_np(s.spectra()["nu_eff"])
+    assert nu[1] == 2 and nu[2] == 2                       # px, py: invariant pi pairs
+
+
+def test_errors_are_reported(eg):
+    w = wl.make("diamond_64")
+    pos = torch.tensor(w.pos, device="cuda")
+    with pytest.raises(eg.ElsesError) as e:
+        eg.System(pos, [4.0, 4.0, 4.0], w.sk, 0.0, 30, 0.1, w.n_electrons)
+    assert e.value.code == -1
+    with pytest.raises(eg.ElsesError) as e:
+        eg.System(pos, w.box, w.sk, 0.0, 65, 0.1, w.n_electrons)
+    assert e.value.code == -1
+    bad = pos.clone()
+    bad[3, 1] = float("nan")
+    with pytest.raises(eg.ElsesError) as e:
+        eg.System(bad, w.box, w.sk, 0.0, 30, 0.1, w.n_electrons)
+    assert e.value.code == -3
+    with pytest.raises(eg.ElsesError) as e:
+        eg.System(pos, w.box, w.sk, 0.0, 30, 0.1, w.n_electrons, max_neighbors=4)
+    assert e.value.code == -10
+    s = eg.System(pos, w.box, w.sk, 0.0, 30, 0.1, 10.0 * w.n_electrons)
+    with pytest.raises(eg.ElsesError) as e:
+        s.energy_force()
+    assert e.value.code == -4
+    s2 = eg.System(pos, w.box, w.sk, 0.0, 30, 0.1, w.n_electrons)
+    with pytest.raises(eg.ElsesError) as e:
+        s2.find_mu()
+    assert e.value.code == -9
