@@ -68,6 +68,18 @@ def spectral_moments(eps, w, nu, m_max=3):
     return np.array([np.sum(w[:nu] * e ** m) for m in range(m_max + 1)])
 
 
+def significant_poles_match(eps_g, c_g, eps_o, c_o, tol=1e-9, cmin=1e-6):
+    """Poles with a non-negligible residue weight |c_k| > cmin must agree. Poles whose weight is
+    at rounding level (e.g. from symmetry-decoupled directions of a perfect lattice, where the
+    Krylov space picks up rounding noise) do not enter G, rho or E and are not unique."""
+    sig = np.abs(c_o) > cmin
+    for e, c in zip(eps_o[sig], c_o[sig]):
+        k = int(np.argmin(np.abs(eps_g - e)))
+        if abs(eps_g[k] - e) > tol or abs(abs(c_g[k]) - abs(c)) > 1e-7 * max(1.0, abs(c)):
+            return False
+    return int(np.sum(np.abs(c_g) > 10 * cmin)) <= int(np.sum(sig))
+
+
 def oracle_electron_count(workload, cols_all, mu):
     return pipeline.scalars(cols_all, mu, workload.kT, workload.n_electrons)["N"]
 

@@ -343,3 +343,26 @@ def test_planted_single_gram_schmidt_pass_changes_nothing_visible_but_orthogonal
     """The S-orthonormality of the basis (what CGS2 maintains) is checked directly."""
     col = pipeline.solve_column(diamond64.pos, diamond64.box, diamond64.sk, 0.0, 30, 9)
     assert np.abs(col.Sp - np.eye(col.nu_eff)).max() < 1e-12
+
+
+def test_composite_columns_are_well_conditioned():
+    """The per-column result must be determined by the inputs to far better than the 1e-10 rho
+    gate: a 1e-15 relative symmetric perturbation of H_C moves rho columns of the (thermalised)
+    sp2-sp3 composite by < 1e-10. (Perfect lattices fail this: decoupled symmetry sectors let
+    rounding seed new Krylov directions.)"""
+    w = wl.make("composite_32768")
+    rng = np.random.default_rng(5)
+    for j in wl.sample_columns(4 * w.n_atoms, 6):
+        J, alpha = divmod(int(j), 4)
+        atoms = structure.cluster(w.pos, w.box, J, w.r_cluster)
+        nu = pipeline.nu_for(w, len(atoms))
+        Hc, Sc = hamiltonian.cluster_matrices(w.pos, w.box, w.sk, atoms)
+        jl = 4 * int(np.searchsorted(atoms, J)) + alpha
+        P = rng.normal(size=Hc.shape)
+        rhos = []
+        for H in (Hc, Hc + 1e-15 * np.abs(Hc).max() * 0.5 * (P + P.T)):
+            kc = krylov.arnoldi_column(H, Sc, jl, nu)
+            e, V = krylov.projected_eig(kc.Hp, kc.Sp)
+            c = V.T @ kc.U[jl, :]
+            rhos.append((kc.U @ V) @ (2 * physics.fermi(e, -1.0, 0.1) * c))
+        assert np.abs(rhos[0] - rhos[1]).max() < 1e-10

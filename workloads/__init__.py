@@ -154,13 +154,17 @@ def _grain_sites(center, radius, rot, box):
     return _wrap(local @ rot.T + center, box)
 
 
-def composite(n_atoms: int = 32768, seed: int = GEOMETRY_SEED, gap: float = 1.1):
+def composite(n_atoms: int = 32768, seed: int = GEOMETRY_SEED, gap: float = 1.1,
+              sigma: float = 0.05):
     """sp2-sp3 nano-composite carbon: seeded diamond grains (radius 8-15 A) in AB graphite.
 
     Graphite atoms within R + gap of a grain centre are replaced by the grain. The box is the
     smallest near-cubic graphite supercell (candidates in order of volume) for which the composite holds between
     n_atoms and 1.02*n_atoms atoms; the excess is then removed by deleting seeded-random graphite
-    atoms (vacancies). Returns (pos, box, is_grain bool[N]).
+    atoms (vacancies). Every atom is then displaced by seeded Gaussian noise of width `sigma`
+    (a finite-temperature snapshot; perfect lattices leave whole symmetry sectors of a cluster
+    decoupled, and the Krylov space of a column then picks up directions seeded by rounding).
+    Returns (pos, box, is_grain bool[N]).
     """
     a = GRAPHITE_CC * math.sqrt(3.0)
     lat = np.array([a, a * math.sqrt(3.0), 2.0 * GRAPHITE_C2])
@@ -214,6 +218,8 @@ def composite(n_atoms: int = 32768, seed: int = GEOMETRY_SEED, gap: float = 1.1)
             pos = np.concatenate([graphite_left[mask], grain_pos])
             is_grain = np.concatenate([np.zeros(int(mask.sum()), bool),
                                        np.ones(len(grain_pos), bool)])
+            if sigma > 0.0:
+                pos = _wrap(pos + np.random.default_rng(seed + 1).normal(0.0, sigma, pos.shape), box)
             return pos, box, is_grain
     raise RuntimeError("composite: no box size in the search range hit the atom count")
 
