@@ -82,8 +82,13 @@ struct EigArgs {
     const double* surow;
     const double* hurow;
     const int* nu_eff;      // [M] global
-    double* work;           // [elem][ncols_pad]
-    int ncols_pad;
+    double* tri;            // [col][5 nu_max]: tridiagonal D, E and the three vectors
+    double* fac;            // [col][2 nu_max^2]: Householder reflectors + tau, Cholesky factor
+    double* rot_c;          // [col][rot_cap]: recorded Givens rotations
+    double* rot_s;
+    unsigned char* rot_k;
+    int* rot_n;             // [col]
+    int* perm;              // [col][nu_max]: ascending order of the eigenvalues
     double* eps;            // [M][nu_max] global
     double* c;
     double* d;
@@ -91,7 +96,9 @@ struct EigArgs {
     double* V;              // [batch col][nu_max*nu_max] (row n = Krylov index, col k = eigen index)
     int* status;
 };
-size_t eig_work_doubles(int nu_max);
+__host__ __device__ size_t eig_tri_doubles(int nm);
+__host__ __device__ size_t eig_fac_doubles(int nm);
+__host__ __device__ size_t eig_rot_cap(int nm);
 void projected_eig(const EigArgs& a, cudaStream_t st);
 
 // ---------------------------------------------------------------- a7, a9 (reduce.cu)

@@ -47,8 +47,10 @@ __device__ __forceinline__ int nu_for(const KrylovArgs& a, int n_at) {
     return a.nu_default;
 }
 
-__device__ __forceinline__ double dot4(const double2 a0, const double2 a1, const double2 b0, const double2 b1) {
-    return fma(a0.x, b0.x, fma(a0.y, b0.y, fma(a1.x, b1.x, a1.y * b1.y)));
+// acc + a . b over 4 orbitals: four FMAs straight into the accumulator.
+__device__ __forceinline__ double fma4(const double2 a0, const double2 a1, const double2 b0, const double2 b1,
+                                       double acc) {
+    return fma(a1.y, b1.y, fma(a1.x, b1.x, fma(a0.y, b0.y, fma(a0.x, b0.x, acc))));
 }
 
 // y = A x on the cluster (lane-owned rows; x gathered from shared memory).
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
                         double2 hu0, hu1, su0, su1;
                         ld4(B + 4 * p, hu0, hu1);
                         ld4(C + 4 * p, su0, su1);
-                        if (k0 == 0) acc[30] += dot4(hu0, hu1, hu0, hu1);
+                        if (k0 == 0) acc[30] = fma4(hu0, hu1, hu0, hu1, acc[30]);
 #pragma unroll
                         for (int kk = 0; kk < 10; ++kk) {
                             const int k = k0 + kk;
@@ -264,9 +266,9 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
                                 double2 u0, u1, v0, v1;
                                 ld4(Uw + 4 * ((size_t)k * NP + p), u0, u1);
                                 ld4(SUw + 4 * ((size_t)k * NP + p), v0, v1);
-                                acc[kk] += dot4(u0, u1, hu0, hu1);
-                                acc[10 + kk] += dot4(u0, u1, su0, su1);
-                                acc[20 + kk] += dot4(v0, v1, hu0, hu1);
+                                acc[kk] = fma4(u0, u1, hu0, hu1, acc[kk]);
+                                acc[10 + kk] = fma4(u0, u1, su0, su1, acc[10 + kk]);
+                                acc[20 + kk] = fma4(v0, v1, hu0, hu1, acc[20 + kk]);
                             }
                         }
                     }
@@ -303,7 +305,7 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
                         if (kk <= n) {
                             double2 v0, v1;
                             ld4(SUw + 4 * ((size_t)kk * NP + p), v0, v1);
-                            acc2[kk] += dot4(v0, v1, w0, w1);
+                            acc2[kk] = fma4(v0, v1, w0, w1, acc2[kk]);
                         }
                     }
                 }
@@ -322,7 +324,7 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
                             if (32 + kk <= n) {
                                 double2 v0, v1;
                                 ld4(SUw + 4 * ((size_t)(32 + kk) * NP + p), v0, v1);
-                                acc2[kk] += dot4(v0, v1, w0, w1);
+                                acc2[kk] = fma4(v0, v1, w0, w1, acc2[kk]);
                             }
                         }
                     }
@@ -353,7 +355,7 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
                     double2 w0, w1, v0, v1;
                     ld4(B + 4 * p, w0, w1);
                     ld4(C + 4 * p, v0, v1);
-                    part += dot4(w0, w1, v0, v1);
+                    part = fma4(w0, w1, v0, v1, part);
                 }
                 const double beta2 = warp_sum(part);
                 if (!(beta2 == beta2)) {   // NaN

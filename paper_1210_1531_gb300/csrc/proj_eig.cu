@@ -6,212 +6,349 @@
 // The Green's-function column then has poles e_k and residues Z_ik c_k with Z = U V and
 // c = V^T U^T e_j; kept per column are (e, c, d = V^T (SU)_j, g = V^T (HU)_j) and V.
 //
-// GB300 form: one thread per column (the problem is small, sequential and FP64; spreading it
-// over a warp would repeat its scalar recurrences on every lane of the FP64 pipe). Each
-// thread's matrices live in global memory in [element][column] order, so the 32 threads of a
-// warp touch consecutive addresses. Symmetric eigensolver: Householder reduction to
-// tridiagonal form, then implicit-shift QR sweeps (Wilkinson shift, Givens bulge chase) with
-// the rotations accumulated into Q; eigenvalues sorted ascending.
+// GB300 form. On this part the FP64 pipe charges a whole warp instruction whatever the number
+// of active lanes, so every FP64 instruction must carry work on all lanes:
+//   k_eig_reduce  one warp per column, matrices in shared memory: Cholesky, the reduction
+//                 A = L^-1 H' L^-T and the Householder reduction of A to tridiagonal form T
+//                 (lanes over rows / columns); the three vectors L^-1 (U, SU, HU)_j are taken
+//                 to the tridiagonal basis.
+//   k_eig_chase   one thread per column: implicit-shift QR sweeps on T (Wilkinson shift, Givens
+//                 bulge chase) -- the sequential part -- rotating the three vectors along, so
+//                 that they become c, d, g; the rotations are recorded.
+//   k_eig_vectors one warp per column: Q_H from the Householder reflectors, the recorded
+//                 rotations applied to its columns (lanes over rows), V = L^-T Q.
 #include "internal.h"
 
 namespace elses {
 
-size_t eig_work_doubles(int nu_max) { return 3 * (size_t)nu_max * nu_max + 6 * (size_t)nu_max; }
+__host__ __device__ size_t eig_tri_doubles(int nm) { return 5 * (size_t)nm; }        // D, E, yc, yd, yg
+__host__ __device__ size_t eig_fac_doubles(int nm) { return 2 * (size_t)nm * nm; }   // reflectors + tau, L
+__host__ __device__ size_t eig_rot_cap(int nm) { return 2 * (size_t)nm * nm + 64; }  // Givens rotations per column
 
-__global__ void k_proj_eig(const EigArgs a) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+// packed upper storage: element (i, k), i <= k, at i + k (k + 1) / 2
+__device__ __forceinline__ double packed(const double* P, int i, int k) {
+    return i <= k ? P[i + k * (k + 1) / 2] : P[k + i * (i + 1) / 2];
+}
+
+// ----------------------------------------------------------------------------- k_eig_reduce
+__global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
+    extern __shared__ __align__(16) double sm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int c = blockIdx.x * (blockDim.x >> 5) + wib;
     if (c >= a.ncols) return;
+    const int nm = a.nu_max, ld = nm + 1;
+    double* A = sm + (size_t)wib * (2 * nm * ld + 4 * nm);
+    double* L = A + nm * ld;
+    double* inv = L + nm * ld;     // 1 / L_ii
+    double* P = inv + nm;          // Householder work vector
+    double* Y = P + nm;            // 2 * nm: scratch for the three vectors (nm each, 3 used: Y, Y+nm... see below)
+    double* yv = a.tri + (size_t)c * eig_tri_doubles(nm);   // D, E, yc, yd, yg (global)
     const int j = a.col0 + c;
     const int nu = a.nu_eff[j];
-    const int nm = a.nu_max;
-    const size_t st = a.ncols_pad;
-    double* W = a.work + c;
-    const size_t oA = 0, oQ = (size_t)nm * nm, oL = 2 * (size_t)nm * nm, oD = 3 * (size_t)nm * nm;
-    const size_t oE = oD + nm, oT = oE + nm, oP = oT + nm, oI = oP + nm, oX = oI + nm;
-#define AM(i, k) W[(oA + (size_t)(i) * nm + (k)) * st]
-#define QM(i, k) W[(oQ + (size_t)(i) * nm + (k)) * st]
-#define LM(i, k) W[(oL + (size_t)(i) * nm + (k)) * st]
-#define DV(i) W[(oD + (i)) * st]
-#define EV(i) W[(oE + (i)) * st]
-#define TV(i) W[(oT + (i)) * st]
-#define PV(i) W[(oP + (i)) * st]
-#define IV(i) W[(oI + (i)) * st]
-#define XV(i) W[(oX + (i)) * st]
     const int PK = nm * (nm + 1) / 2;
     const double* Hp = a.Hp + (size_t)c * PK;
     const double* Sp = a.Sp + (size_t)c * PK;
-    // packed upper storage: element (i, k), i <= k, at i + k (k + 1) / 2
-#define PACK(P, i, k) ((i) <= (k) ? (P)[(i) + (k) * ((k) + 1) / 2] : (P)[(k) + (i) * ((i) + 1) / 2])
+    (void)Y;
 
-    // 1. Cholesky of S'
-    for (int i = 0; i < nu; ++i) {
-        for (int k = 0; k <= i; ++k) {
-            double s = PACK(Sp, i, k);
-            for (int m = 0; m < k; ++m) s -= LM(i, m) * LM(k, m);
-            if (i == k) {
-                if (!(s > 0.0)) {
-                    flag(a.status, DEV_NOT_SPD);
-                    return;
-                }
-                const double l = sqrt(s);
-                LM(i, i) = l;
-                IV(i) = 1.0 / l;
-            } else {
-                LM(i, k) = s * IV(k);
-            }
-        }
+    for (int q = lane; q < nu * nu; q += 32) {
+        const int i = q / nu, k = q % nu;
+        A[i * ld + k] = packed(Hp, i, k);
+        L[i * ld + k] = packed(Sp, i, k);
     }
-    // 2. X = L^-1 H' (kept in Q), 3. Y = L^-1 X^T (kept in A), A = (Y + Y^T) / 2
-    for (int n = 0; n < nu; ++n)
-        for (int i = 0; i < nu; ++i) {
-            double s = PACK(Hp, i, n);
-            for (int m = 0; m < i; ++m) s -= LM(i, m) * QM(m, n);
-            QM(i, n) = s * IV(i);
+    __syncwarp();
+    // Cholesky S' = L L^T (right-looking, lanes over rows of the trailing block)
+    bool spd = true;
+    for (int k = 0; k < nu; ++k) {
+        const double dk = L[k * ld + k];
+        if (!(dk > 0.0)) { spd = false; break; }
+        const double lkk = sqrt(dk), ik = 1.0 / lkk;
+        __syncwarp();
+        for (int i = k + 1 + lane; i < nu; i += 32) L[i * ld + k] *= ik;
+        if (lane == 0) { L[k * ld + k] = lkk; inv[k] = ik; }
+        __syncwarp();
+        for (int i = k + 1 + lane; i < nu; i += 32) {
+            const double lik = L[i * ld + k];
+            for (int m = k + 1; m <= i; ++m) L[i * ld + m] = fma(-lik, L[m * ld + k], L[i * ld + m]);
         }
-    for (int n = 0; n < nu; ++n)
+        __syncwarp();
+    }
+    if (!spd) {
+        if (lane == 0) flag(a.status, DEV_NOT_SPD);
+        for (int q = lane; q < 5 * nm; q += 32) yv[q] = 0.0;
+        return;
+    }
+    // X = L^-1 H' in place (lanes over columns n), then A = X L^-T in place (lanes over rows i)
+    for (int n = lane; n < nu; n += 32)
         for (int i = 0; i < nu; ++i) {
-            double s = QM(n, i);
-            for (int m = 0; m < i; ++m) s -= LM(i, m) * AM(m, n);
-            AM(i, n) = s * IV(i);
+            double s = A[i * ld + n];
+            for (int m = 0; m < i; ++m) s = fma(-L[i * ld + m], A[m * ld + n], s);
+            A[i * ld + n] = s * inv[i];
         }
-    for (int i = 0; i < nu; ++i)
+    __syncwarp();
+    for (int i = lane; i < nu; i += 32)
+        for (int n = 0; n < nu; ++n) {
+            double s = A[i * ld + n];
+            for (int m = 0; m < n; ++m) s = fma(-A[i * ld + m], L[n * ld + m], s);
+            A[i * ld + n] = s * inv[n];
+        }
+    __syncwarp();
+    for (int i = lane; i < nu; i += 32)
         for (int k = 0; k < i; ++k) {
-            const double v = 0.5 * (AM(i, k) + AM(k, i));
-            AM(i, k) = v;
-            AM(k, i) = v;
+            const double v = 0.5 * (A[i * ld + k] + A[k * ld + i]);
+            A[i * ld + k] = v;
+            A[k * ld + i] = v;
         }
-    // 4. Householder tridiagonalisation, Q accumulated
-    for (int i = 0; i < nu; ++i)
-        for (int k = 0; k < nu; ++k) QM(i, k) = (i == k) ? 1.0 : 0.0;
+    __syncwarp();
+    // Householder reduction: reflector k stored in column k below the diagonal, tau_k kept
+    double* E = yv + nm;
     for (int k = 0; k + 2 < nu; ++k) {
-        double sigma = 0.0;
-        for (int i = k + 1; i < nu; ++i) sigma += AM(i, k) * AM(i, k);
-        const double x0 = AM(k + 1, k);
-        if (sigma == 0.0) continue;
-        const double alpha = -copysign(sqrt(sigma), x0);
-        const double tau = 1.0 / (alpha * (alpha - x0));   // 2 / ||v||^2
-        TV(k + 1) = x0 - alpha;
-        for (int i = k + 2; i < nu; ++i) TV(i) = AM(i, k);
-        double K = 0.0;
-        for (int i = k + 1; i < nu; ++i) {
-            double s = 0.0;
-            for (int m = k + 1; m < nu; ++m) s += AM(i, m) * TV(m);
-            PV(i) = tau * s;
-            K += TV(i) * PV(i);
+        double part = 0.0;
+        for (int i = k + 1 + lane; i < nu; i += 32) part = fma(A[i * ld + k], A[i * ld + k], part);
+        const double sigma = warp_sum(part);
+        const double x0 = A[(k + 1) * ld + k];
+        __syncwarp();
+        if (sigma == 0.0) {
+            if (lane == 0) { E[k] = 0.0; P[k] = 0.0; }
+            continue;
         }
-        K *= 0.5 * tau;
-        for (int i = k + 1; i < nu; ++i) PV(i) -= K * TV(i);
-        for (int i = k + 1; i < nu; ++i)
-            for (int m = k + 1; m < nu; ++m) AM(i, m) -= TV(i) * PV(m) + PV(i) * TV(m);
-        AM(k + 1, k) = alpha;
-        AM(k, k + 1) = alpha;
-        for (int i = k + 2; i < nu; ++i) { AM(i, k) = 0.0; AM(k, i) = 0.0; }
-        for (int r = 0; r < nu; ++r) {
+        const double alpha = -copysign(sqrt(sigma), x0);
+        const double tau = 1.0 / (alpha * (alpha - x0));
+        if (lane == 0) A[(k + 1) * ld + k] = x0 - alpha;
+        __syncwarp();
+        // p = tau A v (rows i > k)
+        double kp = 0.0;
+        for (int i = k + 1 + lane; i < nu; i += 32) {
+            double s = 0.0;
+            for (int m = k + 1; m < nu; ++m) s = fma(A[i * ld + m], A[m * ld + k], s);
+            s *= tau;
+            P[i] = s;
+            kp = fma(A[i * ld + k], s, kp);
+        }
+        const double K = 0.5 * tau * warp_sum(kp);
+        __syncwarp();
+        for (int i = k + 1 + lane; i < nu; i += 32) P[i] = fma(-K, A[i * ld + k], P[i]);
+        __syncwarp();
+        for (int i = k + 1 + lane; i < nu; i += 32) {
+            const double vi = A[i * ld + k], qi = P[i];
+            for (int m = k + 1; m < nu; ++m)
+                A[i * ld + m] = fma(-vi, P[m], fma(-qi, A[m * ld + k], A[i * ld + m]));
+        }
+        __syncwarp();
+        if (lane == 0) { E[k] = alpha; P[k] = tau; }   // P[k] keeps tau_k (P[i > k] reused later)
+        __syncwarp();
+    }
+    // tridiagonal T: D, E
+    double* D = yv;
+    for (int i = lane; i < nu; i += 32) D[i] = A[i * ld + i];
+    if (lane == 0 && nu >= 2) E[nu - 2] = A[(nu - 1) * ld + (nu - 2)];
+    if (lane == 0 && nu >= 2) {
+        // the last two reflector slots are unused: mark them
+        P[nu - 2] = 0.0;
+        P[nu - 1] = 0.0;
+    }
+    __syncwarp();
+    // the three vectors: z = L^-1 (U, SU, HU)_j, then y = Q_H^T z (reflectors k = 0, 1, ...)
+    if (lane < 3) {
+        const double* src = (lane == 0 ? a.urow : lane == 1 ? a.surow : a.hurow) + (size_t)c * nm;
+        double* y = yv + (2 + lane) * nm;
+        for (int i = 0; i < nu; ++i) {
+            double s = src[i];
+            for (int m = 0; m < i; ++m) s = fma(-L[i * ld + m], y[m], s);
+            y[i] = s * inv[i];
+        }
+        for (int k = 0; k + 2 < nu; ++k) {
+            const double tau = P[k];
+            if (tau == 0.0) continue;
             double t = 0.0;
-            for (int m = k + 1; m < nu; ++m) t += QM(r, m) * TV(m);
+            for (int m = k + 1; m < nu; ++m) t = fma(A[m * ld + k], y[m], t);
             t *= tau;
-            for (int m = k + 1; m < nu; ++m) QM(r, m) -= t * TV(m);
+            for (int m = k + 1; m < nu; ++m) y[m] = fma(-t, A[m * ld + k], y[m]);
         }
     }
-    for (int i = 0; i < nu; ++i) DV(i) = AM(i, i);
-    for (int i = 0; i + 1 < nu; ++i) EV(i) = AM(i + 1, i);
-    // 5. implicit-shift QR on the tridiagonal (D, E)
+    __syncwarp();
+    // factors for k_eig_vectors: reflectors (column k below the diagonal, tau_k on the diagonal), L
+    double* F = a.fac + (size_t)c * eig_fac_doubles(nm);
+    for (int q = lane; q < nu * nu; q += 32) {
+        const int i = q / nu, k = q % nu;
+        F[i * nm + k] = (i == k) ? P[k] : A[i * ld + k];
+        F[nm * nm + i * nm + k] = L[i * ld + k];
+    }
+}
+
+// ----------------------------------------------------------------------------- k_eig_chase
+__global__ void __launch_bounds__(64) k_eig_chase(const EigArgs a) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.ncols) return;
+    const int nm = a.nu_max;
+    const int j = a.col0 + c;
+    const int nu = a.nu_eff[j];
+    double* t = a.tri + (size_t)c * eig_tri_doubles(nm);
+    double* D = t;
+    double* E = t + nm;
+    double* yc = t + 2 * nm;
+    double* yd = t + 3 * nm;
+    double* yg = t + 4 * nm;
+    double* rc = a.rot_c + (size_t)c * eig_rot_cap(nm);
+    double* rs = a.rot_s + (size_t)c * eig_rot_cap(nm);
+    unsigned char* rk = a.rot_k + (size_t)c * eig_rot_cap(nm);
+    const size_t cap = eig_rot_cap(nm);
+    size_t nrot = 0;
+    bool ok = true;
     const double eps = 2.220446049250313e-16;
     int hi = nu - 1, sweeps = 0;
-    while (hi > 0) {
-        if (fabs(EV(hi - 1)) <= eps * (fabs(DV(hi - 1)) + fabs(DV(hi)))) {
-            EV(hi - 1) = 0.0;
+    while (hi > 0 && ok) {
+        if (fabs(E[hi - 1]) <= eps * (fabs(D[hi - 1]) + fabs(D[hi]))) {
+            E[hi - 1] = 0.0;
             --hi;
             continue;
         }
         int lo = hi - 1;
-        while (lo > 0 && fabs(EV(lo - 1)) > eps * (fabs(DV(lo - 1)) + fabs(DV(lo)))) --lo;
-        if (lo > 0) EV(lo - 1) = 0.0;
-        if (++sweeps > 30 * nu) {
-            flag(a.status, DEV_TIMEOUT);
+        while (lo > 0 && fabs(E[lo - 1]) > eps * (fabs(D[lo - 1]) + fabs(D[lo]))) --lo;
+        if (lo > 0) E[lo - 1] = 0.0;
+        if (++sweeps > 30 * nu || nrot + (hi - lo) > cap) {
+            ok = false;
             break;
         }
-        const double delta = 0.5 * (DV(hi - 1) - DV(hi));
-        const double b2 = EV(hi - 1) * EV(hi - 1);
+        const double delta = 0.5 * (D[hi - 1] - D[hi]);
+        const double b2 = E[hi - 1] * E[hi - 1];
         const double den = delta + copysign(sqrt(delta * delta + b2), delta);
-        const double mu = DV(hi) - (den != 0.0 ? b2 / den : 0.0);
-        double x = DV(lo) - mu, z = EV(lo);
+        const double mu = D[hi] - (den != 0.0 ? b2 / den : 0.0);
+        double x = D[lo] - mu, z = E[lo];
         for (int k = lo; k < hi; ++k) {
             const double r = hypot(x, z);
             double cr = 1.0, sr = 0.0;
             if (r != 0.0) { cr = x / r; sr = z / r; }
-            if (k > lo) EV(k - 1) = r;
-            const double ak = DV(k), ak1 = DV(k + 1), b = EV(k);
+            if (k > lo) E[k - 1] = r;
+            const double ak = D[k], ak1 = D[k + 1], b = E[k];
             const double cc = cr * cr, ss = sr * sr, cs = cr * sr;
-            DV(k) = cc * ak + 2.0 * cs * b + ss * ak1;
-            DV(k + 1) = ss * ak - 2.0 * cs * b + cc * ak1;
-            EV(k) = cs * (ak1 - ak) + (cc - ss) * b;
+            D[k] = cc * ak + 2.0 * cs * b + ss * ak1;
+            D[k + 1] = ss * ak - 2.0 * cs * b + cc * ak1;
+            E[k] = cs * (ak1 - ak) + (cc - ss) * b;
             if (k + 1 < hi) {
-                const double bn = EV(k + 1);
+                const double bn = E[k + 1];
                 z = sr * bn;
-                EV(k + 1) = cr * bn;
-                x = EV(k);
+                E[k + 1] = cr * bn;
+                x = E[k];
             }
-            for (int q = 0; q < nu; ++q) {
-                const double qk = QM(q, k), qk1 = QM(q, k + 1);
-                QM(q, k) = cr * qk + sr * qk1;
-                QM(q, k + 1) = -sr * qk + cr * qk1;
-            }
+            // the three vectors follow P^T: y <- R y on rows k, k+1
+            double u0 = yc[k], u1 = yc[k + 1];
+            yc[k] = cr * u0 + sr * u1; yc[k + 1] = cr * u1 - sr * u0;
+            u0 = yd[k]; u1 = yd[k + 1];
+            yd[k] = cr * u0 + sr * u1; yd[k + 1] = cr * u1 - sr * u0;
+            u0 = yg[k]; u1 = yg[k + 1];
+            yg[k] = cr * u0 + sr * u1; yg[k + 1] = cr * u1 - sr * u0;
+            rc[nrot] = cr;
+            rs[nrot] = sr;
+            rk[nrot] = (unsigned char)k;
+            ++nrot;
         }
     }
-    // 6. ascending order (selection, columns of Q follow)
+    if (!ok) flag(a.status, DEV_TIMEOUT);
+    a.rot_n[c] = ok ? (int)nrot : 0;
+    // ascending order; perm[out] = index into the unsorted arrays
+    int* perm = a.perm + (size_t)c * nm;
+    for (int k = 0; k < nu; ++k) perm[k] = k;
     for (int k = 0; k + 1 < nu; ++k) {
         int m = k;
         for (int q = k + 1; q < nu; ++q)
-            if (DV(q) < DV(m)) m = q;
-        if (m != k) {
-            const double t = DV(k); DV(k) = DV(m); DV(m) = t;
-            for (int q = 0; q < nu; ++q) { const double u = QM(q, k); QM(q, k) = QM(q, m); QM(q, m) = u; }
-        }
+            if (D[perm[q]] < D[perm[m]]) m = q;
+        const int tmp = perm[k]; perm[k] = perm[m]; perm[m] = tmp;
     }
-    // 7. V = L^-T Q (back substitution, kept in A), spectra
-    for (int k = 0; k < nu; ++k)
-        for (int i = nu - 1; i >= 0; --i) {
-            double s = QM(i, k);
-            for (int m = i + 1; m < nu; ++m) s -= LM(m, i) * AM(m, k);
-            AM(i, k) = s * IV(i);
-        }
-    const double* ur = a.urow + (size_t)c * nm;
-    const double* sr = a.surow + (size_t)c * nm;
-    const double* hr = a.hurow + (size_t)c * nm;
-    double* Vo = a.V + (size_t)c * nm * nm;
     for (int k = 0; k < nm; ++k) {
-        double cc = 0.0, dd = 0.0, gg = 0.0, e = 0.0;
-        if (k < nu) {
-            for (int n = 0; n < nu; ++n) {
-                const double v = AM(n, k);
-                cc += v * ur[n];
-                dd += v * sr[n];
-                gg += v * hr[n];
-                Vo[(size_t)n * nm + k] = v;
-            }
-            e = DV(k);
+        double e = 0.0, cv = 0.0, dv = 0.0, gv = 0.0;
+        if (k < nu && ok) {
+            const int p = perm[k];
+            e = D[p]; cv = yc[p]; dv = yd[p]; gv = yg[p];
         }
         a.eps[(size_t)j * nm + k] = e;
-        a.c[(size_t)j * nm + k] = cc;
-        a.d[(size_t)j * nm + k] = dd;
-        a.g[(size_t)j * nm + k] = gg;
+        a.c[(size_t)j * nm + k] = cv;
+        a.d[(size_t)j * nm + k] = dv;
+        a.g[(size_t)j * nm + k] = gv;
     }
-#undef AM
-#undef QM
-#undef LM
-#undef DV
-#undef EV
-#undef TV
-#undef PV
-#undef IV
-#undef XV
-#undef PACK
 }
 
+// ----------------------------------------------------------------------------- k_eig_vectors
+__global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a) {
+    extern __shared__ __align__(16) double sm[];
+    const int lane = threadIdx.x;
+    const int c = blockIdx.x;
+    if (c >= a.ncols) return;
+    const int nm = a.nu_max, ld = nm + 1;
+    const int j = a.col0 + c;
+    const int nu = a.nu_eff[j];
+    double* R = sm;                 // reflectors (column k below the diagonal), tau_k on the diagonal
+    double* L = R + nm * ld;
+    double* Q = L + nm * ld;
+    double* inv = Q + nm * ld;
+    const double* F = a.fac + (size_t)c * eig_fac_doubles(nm);
+    for (int q = lane; q < nu * nu; q += 32) {
+        const int i = q / nu, k = q % nu;
+        R[i * ld + k] = F[i * nm + k];
+        L[i * ld + k] = F[nm * nm + i * nm + k];
+        Q[i * ld + k] = (i == k) ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    for (int i = lane; i < nu; i += 32) inv[i] = 1.0 / L[i * ld + i];
+    // Q_H = H_0 H_1 ... H_{nu-3}, accumulated from the last reflector (rows / columns > k only)
+    for (int k = nu - 3; k >= 0; --k) {
+        const double tau = R[k * ld + k];
+        if (tau == 0.0) continue;
+        for (int n = k + 1 + lane; n < nu; n += 32) {
+            double t = 0.0;
+            for (int i = k + 1; i < nu; ++i) t = fma(R[i * ld + k], Q[i * ld + n], t);
+            t *= tau;
+            for (int i = k + 1; i < nu; ++i) Q[i * ld + n] = fma(-t, R[i * ld + k], Q[i * ld + n]);
+        }
+        __syncwarp();
+    }
+    // Q <- Q R^T for every recorded rotation (columns k, k+1; lanes over rows)
+    const int nrot = a.rot_n[c];
+    const double* rc = a.rot_c + (size_t)c * eig_rot_cap(nm);
+    const double* rs = a.rot_s + (size_t)c * eig_rot_cap(nm);
+    const unsigned char* rk = a.rot_k + (size_t)c * eig_rot_cap(nm);
+    for (int r = 0; r < nrot; ++r) {
+        const double cr = __ldg(rc + r), sr = __ldg(rs + r);
+        const int k = __ldg(rk + r);
+        if (lane < nu) {
+            const double q0 = Q[lane * ld + k], q1 = Q[lane * ld + k + 1];
+            Q[lane * ld + k] = fma(cr, q0, sr * q1);
+            Q[lane * ld + k + 1] = fma(cr, q1, -sr * q0);
+        }
+        if (nu > 32) {
+            for (int q = lane + 32; q < nu; q += 32) {
+                const double q0 = Q[q * ld + k], q1 = Q[q * ld + k + 1];
+                Q[q * ld + k] = fma(cr, q0, sr * q1);
+                Q[q * ld + k + 1] = fma(cr, q1, -sr * q0);
+            }
+        }
+    }
+    __syncwarp();
+    // V = L^-T Q in place (lanes over columns m, rows bottom-up)
+    for (int m = lane; m < nu; m += 32)
+        for (int i = nu - 1; i >= 0; --i) {
+            double s = Q[i * ld + m];
+            for (int l = i + 1; l < nu; ++l) s = fma(-L[l * ld + i], Q[l * ld + m], s);
+            Q[i * ld + m] = s * inv[i];
+        }
+    __syncwarp();
+    const int* perm = a.perm + (size_t)c * nm;
+    double* Vo = a.V + (size_t)c * nm * nm;
+    for (int q = lane; q < nu * nu; q += 32) {
+        const int n = q / nu, k = q % nu;
+        Vo[(size_t)n * nm + k] = Q[n * ld + perm[k]];
+    }
+}
+
+size_t eig_smem_reduce(int nm) { return sizeof(double) * 2 * (2 * (size_t)nm * (nm + 1) + 4 * nm); }
+size_t eig_smem_vectors(int nm) { return sizeof(double) * (3 * (size_t)nm * (nm + 1) + nm); }
+
 void projected_eig(const EigArgs& a, cudaStream_t st) {
-    const int T = 64;
-    k_proj_eig<<<(a.ncols + T - 1) / T, T, 0, st>>>(a);
+    const size_t s1 = eig_smem_reduce(a.nu_max), s3 = eig_smem_vectors(a.nu_max);
+    cudaFuncSetAttribute(k_eig_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
+    cudaFuncSetAttribute(k_eig_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s3);
+    k_eig_reduce<<<(a.ncols + 1) / 2, 64, s1, st>>>(a);
+    k_eig_chase<<<(a.ncols + 63) / 64, 64, 0, st>>>(a);
+    k_eig_vectors<<<a.ncols, 32, s3, st>>>(a);
 }
 
 }  // namespace elses

@@ -90,7 +90,9 @@ struct elses_system_s {
     std::vector<int> h_row_ptr;
 
     int nu_max = 0, na_max = 0, k3_grid = 0, batch_atoms = 0;
-    DevBuf<double> kscratch, Hp, Sp, urow, surow, hurow, eigwork;
+    DevBuf<double> kscratch, Hp, Sp, urow, surow, hurow, etri, efac, erot_c, erot_s;
+    DevBuf<unsigned char> erot_k;
+    DevBuf<int> erot_n, eperm;
     DevBuf<double> eps, cc, dd, gg, V, UP, Vb, UPb;
     DevBuf<int> nu_eff, order;
     DevBuf<double> rho, rhoE, gblock;
@@ -194,8 +196,9 @@ int prepare_columns(elses_system s) {
     TRY(s->kscratch.ensure(per_cta * s->k3_grid));
     // batch of atoms for the Krylov -> eigensolver hand-off
     const size_t PK = (size_t)nm * (nm + 1) / 2;
-    const size_t per_col = 2 * PK + 3 * (size_t)nm + eig_work_doubles(nm);
-    size_t cols = std::max<size_t>(128, (size_t)(1u << 29) / (per_col * sizeof(double)));   // ~512 MB
+    const size_t per_col = sizeof(double) * (2 * PK + 3 * (size_t)nm + eig_tri_doubles(nm) + eig_fac_doubles(nm) +
+                                             2 * eig_rot_cap(nm)) + eig_rot_cap(nm) + sizeof(int) * (nm + 1);
+    size_t cols = std::max<size_t>(128, (size_t)(1u << 30) / per_col);   // ~1 GB of batch buffers
     s->batch_atoms = (int)std::min<size_t>((size_t)s->n, std::max<size_t>(32, cols / 4));
     const size_t bc = 4 * (size_t)s->batch_atoms;
     const size_t bc_pad = ((bc + 31) / 32) * 32;
@@ -204,7 +207,14 @@ int prepare_columns(elses_system s) {
     TRY(s->urow.ensure(bc * nm));
     TRY(s->surow.ensure(bc * nm));
     TRY(s->hurow.ensure(bc * nm));
-    TRY(s->eigwork.ensure(bc_pad * eig_work_doubles(nm)));
+    (void)bc_pad;
+    TRY(s->etri.ensure(bc * eig_tri_doubles(nm)));
+    TRY(s->efac.ensure(bc * eig_fac_doubles(nm)));
+    TRY(s->erot_c.ensure(bc * eig_rot_cap(nm)));
+    TRY(s->erot_s.ensure(bc * eig_rot_cap(nm)));
+    TRY(s->erot_k.ensure(bc * eig_rot_cap(nm)));
+    TRY(s->erot_n.ensure(bc));
+    TRY(s->eperm.ensure(bc * nm));
     const size_t M = s->M;
     TRY(s->eps.ensure(M * nm));
     TRY(s->cc.ensure(M * nm));
@@ -300,8 +310,13 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
     ea.surow = s->surow.p;
     ea.hurow = s->hurow.p;
     ea.nu_eff = s->nu_eff.p;
-    ea.work = s->eigwork.p;
-    ea.ncols_pad = ((4 * s->batch_atoms + 31) / 32) * 32;
+    ea.tri = s->etri.p;
+    ea.fac = s->efac.p;
+    ea.rot_c = s->erot_c.p;
+    ea.rot_s = s->erot_s.p;
+    ea.rot_k = s->erot_k.p;
+    ea.rot_n = s->erot_n.p;
+    ea.perm = s->eperm.p;
     ea.eps = s->eps.p;
     ea.c = s->cc.p;
     ea.d = s->dd.p;
@@ -311,7 +326,7 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
     s->tic(T_EIG, st);
     projected_eig(ea, st);
     s->toc(st);
-    s->stats.launches++;
+    s->stats.launches += 3;
     s->stats.columns += 4LL * (e - b);
     *V_out = ea.V;
     *v_col0 = 4 * b;
@@ -371,13 +386,16 @@ const char* elses_last_error(void) { return g_err.c_str(); }
 void elses_system_destroy(elses_system s) {
     if (!s) return;
     DevBuf<double>* dbs[] = {&s->pos, &s->H, &s->S, &s->kscratch, &s->Hp, &s->Sp, &s->urow,
-                             &s->surow, &s->hurow, &s->eigwork, &s->eps, &s->cc, &s->dd, &s->gg,
+                             &s->surow, &s->hurow, &s->etri, &s->efac, &s->erot_c, &s->erot_s,
+                             &s->eps, &s->cc, &s->dd, &s->gg,
                              &s->V, &s->UP, &s->Vb, &s->UPb, &s->rho, &s->rhoE, &s->gblock,
                              &s->partials, &s->zbuf};
     for (auto* b : dbs) b->release();
     DevBuf<int>* ibs[] = {&s->cell_of, &s->cell_count, &s->cell_start, &s->cursor, &s->cell_atoms,
                           &s->row_cnt, &s->row_ptr, &s->col_idx, &s->row_of, &s->tmap, &s->cl_cnt,
-                          &s->cl_ptr, &s->cl_idx, &s->counters, &s->nu_eff, &s->order};
+                          &s->cl_ptr, &s->cl_idx, &s->counters, &s->nu_eff, &s->order, &s->erot_n,
+                          &s->eperm};
+    s->erot_k.release();
     for (auto* b : ibs) b->release();
     s->bstate.release();
     s->ticket.release();
