@@ -144,8 +144,9 @@ class ClockSampler:
 def krylov_flops(sys_g, w):
     """Algorithmic FP64 flops of the Krylov build + projection (a3, a4) over all columns.
 
-    Per column with n_c = 4 |C| orbitals, b_C in-cluster 4x4 blocks and nu_eff steps:
-      sparse products  2 nu_eff of them (H u_n; S u_1 and S w), 2 * 16 b_C flops each
+    Per column with n_c = 4 |C| orbitals, b_off off-site 4x4 blocks inside the cluster and
+    nu_eff steps (the on-site blocks of the Slater-Koster model are S = I and H diagonal):
+      sparse products  nu_eff with H (32 b_off + 4 |C|) and nu_eff with S (32 b_off)
       projection + first CGS pass  sum_{n<nu} (3 dots of n+1 vectors + ||H u_n||^2) = (6(n+1)+2) n_c
       CGS update, second pass, update, beta, scaling  sum_{n<nu-1} (6(n+1) + 4) n_c
     """
@@ -164,13 +165,13 @@ def krylov_flops(sys_g, w):
         inc = np.zeros(w.n_atoms, bool)
         inc[C] = True
         rows = np.concatenate([ci[rp[a]:rp[a + 1]] for a in C])
-        b_c = int(inc[rows].sum())
+        b_off = int(inc[rows].sum()) - len(C)
         n_c = 4 * len(C)
         for nu in nu_eff[J]:
             nu = int(nu)
             k = np.arange(1, nu + 1)
             dense = float(np.sum(6 * k + 2) + np.sum(6 * k[:-1] + 4)) * n_c
-            total += 2 * nu * 32.0 * b_c + dense
+            total += nu * (64.0 * b_off + 4.0 * len(C)) + dense
     return total
 
 

@@ -54,6 +54,7 @@ struct KrylovArgs {
     int class_max_atoms[4];
     int class_nu[4];
     double breakdown_tol;
+    int onsite_diag;        // 1: on-site S blocks are I and on-site H blocks diagonal
     int na_max;             // cluster capacity rounded up to a multiple of 32
     int deg_max;            // maximum pattern row length
     double* scratch;        // per resident CTA: 4 warps x (U, SU) x nu_max x na_max x 4

@@ -53,14 +53,28 @@ __device__ __forceinline__ double fma4(const double2 a0, const double2 a1, const
     return fma(a1.y, b1.y, fma(a1.x, b1.x, fma(a0.y, b0.y, fma(a0.x, b0.x, acc))));
 }
 
-// y = A x on the cluster (lane-owned rows; x gathered from shared memory).
+// y = A x on the cluster (lane-owned rows; x gathered from shared memory). With `onsite` the
+// ELL holds only the off-site blocks and the on-site block is applied as a diagonal: `diag`
+// (4 values per position) or the identity when diag is null.
 __device__ __forceinline__ void spmv(const double* __restrict__ vals, const Ent* __restrict__ ell,
                                      const int* __restrict__ ell_off, int NS, const double* x,
-                                     double* y, int lane) {
+                                     double* y, int lane, bool onsite, const double* diag) {
     for (int s = 0; s < NS; ++s) {
         const int W = (ell_off[s + 1] - ell_off[s]) >> 5;
         const Ent* es = ell + ell_off[s] + lane;
+        const int po = 4 * (s * 32 + lane);
         double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
+        if (onsite) {
+            const double2 o01 = *reinterpret_cast<const double2*>(x + po);
+            const double2 o23 = *reinterpret_cast<const double2*>(x + po + 2);
+            if (diag) {
+                const double2 d01 = *reinterpret_cast<const double2*>(diag + po);
+                const double2 d23 = *reinterpret_cast<const double2*>(diag + po + 2);
+                y0 = d01.x * o01.x; y1 = d01.y * o01.y; y2 = d23.x * o23.x; y3 = d23.y * o23.y;
+            } else {
+                y0 = o01.x; y1 = o01.y; y2 = o23.x; y3 = o23.y;
+            }
+        }
         for (int k = 0; k < W; ++k) {
             const Ent en = es[32 * k];
             if (en.blk >= 0) {
@@ -75,7 +89,7 @@ __device__ __forceinline__ void spmv(const double* __restrict__ vals, const Ent*
                 y3 = fma(a6.x, x01.x, fma(a6.y, x01.y, fma(a7.x, x23.x, fma(a7.y, x23.y, y3))));
             }
         }
-        double2* yo = reinterpret_cast<double2*>(y + 4 * (s * 32 + lane));
+        double2* yo = reinterpret_cast<double2*>(y + po);
         yo[0] = make_double2(y0, y1);
         yo[1] = make_double2(y2, y3);
     }
@@ -92,10 +106,33 @@ __device__ __forceinline__ void st4(double* p, const double2 a, const double2 b)
     q[1] = b;
 }
 
+// w -= sum_{k <= n} U[:, k] h_k on the lane's rows of slot position p; the basis rows are
+// fetched eight at a time before they are used, so their latency overlaps.
+__device__ __forceinline__ void sub_basis(const double* Ub, int NP, int p, const double* h, int n,
+                                          double2& w0, double2& w1) {
+    for (int k0 = 0; k0 <= n; k0 += 8) {
+        double2 ua[8], ub[8];
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk)
+            if (k0 + kk <= n) ld4(Ub + 4 * ((size_t)(k0 + kk) * NP + p), ua[kk], ub[kk]);
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            if (k0 + kk <= n) {
+                const double hk = h[k0 + kk];
+                w0.x = fma(-ua[kk].x, hk, w0.x);
+                w0.y = fma(-ua[kk].y, hk, w0.y);
+                w1.x = fma(-ub[kk].x, hk, w1.x);
+                w1.y = fma(-ub[kk].y, hk, w1.y);
+            }
+        }
+    }
+}
+
 size_t krylov_smem_bytes(int na_max, int deg_max) {
     size_t b = 0;
     b += sizeof(double) * (size_t)kWarpsPerAtom * 3 * na_max * 4;   // u, hu/w, su per warp
     b += sizeof(double) * (size_t)kWarpsPerAtom * kMaxNu;            // CGS coefficients
+    b += sizeof(double) * (size_t)na_max * 4;                        // on-site H diagonal
     b += sizeof(Ent) * (size_t)na_max * deg_max;                     // ELL
     b += sizeof(int) * (size_t)(4 * na_max + na_max / 32 + 2);       // lists
     return (b + 15) & ~(size_t)15;
@@ -106,7 +143,9 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
     const int NA = a.na_max;
     double* vec = reinterpret_cast<double*>(smem_raw);
     double* hbuf = vec + (size_t)kWarpsPerAtom * 3 * NA * 4;
-    Ent* ell = reinterpret_cast<Ent*>(hbuf + kWarpsPerAtom * kMaxNu);
+    double* hdiag = hbuf + kWarpsPerAtom * kMaxNu;
+    Ent* ell = reinterpret_cast<Ent*>(hdiag + (size_t)NA * 4);
+    const bool onsite = a.onsite_diag != 0;
     int* cl = reinterpret_cast<int*>(ell + (size_t)NA * a.deg_max);
     int* deg = cl + NA;
     int* pos_of = deg + NA;
@@ -146,7 +185,10 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
         for (int q = tid; q < n_at; q += kThreads) {
             const int A = cl[q];
             int cnt = 0;
-            for (int e = a.row_ptr[A]; e < a.row_ptr[A + 1]; ++e) cnt += bsearch_sorted(cl, n_at, a.col_idx[e]) >= 0;
+            for (int e = a.row_ptr[A]; e < a.row_ptr[A + 1]; ++e) {
+                const int ce = a.col_idx[e];
+                cnt += (!onsite || ce != A) && bsearch_sorted(cl, n_at, ce) >= 0;
+            }
             deg[q] = cnt;
         }
         __syncthreads();
@@ -190,14 +232,21 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
             const int W = (ell_off[s + 1] - ell_off[s]) >> 5;
             Ent* col = ell + ell_off[s] + l;
             int k = 0;
+            double hd[4] = {0.0, 0.0, 0.0, 0.0};
             if (q >= 0) {
                 const int A = cl[q];
                 for (int e = a.row_ptr[A]; e < a.row_ptr[A + 1]; ++e) {
-                    const int b = bsearch_sorted(cl, n_at, a.col_idx[e]);
+                    const int ce = a.col_idx[e];
+                    if (onsite && ce == A) {
+                        for (int r = 0; r < 4; ++r) hd[r] = a.H[16 * (size_t)e + 5 * r];
+                        continue;
+                    }
+                    const int b = bsearch_sorted(cl, n_at, ce);
                     if (b >= 0) col[32 * (k++)] = Ent{4 * pos_of[b], e};
                 }
             }
             for (; k < W; ++k) col[32 * k] = Ent{0, -1};
+            for (int r = 0; r < 4; ++r) hdiag[4 * p + r] = hd[r];
         }
         __syncthreads();
 
@@ -227,7 +276,7 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
             __syncwarp();
             if (lane == 0) A[jp] = 1.0 / sqrt(sjj);
             __syncwarp();
-            spmv(a.S, ell, ell_off, NS, A, C, lane);
+            spmv(a.S, ell, ell_off, NS, A, C, lane, onsite, nullptr);
             for (int s = 0; s < NS; ++s) {
                 const int p = s * 32 + lane;
                 double2 x0, x1;
@@ -240,7 +289,7 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
 
             int nu_eff = nu;
             for (int n = 0; n < nu; ++n) {
-                spmv(a.H, ell, ell_off, NS, A, B, lane);
+                spmv(a.H, ell, ell_off, NS, A, B, lane, onsite, hdiag);
                 __syncwarp();
                 if (lane == 0) {
                     a.urow[(size_t)col * a.nu_max + n] = A[jp];
@@ -292,13 +341,7 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
                     const int p = s * 32 + lane;
                     double2 w0, w1;
                     ld4(B + 4 * p, w0, w1);
-                    for (int k = 0; k <= n; ++k) {
-                        const double hk = h[k];
-                        double2 u0, u1;
-                        ld4(Uw + 4 * ((size_t)k * NP + p), u0, u1);
-                        w0.x = fma(-u0.x, hk, w0.x); w0.y = fma(-u0.y, hk, w0.y);
-                        w1.x = fma(-u1.x, hk, w1.x); w1.y = fma(-u1.y, hk, w1.y);
-                    }
+                    sub_basis(Uw, NP, p, h, n, w0, w1);
                     st4(B + 4 * p, w0, w1);
 #pragma unroll
                     for (int kk = 0; kk < 32; ++kk) {
@@ -337,18 +380,12 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
                     const int p = s * 32 + lane;
                     double2 w0, w1;
                     ld4(B + 4 * p, w0, w1);
-                    for (int k = 0; k <= n; ++k) {
-                        const double hk = h[k];
-                        double2 u0, u1;
-                        ld4(Uw + 4 * ((size_t)k * NP + p), u0, u1);
-                        w0.x = fma(-u0.x, hk, w0.x); w0.y = fma(-u0.y, hk, w0.y);
-                        w1.x = fma(-u1.x, hk, w1.x); w1.y = fma(-u1.y, hk, w1.y);
-                    }
+                    sub_basis(Uw, NP, p, h, n, w0, w1);
                     st4(B + 4 * p, w0, w1);
                 }
                 __syncwarp();
                 // Sw and beta
-                spmv(a.S, ell, ell_off, NS, B, C, lane);
+                spmv(a.S, ell, ell_off, NS, B, C, lane, onsite, nullptr);
                 double part = 0.0;
                 for (int s = 0; s < NS; ++s) {
                     const int p = s * 32 + lane;

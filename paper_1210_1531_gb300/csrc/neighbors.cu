@@ -159,6 +159,13 @@ __global__ void k_lists(const double* __restrict__ pos, int n, CellGrid g,
     int* buf = sbuf + wib * cap;
     const double xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
     const double r2 = __dmul_rn(r, r);
+    const float fxi = (float)xi, fyi = (float)yi, fzi = (float)zi;
+    const float fL[3] = {(float)g.L[0], (float)g.L[1], (float)g.L[2]};
+    const float fiL[3] = {1.0f / fL[0], 1.0f / fL[1], 1.0f / fL[2]};
+    // the FP32 image choice can differ from the exact one only for |d| ~ L/2, which is farther
+    // than r whenever L/2 - r is not tiny; otherwise every candidate takes the exact test
+    const bool pre_ok = 0.5 * g.L[0] - r > 0.01 && 0.5 * g.L[1] - r > 0.01 && 0.5 * g.L[2] - r > 0.01;
+    const float r2_pre = pre_ok ? ((float)r + 0.05f) * ((float)r + 0.05f) : 3.0e38f;
     const int c = cell_of[i];
     const int ci[3] = {c / (g.nc[1] * g.nc[2]), (c / g.nc[2]) % g.nc[1], c % g.nc[2]};
     const int reach[3] = {reach0, reach1, reach2};
@@ -183,10 +190,19 @@ __global__ void k_lists(const double* __restrict__ pos, int n, CellGrid g,
                     int j = -1;
                     if (q < s1) {
                         j = cell_atoms[q];
-                        const double dx = min_image(__dsub_rn(pos[3 * j], xi), g.L[0]);
-                        const double dy = min_image(__dsub_rn(pos[3 * j + 1], yi), g.L[1]);
-                        const double dz = min_image(__dsub_rn(pos[3 * j + 2], zi), g.L[2]);
-                        hit = dist2_exact(dx, dy, dz) <= r2;
+                        // FP32 prefilter (error < 1e-3 A^2 for boxes of a few hundred A): only
+                        // candidates near the sphere take the exact FP64 test below
+                        const float fx = (float)pos[3 * j] - fxi, fy = (float)pos[3 * j + 1] - fyi,
+                                    fz = (float)pos[3 * j + 2] - fzi;
+                        const float gx = fx - fL[0] * rintf(fx * fiL[0]);
+                        const float gy = fy - fL[1] * rintf(fy * fiL[1]);
+                        const float gz = fz - fL[2] * rintf(fz * fiL[2]);
+                        if (gx * gx + gy * gy + gz * gz <= r2_pre) {
+                            const double dx = min_image(__dsub_rn(pos[3 * j], xi), g.L[0]);
+                            const double dy = min_image(__dsub_rn(pos[3 * j + 1], yi), g.L[1]);
+                            const double dz = min_image(__dsub_rn(pos[3 * j + 2], zi), g.L[2]);
+                            hit = dist2_exact(dx, dy, dz) <= r2;
+                        }
                     }
                     const unsigned m = __ballot_sync(0xffffffffu, hit);
                     if (FILL && hit) {

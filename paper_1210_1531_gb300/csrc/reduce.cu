@@ -36,7 +36,7 @@ int reduce_grid() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return 2 * (sms > 0 ? sms : 1);
+    return 4 * (sms > 0 ? sms : 1);
 }
 
 template <int NV>
@@ -59,14 +59,40 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* part
     }
 }
 
-// Returns true in thread 0 of the last block to finish (after all partials are visible).
+// True in every thread of the last block to finish (after all partials are visible).
 __device__ __forceinline__ bool last_block(unsigned* ticket) {
     __shared__ bool is_last;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     __syncthreads();
-    return is_last && threadIdx.x == 0;
+    return is_last;
+}
+
+// Sum of the block partials [b][q], q < NV, by all threads of one block in a fixed order
+// (thread t takes blocks t, t + T, ...; then a fixed tree). Result valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void sum_partials(const double* partials, int nblocks, double (&out)[NV]) {
+    __shared__ double sh[NV][kRedThreads / 32];
+    double v[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] += __ldcg(partials + 4 * (size_t)b + q);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        const double x = warp_sum(v[q]);
+        if (lane == 0) sh[q][w] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double s = 0.0;
+        for (int i = 0; i < kRedThreads / 32; ++i) s += sh[q][i];
+        out[q] = s;
+    }
 }
 
 __global__ void k_bracket(const ReduceArgs a) {
@@ -94,7 +120,7 @@ __global__ void k_bracket(const ReduceArgs a) {
         a.partials[4 * (size_t)blockIdx.x] = smn[0];
         a.partials[4 * (size_t)blockIdx.x + 1] = smx[0];
     }
-    if (last_block(a.ticket)) {
+    if (last_block(a.ticket) && threadIdx.x == 0) {
         double lo = 1e300, hi = -1e300;
         for (int b = 0; b < gridDim.x; ++b) {
             lo = fmin(lo, __ldcg(a.partials + 4 * (size_t)b));
@@ -112,7 +138,10 @@ __global__ void k_bracket(const ReduceArgs a) {
 }
 
 // mode 0: N(lo); 1: N(hi) and the bracket check; 2: one bisection step; 3: scalars at mu_in.
-__global__ void k_count(const ReduceArgs a, int mode, double mu_in) {
+// One thread per pole (flattened [column][k]); poles more than 50 kT from x contribute their
+// limit (f = 1 below, 0 above) without an exponential: the neglected part is below e^-50 of
+// their weight, far under the rounding of the sums.
+__global__ void __launch_bounds__(kRedThreads) k_count(const ReduceArgs a, int mode, double mu_in) {
     BisectState* s = a.state;
     double x;
     if (mode == 2) {
@@ -122,27 +151,37 @@ __global__ void k_count(const ReduceArgs a, int mode, double mu_in) {
     else if (mode == 1) x = s->hi;
     else x = mu_in;
     double v[3] = {0.0, 0.0, 0.0};
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.M; j += gridDim.x * blockDim.x) {
-        const int nu = a.nu_eff[j];
-        const size_t b = (size_t)j * a.nu_max;
-        for (int k = 0; k < nu; ++k) {
-            const double e = a.eps[b + k], cc = a.c[b + k];
-            const double f2 = 2.0 * fermi((e - x) / a.kT);
-            v[0] += f2 * a.d[b + k] * cc;
-            if (mode == 3) {
-                v[1] += f2 * a.g[b + k] * cc;
-                v[2] += a.d[b + k] * cc * omega_w(e, x, a.kT);
-            }
+    const size_t total = (size_t)a.M * a.nu_max;
+    const double inv_kT = 1.0 / a.kT;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+         p += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(p / a.nu_max), k = (int)(p - (size_t)j * a.nu_max);
+        if (k >= __ldg(a.nu_eff + j)) continue;
+        const double e = a.eps[p], cc = a.c[p];
+        const double t = (e - x) * inv_kT;
+        double f2, om = 0.0;
+        if (t < -50.0) {
+            f2 = 2.0;
+            if (mode == 3) om = 2.0 * (e - x);
+        } else if (t > 50.0) {
+            continue;
+        } else {
+            f2 = 2.0 * fermi(t);
+            if (mode == 3) om = omega_w(e, x, a.kT);
+        }
+        const double dc = a.d[p] * cc;
+        v[0] = fma(f2, dc, v[0]);
+        if (mode == 3) {
+            v[1] = fma(f2 * a.g[p], cc, v[1]);
+            v[2] = fma(dc, om, v[2]);
         }
     }
     block_reduce_store<3>(v, a.partials, 4);
-    if (last_block(a.ticket)) {
-        double N = 0.0, E = 0.0, Om = 0.0;
-        for (int b = 0; b < gridDim.x; ++b) {
-            N += __ldcg(a.partials + 4 * (size_t)b);
-            E += __ldcg(a.partials + 4 * (size_t)b + 1);
-            Om += __ldcg(a.partials + 4 * (size_t)b + 2);
-        }
+    if (!last_block(a.ticket)) return;
+    double tot[3];
+    sum_partials<3>(a.partials, gridDim.x, tot);
+    if (threadIdx.x == 0) {
+        const double N = tot[0], E = tot[1], Om = tot[2];
         if (mode == 0) s->n_lo = N;
         else if (mode == 1) {
             s->n_hi = N;

@@ -269,6 +269,7 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
         ka.class_nu[c] = s->p.class_nu[c];
     }
     ka.breakdown_tol = s->p.breakdown_tol;
+    ka.onsite_diag = s->user_hs ? 0 : 1;   // Slater-Koster on-site blocks: S = I, H diagonal
     ka.na_max = s->na_max;
     ka.deg_max = s->max_nb;
     ka.scratch = s->kscratch.p;

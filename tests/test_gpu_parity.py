@@ -133,6 +133,23 @@ def test_batched_schedule_equals_plain(eg, d64):
     assert mu == d64["mu"] and e_band == d64["e_band"] and np.array_equal(gu.to_np(F), d64["F"])
 
 
+def test_user_supplied_hs_general_onsite_path(eg, d64):
+    """elses_set_hs takes the general path (full on-site blocks in the sparse products); with
+    the same H, S it must reproduce the Slater-Koster path to rounding."""
+    w = d64["w"]
+    s2 = eg.system_for(w)
+    H, S = s2.hs()
+    s2.set_hs(H, S)
+    s2.green_columns()
+    rho, _ = s2.density_matrix(d64["mu"])
+    assert np.abs(gu.to_np(rho) - d64["rho"]).max() <= gu.RHO_TOL
+    e = s2.energies(d64["mu"])
+    assert abs(e["E_band"] - d64["e_band"]) / w.n_atoms <= gu.E_TOL_PER_ATOM
+    with pytest.raises(eg.ElsesError) as err:
+        s2.energy_force()
+    assert err.value.code == -9
+
+
 # ----------------------------------------------------------------------------- full subspace
 @pytest.fixture(scope="module")
 def full(eg):
