@@ -164,6 +164,26 @@ int elses_reset_stats(elses_system sys);
  * every SM, timed with CUDA events. */
 int elses_probe_fp64(double* gflops_host, void* stream);
 
+/* Allocation-free chemical-potential bisection. The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they need mu -- an application
+ * whose own allocator has already reserved the device memory, or a loop in which allocation
+ * (and the synchronisation it implies) is not allowed. It runs the same bisection as
+ * elses_find_mu (same kernels, same result) on caller-owned spectra in the layout of
+ * elses_get_spectra: eps, c, d, g double[n_columns][nu_max] and nu_eff int[n_columns] on the
+ * device (g may be NULL unless e_band_host is requested); mu_tol <= 0 and max_bisect <= 0 take
+ * the defaults 1e-13 and 100. It calls no cudaMalloc / cudaFree: its scratch (block partial sums,
+ * bracket state, ticket) is one static device array of 4096 x 4 + 32 doubles (about 131 KB)
+ * that every GPU loading the library holds until exit; a device that would need more than
+ * 4096 reduction blocks is rejected with ELSES_ERR_CAPACITY. The first call on a device looks
+ * the array's address up (make that first call before any stream capture). All calls share the
+ * array and it keeps the last call's contents: calls that overlap on the GPU race and must be
+ * serialised by the caller. Synchronises `stream` before returning. */
+int elses_find_mu_static(int n_columns, int nu_max, const double* eps_dev, const double* c_dev,
+                         const double* d_dev, const double* g_dev, const int* nu_eff_dev,
+                         double kT, double n_electrons, double mu_tol, int max_bisect,
+                         double* mu_host, double* n_at_mu_host, double* e_band_host,
+                         void* stream);
+
 void elses_system_destroy(elses_system sys);
 const char* elses_last_error(void);
 int elses_version(void);

@@ -61,8 +61,8 @@ EXPORTS = (
     "elses_build_clusters", "elses_set_hs", "elses_green_columns", "elses_find_mu",
     "elses_density_matrix", "elses_energies", "elses_energy_force", "elses_get_pattern",
     "elses_get_hs", "elses_get_clusters", "elses_get_spectra", "elses_get_stats",
-    "elses_reset_stats", "elses_probe_fp64", "elses_system_destroy", "elses_last_error",
-    "elses_version",
+    "elses_reset_stats", "elses_probe_fp64", "elses_find_mu_static", "elses_system_destroy",
+    "elses_last_error", "elses_version",
 )
 
 _lib = None
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "elses_get_stats": [P, ctypes.POINTER(Stats)],
         "elses_reset_stats": [P],
         "elses_probe_fp64": [pD, V],
+        "elses_find_mu_static": [I, I, P, P, P, P, P, D, D, D, I, pD, pD, pD, V],
         "elses_system_destroy": [P],
         "elses_last_error": [],
         "elses_version": [],
@@ -281,6 +282,21 @@ def probe_fp64(stream=None) -> float:
     g = ctypes.c_double(0.0)
     _check(load_library().elses_probe_fp64(ctypes.byref(g), _stream(stream)))
     return g.value
+
+
+def find_mu_static(eps, c, d, nu_eff, kT, n_electrons, g=None, mu_tol=0.0, max_bisect=0,
+                   stream=None):
+    """elses_find_mu_static on CUDA tensors eps, c, d (float64 [M, nu_max]) and nu_eff (int32 [M]).
+
+    For callers that cannot allocate device memory: the library side allocates nothing (its
+    scratch is a static device array). Returns (mu, N(mu), E_band or None)."""
+    M, nm = eps.shape
+    mu, n, e = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load_library().elses_find_mu_static(
+        int(M), int(nm), _ptr(eps), _ptr(c), _ptr(d), _ptr(g), _ptr(nu_eff), float(kT),
+        float(n_electrons), float(mu_tol), int(max_bisect), ctypes.byref(mu), ctypes.byref(n),
+        ctypes.byref(e) if g is not None else None, _stream(stream)))
+    return mu.value, n.value, (e.value if g is not None else None)
 
 
 def system_for(workload, stream=None, **kw):

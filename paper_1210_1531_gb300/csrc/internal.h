@@ -25,6 +25,9 @@ void fill_lists(const double* pos, int n, const CellGrid& g, const int* cell_of,
                 const int* cell_start, const int* cell_atoms, double r, const int* ptr, int* idx,
                 int cap, int* status, cudaStream_t st);
 
+// Sets the thread-local message returned by elses_last_error and returns `code`.
+int report_error(int code, const char* fmt, ...);
+
 void check_finite(const double* x, int count, int* status, cudaStream_t st);
 int probe_fp64(double* gflops, cudaStream_t st);   // returns a cudaError_t value
 

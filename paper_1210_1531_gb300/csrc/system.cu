@@ -33,6 +33,18 @@ static int fail(int code, const char* fmt, ...) {
     return code;
 }
 
+namespace elses {
+int report_error(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+}  // namespace elses
+
 #define CUDA_TRY(x)                                                                        \
     do {                                                                                   \
         cudaError_t e_ = (x);                                                              \
