@@ -31,6 +31,9 @@ sys.path.insert(0, ROOT)
 METRIC = "Green's-fn columns/sec & energy+force steps/sec at |drho|<=1e-10, batched vs plain"
 WORKLOAD = "diamond_4096"
 FP64_NOMINAL_GFLOPS = 152 * 2 * 2 * 2.07     # SMs x FP64 FMA/clk/SM x 2 flops x GHz
+# DRAM bytes (read + write) of one k_krylov launch on the 4096-atom step, from the ncu capture in
+# profiles/k_krylov_diamond4096.md; valid only while krylov.cu is the source that was captured.
+KRYLOV_TRAFFIC = {"krylov_sha256_prefix": "66a1296f61c67c19", "bytes_per_launch": 155.9e9}
 
 
 def parse():
@@ -176,6 +179,13 @@ def krylov_flops(sys_g, w):
 
 
 # ----------------------------------------------------------------------------- our arm
+def krylov_traffic():
+    import hashlib
+    path = os.path.join(ROOT, "paper_1210_1531_gb300", "csrc", "krylov.cu")
+    h = hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    return KRYLOV_TRAFFIC["bytes_per_launch"] if h == KRYLOV_TRAFFIC["krylov_sha256_prefix"] else None
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -307,7 +317,8 @@ def run_ours(args):
             "gpu_launches": int(stats["launches"]),
             "roofline": {"bound": "alu", "kernel": "k_krylov (a3 Krylov build + a4 projection)",
                          "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
-                         "frac": achieved / FP64_NOMINAL_GFLOPS, "traffic": None,
+                         "frac": achieved / FP64_NOMINAL_GFLOPS,
+                         "traffic": krylov_traffic() if args.workload == WORKLOAD else None,
                          "peak_probe": peak_probe, "flops_per_launch": flops_per_launch,
                          "launch_ms": k_launch_ms,
                          "peak_note": "FP64 FMA pipe: 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s); peak_probe = measured FMA-chain throughput"},

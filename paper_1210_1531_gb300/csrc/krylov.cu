@@ -53,43 +53,59 @@ __device__ __forceinline__ double fma4(const double2 a0, const double2 a1, const
     return fma(a1.y, b1.y, fma(a1.x, b1.x, fma(a0.y, b0.y, fma(a0.x, b0.x, acc))));
 }
 
-// y = A x on the cluster (lane-owned rows; x gathered from shared memory). With `onsite` the
-// ELL holds only the off-site blocks and the on-site block is applied as a diagonal: `diag`
-// (4 values per position) or the identity when diag is null.
-__device__ __forceinline__ void spmv(const double* __restrict__ vals, const Ent* __restrict__ ell,
-                                     const int* __restrict__ ell_off, int NS, const double* x,
-                                     double* y, int lane, bool onsite, const double* diag) {
+// y = A x on the cluster (lane-owned rows; x gathered from shared memory). Each lane walks
+// one list holding the entries of all its rows in slot order (entry.p4 low 16 bits: neighbour
+// offset in x; high bits: the row's slot), so lanes stop after their own entry count instead of
+// after the widest row of every slot. Rows start from the on-site term: `diag` (4 values per
+// position), the identity when diag is null, or zero when the on-site block is a list entry.
+__device__ __forceinline__ void spmv(const double* __restrict__ vals, const Ent* __restrict__ ent,
+                                     int kmax, int NS, const double* x, double* y, int lane,
+                                     bool onsite, const double* diag) {
     for (int s = 0; s < NS; ++s) {
-        const int W = (ell_off[s + 1] - ell_off[s]) >> 5;
-        const Ent* es = ell + ell_off[s] + lane;
         const int po = 4 * (s * 32 + lane);
-        double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
+        double2 o01 = make_double2(0.0, 0.0), o23 = make_double2(0.0, 0.0);
         if (onsite) {
-            const double2 o01 = *reinterpret_cast<const double2*>(x + po);
-            const double2 o23 = *reinterpret_cast<const double2*>(x + po + 2);
+            o01 = *reinterpret_cast<const double2*>(x + po);
+            o23 = *reinterpret_cast<const double2*>(x + po + 2);
             if (diag) {
                 const double2 d01 = *reinterpret_cast<const double2*>(diag + po);
                 const double2 d23 = *reinterpret_cast<const double2*>(diag + po + 2);
-                y0 = d01.x * o01.x; y1 = d01.y * o01.y; y2 = d23.x * o23.x; y3 = d23.y * o23.y;
-            } else {
-                y0 = o01.x; y1 = o01.y; y2 = o23.x; y3 = o23.y;
+                o01.x *= d01.x; o01.y *= d01.y; o23.x *= d23.x; o23.y *= d23.y;
             }
         }
-        for (int k = 0; k < W; ++k) {
-            const Ent en = es[32 * k];
-            if (en.blk >= 0) {
-                const double2* b2 = reinterpret_cast<const double2*>(vals + 16 * (size_t)en.blk);
-                const double2 a0 = __ldg(b2 + 0), a1 = __ldg(b2 + 1), a2 = __ldg(b2 + 2), a3 = __ldg(b2 + 3);
-                const double2 a4 = __ldg(b2 + 4), a5 = __ldg(b2 + 5), a6 = __ldg(b2 + 6), a7 = __ldg(b2 + 7);
-                const double2 x01 = *reinterpret_cast<const double2*>(x + en.p4);
-                const double2 x23 = *reinterpret_cast<const double2*>(x + en.p4 + 2);
-                y0 = fma(a0.x, x01.x, fma(a0.y, x01.y, fma(a1.x, x23.x, fma(a1.y, x23.y, y0))));
-                y1 = fma(a2.x, x01.x, fma(a2.y, x01.y, fma(a3.x, x23.x, fma(a3.y, x23.y, y1))));
-                y2 = fma(a4.x, x01.x, fma(a4.y, x01.y, fma(a5.x, x23.x, fma(a5.y, x23.y, y2))));
-                y3 = fma(a6.x, x01.x, fma(a6.y, x01.y, fma(a7.x, x23.x, fma(a7.y, x23.y, y3))));
+        *reinterpret_cast<double2*>(y + po) = o01;
+        *reinterpret_cast<double2*>(y + po + 2) = o23;
+    }
+    int cur = -1;
+    double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
+    for (int k = 0; k < kmax; ++k) {
+        const Ent en = ent[32 * k + lane];
+        if (en.blk >= 0) {
+            const int s = en.p4 >> 16, p4 = en.p4 & 0xffff;
+            if (s != cur) {
+                if (cur >= 0) {
+                    double2* yo = reinterpret_cast<double2*>(y + 4 * (cur * 32 + lane));
+                    yo[0] = make_double2(y0, y1);
+                    yo[1] = make_double2(y2, y3);
+                }
+                cur = s;
+                const double2* yi = reinterpret_cast<const double2*>(y + 4 * (s * 32 + lane));
+                const double2 i01 = yi[0], i23 = yi[1];
+                y0 = i01.x; y1 = i01.y; y2 = i23.x; y3 = i23.y;
             }
+            const double2* b2 = reinterpret_cast<const double2*>(vals + 16 * (size_t)en.blk);
+            const double2 a0 = __ldg(b2 + 0), a1 = __ldg(b2 + 1), a2 = __ldg(b2 + 2), a3 = __ldg(b2 + 3);
+            const double2 a4 = __ldg(b2 + 4), a5 = __ldg(b2 + 5), a6 = __ldg(b2 + 6), a7 = __ldg(b2 + 7);
+            const double2 x01 = *reinterpret_cast<const double2*>(x + p4);
+            const double2 x23 = *reinterpret_cast<const double2*>(x + p4 + 2);
+            y0 = fma(a0.x, x01.x, fma(a0.y, x01.y, fma(a1.x, x23.x, fma(a1.y, x23.y, y0))));
+            y1 = fma(a2.x, x01.x, fma(a2.y, x01.y, fma(a3.x, x23.x, fma(a3.y, x23.y, y1))));
+            y2 = fma(a4.x, x01.x, fma(a4.y, x01.y, fma(a5.x, x23.x, fma(a5.y, x23.y, y2))));
+            y3 = fma(a6.x, x01.x, fma(a6.y, x01.y, fma(a7.x, x23.x, fma(a7.y, x23.y, y3))));
         }
-        double2* yo = reinterpret_cast<double2*>(y + po);
+    }
+    if (cur >= 0) {
+        double2* yo = reinterpret_cast<double2*>(y + 4 * (cur * 32 + lane));
         yo[0] = make_double2(y0, y1);
         yo[1] = make_double2(y2, y3);
     }
@@ -134,7 +150,7 @@ size_t krylov_smem_bytes(int na_max, int deg_max) {
     b += sizeof(double) * (size_t)kWarpsPerAtom * kMaxNu;            // CGS coefficients
     b += sizeof(double) * (size_t)na_max * 4;                        // on-site H diagonal
     b += sizeof(Ent) * (size_t)na_max * deg_max;                     // ELL
-    b += sizeof(int) * (size_t)(4 * na_max + na_max / 32 + 2);       // lists
+    b += sizeof(int) * (size_t)(5 * na_max + 2);                     // lists
     return (b + 15) & ~(size_t)15;
 }
 
@@ -150,8 +166,8 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
     int* deg = cl + NA;
     int* pos_of = deg + NA;
     int* atom_of_rank = pos_of + NA;
-    int* ell_off = atom_of_rank + NA;
-    __shared__ int sh_atom, sh_bad;
+    int* eoff = atom_of_rank + NA;        // first list entry of each position
+    __shared__ int sh_atom, sh_bad, sh_kmax;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int PK = a.nu_max * (a.nu_max + 1) / 2;
@@ -210,14 +226,23 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
             atom_of_rank[rank] = q < n_at ? q : -1 - (s * 32 + l);   // empty: encode its position
         }
         __syncthreads();
-        if (tid == 0) {
+        // per-lane lists: the entries of the lane's rows in slot order
+        if (tid < 32) {
             int off = 0;
-            for (int s = 0; s < NS; ++s) {
-                ell_off[s] = off;
-                off += 32 * deg[atom_of_rank[s * 32]];
+            for (int sl = 0; sl < NS; ++sl) {
+                const int pp = sl * 32 + tid;
+                // rank of position pp (inverse of the snake map)
+                const int l = (sl & 1) ? 31 - tid : tid;
+                const int q = atom_of_rank[sl * 32 + l];
+                eoff[pp] = off;
+                off += q >= 0 ? deg[q] : 0;
             }
-            ell_off[NS] = off;
-            sh_bad = off > NA * a.deg_max;
+            int kmax = off;
+            for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+            if (tid == 0) {
+                sh_kmax = kmax;
+                sh_bad = kmax * 32 > NA * a.deg_max;
+            }
         }
         __syncthreads();
         if (sh_bad) {
@@ -225,13 +250,14 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
             __syncthreads();
             continue;
         }
+        const int kmax = sh_kmax;
+        for (int q = tid; q < kmax * 32; q += kThreads) ell[q] = Ent{0, -1};
+        __syncthreads();
         for (int rank = tid; rank < NS * 32; rank += kThreads) {
             const int q = atom_of_rank[rank];
             const int p = q >= 0 ? pos_of[q] : -1 - q;
-            const int s = p >> 5, l = p & 31;
-            const int W = (ell_off[s + 1] - ell_off[s]) >> 5;
-            Ent* col = ell + ell_off[s] + l;
-            int k = 0;
+            const int sl = p >> 5, l = p & 31;
+            int k = eoff[p];
             double hd[4] = {0.0, 0.0, 0.0, 0.0};
             if (q >= 0) {
                 const int A = cl[q];
@@ -242,10 +268,9 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
                         continue;
                     }
                     const int b = bsearch_sorted(cl, n_at, ce);
-                    if (b >= 0) col[32 * (k++)] = Ent{4 * pos_of[b], e};
+                    if (b >= 0) ell[32 * (k++) + l] = Ent{(4 * pos_of[b]) | (sl << 16), e};
                 }
             }
-            for (; k < W; ++k) col[32 * k] = Ent{0, -1};
             for (int r = 0; r < 4; ++r) hdiag[4 * p + r] = hd[r];
         }
         __syncthreads();
@@ -276,7 +301,7 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
             __syncwarp();
             if (lane == 0) A[jp] = 1.0 / sqrt(sjj);
             __syncwarp();
-            spmv(a.S, ell, ell_off, NS, A, C, lane, onsite, nullptr);
+            spmv(a.S, ell, kmax, NS, A, C, lane, onsite, nullptr);
             for (int s = 0; s < NS; ++s) {
                 const int p = s * 32 + lane;
                 double2 x0, x1;
@@ -289,7 +314,7 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
 
             int nu_eff = nu;
             for (int n = 0; n < nu; ++n) {
-                spmv(a.H, ell, ell_off, NS, A, B, lane, onsite, hdiag);
+                spmv(a.H, ell, kmax, NS, A, B, lane, onsite, hdiag);
                 __syncwarp();
                 if (lane == 0) {
                     a.urow[(size_t)col * a.nu_max + n] = A[jp];
@@ -385,7 +410,7 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
                 }
                 __syncwarp();
                 // Sw and beta
-                spmv(a.S, ell, ell_off, NS, B, C, lane, onsite, nullptr);
+                spmv(a.S, ell, kmax, NS, B, C, lane, onsite, nullptr);
                 double part = 0.0;
                 for (int s = 0; s < NS; ++s) {
                     const int p = s * 32 + lane;
