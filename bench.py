@@ -144,41 +144,6 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- algorithmic flops
-def krylov_flops(sys_g, w):
-    """Algorithmic FP64 flops of the Krylov build + projection (a3, a4) over all columns.
-
-    Per column with n_c = 4 |C| orbitals, b_off off-site 4x4 blocks inside the cluster and
-    nu_eff steps (the on-site blocks of the Slater-Koster model are S = I and H diagonal):
-      sparse products  nu_eff with H (32 b_off + 4 |C|) and nu_eff with S (32 b_off)
-      projection + first CGS pass  sum_{n<nu} (3 dots of n+1 vectors + ||H u_n||^2) = (6(n+1)+2) n_c
-      CGS update, second pass, update, beta, scaling  sum_{n<nu-1} (6(n+1) + 4) n_c
-    """
-    import numpy as np
-    rp, ci = (t.cpu().numpy() for t in sys_g.pattern())
-    cp, cidx, _ = sys_g.clusters()
-    nu_eff = sys_g.spectra()["nu_eff"].cpu().numpy().reshape(-1, 4)
-    if cp is None:
-        n = w.n_atoms
-        clusters = [np.arange(n)] * n
-    else:
-        cp, cidx = cp.cpu().numpy(), cidx.cpu().numpy()
-        clusters = [cidx[cp[J]:cp[J + 1]] for J in range(w.n_atoms)]
-    total = 0.0
-    for J, C in enumerate(clusters):
-        inc = np.zeros(w.n_atoms, bool)
-        inc[C] = True
-        rows = np.concatenate([ci[rp[a]:rp[a + 1]] for a in C])
-        b_off = int(inc[rows].sum()) - len(C)
-        n_c = 4 * len(C)
-        for nu in nu_eff[J]:
-            nu = int(nu)
-            k = np.arange(1, nu + 1)
-            dense = float(np.sum(6 * k + 2) + np.sum(6 * k[:-1] + 4)) * n_c
-            total += nu * (64.0 * b_off + 4.0 * len(C)) + dense
-    return total
-
-
-# ----------------------------------------------------------------------------- our arm
 def krylov_traffic():
     import hashlib
     path = os.path.join(ROOT, "paper_1210_1531_gb300", "csrc", "krylov.cu")
@@ -225,7 +190,7 @@ def run_ours(args):
         return s.energy_force(forces)
 
     keys = ("launches", "krylov_launches", "t_krylov_ms", "t_eig_ms", "t_bisect_ms",
-            "t_density_ms", "t_force_ms")
+            "t_density_ms", "t_force_ms", "krylov_flops")
 
     def timed(s, k, w_steps, barrier=False):
         """w_steps untimed steps, then k steps each timed with CUDA events on the stream; the
@@ -267,9 +232,9 @@ def run_ours(args):
     mu, e_band, f_free, _ = out
 
     # kernel roofline of the dominant kernel (Krylov build + projection), event-timed per launch
-    flops = krylov_flops(batched, w)
+    # algorithmic flops counted by the kernel per column (formula in include/elses.h, elses_stats)
     k_launch_ms = stats["t_krylov_ms"] / max(1, stats["krylov_launches"])
-    flops_per_launch = flops / max(1.0, stats["krylov_launches"] / args.steps)
+    flops_per_launch = stats["krylov_flops"] / max(1.0, stats["krylov_launches"])
     achieved = flops_per_launch / (k_launch_ms * 1e-3) / 1e9      # GFLOP/s
     peak_probe = eg.probe_fp64()
 

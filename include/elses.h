@@ -93,6 +93,11 @@ typedef struct elses_stats {
     double t_bisect_ms;     /* bisection and scalar reductions (a7, a9)                      */
     double t_density_ms;    /* density-matrix kernels (a8)                                   */
     double t_force_ms;      /* force kernels (a10)                                           */
+    double krylov_flops;    /* algorithmic FP64 flops of the Krylov kernels (a3, a4): per column
+                               nu_eff sparse products with H and with S (2 flops per stored
+                               entry; on-site H diagonal 4 per atom, on-site S = I none) plus
+                               CGS2 and projection sum_{n<nu}(6(n+1)+2) n_c
+                               + sum_{n<nu-1}(6(n+1)+4) n_c, n_c = 4 |cluster|               */
 } elses_stats;
 
 typedef struct elses_system_s* elses_system;
@@ -140,6 +145,16 @@ int elses_energies(elses_system sys, double mu, double* n_host, double* e_band_h
  * device; may be NULL). Host outputs may be NULL. Passage: energy and force for MD from rho. */
 int elses_energy_force(elses_system sys, double* mu_host, double* e_band_host,
                        double* f_free_host, double* forces_dev, void* stream);
+
+/* (pi)COHP analysis, Eqs. 4-8: the ICOHP of each block e = (I, J) of the pattern,
+ * B_IJ = sum_ab H_(J,b);(I,a) rho_(I,a);(J,b) (the Fermi-weighted energy integral of the COHP of
+ * Eq. 4 taken by residues), and its sigma / pi parts from the Slater-Koster split of the off-site
+ * H (B = B_sigma + B_pi off-site; on-site blocks have B_sigma = B_pi = 0). sum over all blocks of
+ * B equals E_band (Eq. 6). rho_dev: double[nnzb][4][4] from elses_density_matrix. Outputs
+ * double[nnzb] device (B_sigma, B_pi may be NULL; they need the Slater-Koster H: ERR_STATE after
+ * elses_set_hs). Asynchronous on `stream`. */
+int elses_icohp(elses_system sys, const double* rho_dev, double* B_dev, double* Bsig_dev,
+                double* Bpi_dev, void* stream);
 
 /* Copy-out accessors: each copies library data into caller-owned device buffers (any of which
  * may be NULL to skip it) on `stream`; sizes are returned through the host pointers first

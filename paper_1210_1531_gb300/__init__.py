@@ -54,12 +54,13 @@ class Stats(ctypes.Structure):
                 ("krylov_launches", ctypes.c_longlong), ("bisect_steps", ctypes.c_int),
                 ("pad", ctypes.c_int), ("t_krylov_ms", ctypes.c_double),
                 ("t_eig_ms", ctypes.c_double), ("t_bisect_ms", ctypes.c_double),
-                ("t_density_ms", ctypes.c_double), ("t_force_ms", ctypes.c_double)]
+                ("t_density_ms", ctypes.c_double), ("t_force_ms", ctypes.c_double),
+                ("krylov_flops", ctypes.c_double)]
 
 
 EXPORTS = (
     "elses_build_clusters", "elses_set_hs", "elses_green_columns", "elses_find_mu",
-    "elses_density_matrix", "elses_energies", "elses_energy_force", "elses_get_pattern",
+    "elses_density_matrix", "elses_energies", "elses_energy_force", "elses_icohp", "elses_get_pattern",
     "elses_get_hs", "elses_get_clusters", "elses_get_spectra", "elses_get_stats",
     "elses_reset_stats", "elses_probe_fp64", "elses_find_mu_static", "elses_system_destroy",
     "elses_last_error", "elses_version",
@@ -86,6 +87,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "elses_density_matrix": [P, D, P, P, V],
         "elses_energies": [P, D, pD, pD, pD, pD, V],
         "elses_energy_force": [P, pD, pD, pD, P, V],
+        "elses_icohp": [P, P, P, P, P, V],
         "elses_get_pattern": [P, pI, P, P, V],
         "elses_get_hs": [P, P, P, V],
         "elses_get_clusters": [P, pLL, pI, P, P, V],
@@ -217,6 +219,14 @@ class System:
         _check(self._L.elses_energy_force(self._h, ctypes.byref(mu), ctypes.byref(e), ctypes.byref(f),
                                           _ptr(forces), _stream(stream)))
         return mu.value, e.value, f.value, forces
+
+    def icohp(self, rho, stream=None):
+        """(pi)COHP integrals per pattern block: (B, B_sigma, B_pi), CUDA float64 [nnzb] each."""
+        B = torch.empty(self.nnzb, dtype=torch.float64, device="cuda")
+        Bs, Bp = torch.empty_like(B), torch.empty_like(B)
+        _check(self._L.elses_icohp(self._h, _ptr(rho.contiguous()), _ptr(B), _ptr(Bs), _ptr(Bp),
+                                   _stream(stream)))
+        return B, Bs, Bp
 
     # ------------------------------------------------------------------ accessors (copies)
     def pattern(self, stream=None):

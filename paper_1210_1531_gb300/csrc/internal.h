@@ -38,6 +38,8 @@ void sk_build(const double* pos, int n, const double L[3], const SKDev& sk, cons
 void forces(const double* pos, int n, const double L[3], const SKDev& sk, const int* row_ptr,
             const int* col_idx, const int* row_of, const int* tmap, int nnzb, const double* rho,
             const double* rhoE, double* g_block, double* F, cudaStream_t st);
+void icohp(const double* pos, const double L[3], const SKDev& sk, const int* col_idx, const int* row_of,
+           int nnzb, const double* H, const double* rho, double* B, double* Bsig, double* Bpi, cudaStream_t st);
 
 // ---------------------------------------------------------------- a3, a4 (krylov.cu)
 struct KrylovArgs {
@@ -70,6 +72,7 @@ struct KrylovArgs {
     double* UP;             // pattern rows of U: [(e*4 + alpha)*4 + r][nu_max], e - up_block0
     int up_block0;
     int* status;
+    unsigned long long* flops;   // algorithmic FP64 flops of the columns, accumulated
 };
 size_t krylov_smem_bytes(int na_max, int deg_max);
 int krylov_blocks_per_sm(int na_max, int deg_max);

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
     int* pos_of = deg + NA;
     int* atom_of_rank = pos_of + NA;
     int* eoff = atom_of_rank + NA;        // first list entry of each position
-    __shared__ int sh_atom, sh_bad, sh_kmax;
+    __shared__ int sh_atom, sh_bad, sh_kmax, sh_nent;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int PK = a.nu_max * (a.nu_max + 1) / 2;
@@ -237,9 +237,13 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
                 eoff[pp] = off;
                 off += q >= 0 ? deg[q] : 0;
             }
-            int kmax = off;
-            for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+            int kmax = off, ntot = off;
+            for (int o = 16; o > 0; o >>= 1) {
+                kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+                ntot += __shfl_xor_sync(0xffffffffu, ntot, o);
+            }
             if (tid == 0) {
+                sh_nent = ntot;
                 sh_kmax = kmax;
                 sh_bad = kmax * 32 > NA * a.deg_max;
             }
@@ -448,6 +452,18 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
             if (lane == 0) {
                 a.nu_eff[j] = nu_eff;
                 if (nu_eff < nu) flag(a.status, DEV_BREAKDOWN);
+                if (a.flops) {
+                    // sparse products: nu_eff with H (2 flops per stored entry, 4 per atom on-site
+                    // when diagonal) and nu_eff with S (identity on-site: no flops); dense CGS2 +
+                    // projection: sum_{n<nu}(6(n+1)+2) n_c + sum_{n<nu-1}(6(n+1)+4) n_c
+                    const unsigned long long nent = (unsigned long long)sh_nent;
+                    const unsigned long long nc = 4ull * n_at, v = (unsigned long long)nu_eff;
+                    const unsigned long long spm = onsite ? v * (64ull * nent + 4ull * n_at) : v * 64ull * nent;
+                    const unsigned long long tri = v * (v + 1) / 2;          // sum_{n<v} (n+1)
+                    const unsigned long long trim = v > 0 ? (v - 1) * v / 2 : 0;  // sum_{n<v-1} (n+1)
+                    const unsigned long long dense = nc * (6 * tri + 2 * v) + (v > 0 ? nc * (6 * trim + 4 * (v - 1)) : 0);
+                    atomicAdd(a.flops, spm + dense);
+                }
             }
             __syncwarp();
             // pattern rows of U for rho / G: blocks e = (J, I) of row J, orbital r of atom I

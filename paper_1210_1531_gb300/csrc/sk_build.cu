@@ -131,4 +131,45 @@ void forces(const double* pos, int n, const double L[3], const SKDev& sk, const 
     k_force_atoms<<<(n + T - 1) / T, T, 0, st>>>(n, row_ptr, tmap, g_block, F);
 }
 
+// (pi)COHP integrals of Eqs. 4-8 per block e = (I, J): B = sum_ab H[e][a][b] rho[e][a][b] (H is
+// symmetric, so H_(J,b);(I,a) = H[e][a][b]); the pi part takes only the V_pp_pi (delta_ik - u_i u_k)
+// term of the p-p block, sigma = B - pi off-site; on-site blocks carry no split.
+__global__ void k_icohp(const double* __restrict__ pos, double Lx, double Ly, double Lz, SKDev sk,
+                        const int* __restrict__ col_idx, const int* __restrict__ row_of, int nnzb,
+                        const double* __restrict__ H, const double* __restrict__ rho,
+                        double* __restrict__ B, double* __restrict__ Bsig, double* __restrict__ Bpi) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nnzb) return;
+    double b = 0.0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) b = fma(H[16 * (size_t)e + q], rho[16 * (size_t)e + q], b);
+    B[e] = b;
+    if (!Bsig && !Bpi) return;
+    const int I = row_of[e], J = col_idx[e];
+    double bpi = 0.0;
+    if (I != J) {
+        const double dx = min_image(pos[3 * J] - pos[3 * I], Lx);
+        const double dy = min_image(pos[3 * J + 1] - pos[3 * I + 1], Ly);
+        const double dz = min_image(pos[3 * J + 2] - pos[3 * I + 2], Lz);
+        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+        const double u[3] = {dx / r, dy / r, dz / r};
+        double V[4], dV[4];
+        sk_radial(sk, sk.V0, sk.qH, r, V, dV);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                bpi = fma(V[3] * ((i == k ? 1.0 : 0.0) - u[i] * u[k]), rho[16 * (size_t)e + 4 * (1 + i) + 1 + k], bpi);
+    }
+    if (Bpi) Bpi[e] = bpi;
+    if (Bsig) Bsig[e] = (I != J) ? b - bpi : 0.0;
+}
+
+void icohp(const double* pos, const double L[3], const SKDev& sk, const int* col_idx, const int* row_of,
+           int nnzb, const double* H, const double* rho, double* B, double* Bsig, double* Bpi, cudaStream_t st) {
+    const int T = 256;
+    k_icohp<<<(nnzb + T - 1) / T, T, 0, st>>>(pos, L[0], L[1], L[2], sk, col_idx, row_of, nnzb, H, rho, B,
+                                              Bsig, Bpi);
+}
+
 }  // namespace elses

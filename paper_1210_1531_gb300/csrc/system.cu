@@ -96,6 +96,7 @@ struct elses_system_s {
     DevBuf<int> row_cnt, row_ptr, col_idx, row_of, tmap;
     DevBuf<int> cl_cnt, cl_ptr, cl_idx;
     DevBuf<int> counters;   // [0] max neighbours, [1] max cluster, [2] status, [3] queue
+    DevBuf<unsigned long long> flops_ctr;
     DevBuf<double> H, S;
     int nnzb = 0, max_nb = 0, max_cl = 0;
     long long cl_total = 0;
@@ -292,6 +293,7 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
     ka.hurow = s->hurow.p;
     ka.nu_eff = s->nu_eff.p;
     ka.status = s->counters.p + 2;
+    ka.flops = s->flops_ctr.p;
     if (stored) {
         ka.UP = s->UP.p;
         ka.up_block0 = 0;
@@ -404,6 +406,7 @@ void elses_system_destroy(elses_system s) {
                              &s->V, &s->UP, &s->Vb, &s->UPb, &s->rho, &s->rhoE, &s->gblock,
                              &s->partials, &s->zbuf};
     for (auto* b : dbs) b->release();
+    s->flops_ctr.release();
     DevBuf<int>* ibs[] = {&s->cell_of, &s->cell_count, &s->cell_start, &s->cursor, &s->cell_atoms,
                           &s->row_cnt, &s->row_ptr, &s->col_idx, &s->row_of, &s->tmap, &s->cl_cnt,
                           &s->cl_ptr, &s->cl_idx, &s->counters, &s->nu_eff, &s->order, &s->erot_n,
@@ -473,6 +476,8 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
     CUDA_TRY(cudaMemcpyAsync(s->pos.p, pos_dev, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st));
     TRY(s->counters.ensure(8));
     CUDA_TRY(cudaMemsetAsync(s->counters.p, 0, sizeof(int) * 8, st));
+    TRY(s->flops_ctr.ensure(1));
+    CUDA_TRY(cudaMemsetAsync(s->flops_ctr.p, 0, sizeof(unsigned long long), st));
     check_finite(s->pos.p, 3 * n, s->counters.p + 2, st);
     s->stats.launches++;
     {
@@ -771,6 +776,19 @@ int elses_energy_force(elses_system s, double* mu_host, double* e_band_host, dou
     return warn > 0 ? warn : rc;
 }
 
+int elses_icohp(elses_system s, const double* rho_dev, double* B_dev, double* Bsig_dev, double* Bpi_dev,
+                void* stream) {
+    TRY(check_built(s));
+    if (!rho_dev || !B_dev) return fail(ELSES_ERR_ARG, "null rho or B");
+    if ((Bsig_dev || Bpi_dev) && s->user_hs)
+        return fail(ELSES_ERR_STATE, "the sigma / pi split needs the Slater-Koster H");
+    icohp(s->pos.p, s->box, s->skd, s->col_idx.p, s->row_of.p, s->nnzb, s->H.p, rho_dev, B_dev, Bsig_dev,
+          Bpi_dev, (cudaStream_t)stream);
+    s->stats.launches++;
+    CUDA_TRY(cudaGetLastError());
+    return ELSES_OK;
+}
+
 int elses_get_pattern(elses_system s, int* nnzb_host, int* row_ptr_dev, int* col_idx_dev, void* stream) {
     TRY(check_built(s));
     cudaStream_t st = (cudaStream_t)stream;
@@ -822,6 +840,11 @@ int elses_get_spectra(elses_system s, int* nu_max_host, double* eps_dev, double*
 int elses_get_stats(elses_system s, elses_stats* out) {
     if (!s || !out) return fail(ELSES_ERR_ARG, "null argument");
     *out = s->stats;
+    if (s->flops_ctr.p) {
+        unsigned long long f = 0;
+        CUDA_TRY(cudaMemcpy(&f, s->flops_ctr.p, sizeof f, cudaMemcpyDeviceToHost));
+        out->krylov_flops = (double)f;
+    }
     return ELSES_OK;
 }
 
@@ -829,6 +852,7 @@ int elses_reset_stats(elses_system s) {
     if (!s) return fail(ELSES_ERR_ARG, "null system");
     s->collect();
     s->stats = elses_stats{};
+    if (s->flops_ctr.p) CUDA_TRY(cudaMemset(s->flops_ctr.p, 0, sizeof(unsigned long long)));
     return ELSES_OK;
 }
 

@@ -311,3 +311,14 @@ def test_errors_are_reported(eg):
     with pytest.raises(eg.ElsesError) as e:
         s2.find_mu()
     assert e.value.code == -9
+
+
+def test_icohp_matches_oracle_and_sums_to_band_energy(eg, d64):
+    """(pi)COHP on the GPU (Eqs. 4-8) against the oracle on the same rho; sum B = E_band (Eq. 6)."""
+    from oracle import cohp
+    w = d64["w"]
+    rho = torch.tensor(d64["rho"], device="cuda")
+    B, Bs, Bp = (gu.to_np(t) for t in d64["sys"].icohp(rho))
+    Bo, Bso, Bpo = cohp.icohp(w.pos, w.box, w.sk, d64["rp"], d64["ci"], d64["rho"])
+    assert np.abs(B - Bo).max() < 1e-12 and np.abs(Bs - Bso).max() < 1e-12 and np.abs(Bp - Bpo).max() < 1e-12
+    assert abs(B.sum() - d64["e_band"]) / w.n_atoms < 1e-9

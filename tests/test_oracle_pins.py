@@ -366,3 +366,20 @@ def test_composite_columns_are_well_conditioned():
             c = V.T @ kc.U[jl, :]
             rhos.append((kc.U @ V) @ (2 * physics.fermi(e, -1.0, 0.1) * c))
         assert np.abs(rhos[0] - rhos[1]).max() < 1e-10
+
+
+def test_icohp_pi_part_equals_pp_pi_only_hamiltonian(diamond64):
+    """Eqs. 7-8: the pi part of the off-site H is the V_pp_pi term alone; building H with every
+    other integral switched off (an independent path through the block function) must give the
+    same pi ICOHP, and the sigma part the rest."""
+    w = diamond64
+    res = pipeline.run(w)
+    rp, ci = res["row_ptr"], res["col_idx"]
+    B, Bs, Bp = cohp.icohp(w.pos, w.box, w.sk, rp, ci, res["rho"])
+    pi_only = dataclasses.replace(w.sk, V0=(0.0, 0.0, 0.0, w.sk.V0[3]))
+    Hpi, _ = hamiltonian.bsr_values(w.pos, w.box, pi_only, rp, ci)
+    rows = np.repeat(np.arange(w.n_atoms), np.diff(rp))
+    off = rows != ci
+    Bp_ref = np.einsum("eab,eab->e", Hpi, res["rho"])
+    assert np.abs(Bp[off] - Bp_ref[off]).max() < 1e-12
+    assert np.abs(Bp[~off]).max() == 0.0 and np.abs(Bs[~off]).max() == 0.0
