@@ -79,6 +79,8 @@ typedef struct elses_params {
     int    schedule;        /* 0: plain (persistent CTAs, static atom order), 1: batched
                                (persistent CTAs pulling atoms from a cluster-size-sorted queue) */
     int    timing;          /* 1: time the kernels of each call with CUDA events (elses_stats) */
+    int    k3_ctas_per_sm;  /* resident Krylov CTAs per SM (0: as many as fit); fewer CTAs keep
+                               more of the per-CTA Krylov bases in L2                            */
 } elses_params;
 
 /* Counters and event timings of the calls since the last build (timing = 1 for the times). */
@@ -87,7 +89,7 @@ typedef struct elses_stats {
     long long columns;      /* columns solved (a3-a6)                                        */
     long long krylov_launches;
     int bisect_steps;       /* steps of the last bisection                                   */
-    int pad;
+    int k3_ctas_per_sm;     /* resident Krylov CTAs per SM of the launch shape in use          */
     double t_krylov_ms;     /* Krylov build + projection kernels (a3, a4)                    */
     double t_eig_ms;        /* projected eigenproblem kernels (a5, a6)                       */
     double t_bisect_ms;     /* bisection and scalar reductions (a7, a9)                      */
@@ -145,6 +147,11 @@ int elses_energies(elses_system sys, double mu, double* n_host, double* e_band_h
  * device; may be NULL). Host outputs may be NULL. Passage: energy and force for MD from rho. */
 int elses_energy_force(elses_system sys, double* mu_host, double* e_band_host,
                        double* f_free_host, double* forces_dev, void* stream);
+
+/* a10 alone: forces F_I = -dF_free/dR_I (double[N][3] device) from the rho and rhoE kept by the
+ * last elses_energy_force on the current positions (the adjoint dF/dH = rho, dF/dS = -rhoE
+ * chained with the Slater-Koster dH/dR, dS/dR); ERR_STATE if there are none. Asynchronous. */
+int elses_forces(elses_system sys, double* forces_dev, void* stream);
 
 /* (pi)COHP analysis, Eqs. 4-8: the ICOHP of each block e = (I, J) of the pattern,
  * B_IJ = sum_ab H_(J,b);(I,a) rho_(I,a);(J,b) (the Fermi-weighted energy integral of the COHP of

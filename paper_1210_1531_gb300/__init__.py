@@ -46,13 +46,13 @@ class Params(ctypes.Structure):
                 ("two_pass", ctypes.c_int), ("n_classes", ctypes.c_int),
                 ("class_max_atoms", ctypes.c_int * 4), ("class_nu", ctypes.c_int * 4),
                 ("max_neighbors", ctypes.c_int), ("max_cluster", ctypes.c_int),
-                ("schedule", ctypes.c_int), ("timing", ctypes.c_int)]
+                ("schedule", ctypes.c_int), ("timing", ctypes.c_int), ("k3_ctas_per_sm", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("columns", ctypes.c_longlong),
                 ("krylov_launches", ctypes.c_longlong), ("bisect_steps", ctypes.c_int),
-                ("pad", ctypes.c_int), ("t_krylov_ms", ctypes.c_double),
+                ("k3_ctas_per_sm", ctypes.c_int), ("t_krylov_ms", ctypes.c_double),
                 ("t_eig_ms", ctypes.c_double), ("t_bisect_ms", ctypes.c_double),
                 ("t_density_ms", ctypes.c_double), ("t_force_ms", ctypes.c_double),
                 ("krylov_flops", ctypes.c_double)]
@@ -60,7 +60,8 @@ class Stats(ctypes.Structure):
 
 EXPORTS = (
     "elses_build_clusters", "elses_set_hs", "elses_green_columns", "elses_find_mu",
-    "elses_density_matrix", "elses_energies", "elses_energy_force", "elses_icohp", "elses_get_pattern",
+    "elses_density_matrix", "elses_energies", "elses_energy_force", "elses_forces", "elses_icohp",
+    "elses_get_pattern",
     "elses_get_hs", "elses_get_clusters", "elses_get_spectra", "elses_get_stats",
     "elses_reset_stats", "elses_probe_fp64", "elses_find_mu_static", "elses_system_destroy",
     "elses_last_error", "elses_version",
@@ -88,6 +89,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "elses_energies": [P, D, pD, pD, pD, pD, V],
         "elses_energy_force": [P, pD, pD, pD, P, V],
         "elses_icohp": [P, P, P, P, P, V],
+        "elses_forces": [P, P, V],
         "elses_get_pattern": [P, pI, P, P, V],
         "elses_get_hs": [P, P, P, V],
         "elses_get_clusters": [P, pLL, pI, P, P, V],
@@ -139,7 +141,7 @@ def make_sk(p) -> SK:
 
 def make_params(r_cluster, nu, kT, n_electrons, two_pass=False, nu_classes=(), schedule=0,
                 max_neighbors=0, max_cluster=0, breakdown_tol=0.0, mu_tol=0.0,
-                max_bisect=0, timing=False) -> Params:
+                max_bisect=0, timing=False, k3_ctas_per_sm=0) -> Params:
     p = Params()
     p.r_cluster, p.kT, p.n_electrons = float(r_cluster), float(kT), float(n_electrons)
     p.breakdown_tol, p.mu_tol = float(breakdown_tol), float(mu_tol)
@@ -150,6 +152,7 @@ def make_params(r_cluster, nu, kT, n_electrons, two_pass=False, nu_classes=(), s
         p.class_nu[c] = int(cnu)
     p.max_neighbors, p.max_cluster, p.schedule = int(max_neighbors), int(max_cluster), int(schedule)
     p.timing = int(bool(timing))
+    p.k3_ctas_per_sm = int(k3_ctas_per_sm)
     return p
 
 
@@ -158,14 +161,15 @@ class System:
 
     def __init__(self, pos, box, sk, r_cluster, nu, kT, n_electrons, two_pass=False,
                  nu_classes=(), schedule=0, max_neighbors=0, max_cluster=0, timing=False,
-                 stream=None):
+                 k3_ctas_per_sm=0, stream=None):
         self._L = load_library()
         self._h = ctypes.c_void_p(None)
         self.n = int(pos.shape[0])
         self.M = 4 * self.n
         self.sk = make_sk(sk)
         self.params = make_params(r_cluster, nu, kT, n_electrons, two_pass, nu_classes, schedule,
-                                  max_neighbors, max_cluster, timing=timing)
+                                  max_neighbors, max_cluster, timing=timing,
+                                  k3_ctas_per_sm=k3_ctas_per_sm)
         self.box = (ctypes.c_double * 3)(*[float(b) for b in box])
         self.rebuild(pos, stream)
 
@@ -220,6 +224,12 @@ class System:
                                           _ptr(forces), _stream(stream)))
         return mu.value, e.value, f.value, forces
 
+    def forces(self, out=None, stream=None):
+        """a10 alone (elses_forces) from the rho of the last energy_force: CUDA float64 [N, 3]."""
+        out = torch.empty((self.n, 3), dtype=torch.float64, device="cuda") if out is None else out
+        _check(self._L.elses_forces(self._h, _ptr(out), _stream(stream)))
+        return out
+
     def icohp(self, rho, stream=None):
         """(pi)COHP integrals per pattern block: (B, B_sigma, B_pi), CUDA float64 [nnzb] each."""
         B = torch.empty(self.nnzb, dtype=torch.float64, device="cuda")
@@ -270,7 +280,7 @@ class System:
     def stats(self):
         st = Stats()
         _check(self._L.elses_get_stats(self._h, ctypes.byref(st)))
-        return {name: getattr(st, name) for name, _ in Stats._fields_ if name != "pad"}
+        return {name: getattr(st, name) for name, _ in Stats._fields_}
 
     def reset_stats(self):
         _check(self._L.elses_reset_stats(self._h))
@@ -285,6 +295,37 @@ class System:
             self.close()
         except Exception:
             pass
+
+
+class FreeEnergy(torch.autograd.Function):
+    """F_free(R) = Omega + mu N_e of a System at positions R, differentiable in R.
+
+    forward: rebuild at R, then the whole path through elses_energy_force without forces;
+    backward: the library's adjoint kernels (elses_forces: dF/dH = rho, dF/dS = -rhoE chained
+    with dH/dR, dS/dR), grad_R = -F * grad_out. Returns (F_free, E_band); E_band is not
+    differentiable."""
+
+    @staticmethod
+    def forward(ctx, pos, system):
+        system.rebuild(pos.detach().contiguous())
+        mu = ctypes.c_double(0.0)
+        e, f = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        _check(system._L.elses_energy_force(system._h, ctypes.byref(mu), ctypes.byref(e),
+                                            ctypes.byref(f), None, _stream(None)))
+        ctx.system = system
+        e_band = pos.new_tensor(e.value)
+        ctx.mark_non_differentiable(e_band)
+        return pos.new_tensor(f.value), e_band
+
+    @staticmethod
+    def backward(ctx, grad_f, grad_e):
+        forces = ctx.system.forces()
+        return -forces * grad_f, None
+
+
+def free_energy(pos, system):
+    """Differentiable (F_free, E_band) of `system` at CUDA float64 positions `pos` [N, 3]."""
+    return FreeEnergy.apply(pos, system)
 
 
 def probe_fp64(stream=None) -> float:

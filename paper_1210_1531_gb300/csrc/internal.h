@@ -51,7 +51,8 @@ struct KrylovArgs {
     const int* cl_ptr;      // nullptr: every cluster is the whole system
     const int* cl_idx;
     int atom_begin, atom_end;
-    const int* order;       // optional: atoms of the batch in processing order (batched form)
+    const int* order;       // atoms of this launch in processing order (n_items of them)
+    int n_items;
     int* queue;             // optional: work counter of the persistent queue (batched form)
     int nu_max;             // allocation stride of per-column Krylov arrays
     int nu_default;

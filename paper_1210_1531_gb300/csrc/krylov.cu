@@ -53,24 +53,25 @@ __device__ __forceinline__ double fma4(const double2 a0, const double2 a1, const
     return fma(a1.y, b1.y, fma(a1.x, b1.x, fma(a0.y, b0.y, fma(a0.x, b0.x, acc))));
 }
 
-// y = A x on the cluster (lane-owned rows; x gathered from shared memory). Each lane walks
-// one list holding the entries of all its rows in slot order (entry.p4 low 16 bits: neighbour
-// offset in x; high bits: the row's slot), so lanes stop after their own entry count instead of
-// after the widest row of every slot. Rows start from the on-site term: `diag` (4 values per
-// position), the identity when diag is null, or zero when the on-site block is a list entry.
+// y = A x on the cluster (lane-owned rows; x gathered from shared memory, y in shared or global
+// memory). Each lane walks one list holding the entries of all its rows in slot order
+// (entry.p4 low 16 bits: neighbour offset in x; high bits: the row's slot), so lanes stop after
+// their own entry count instead of after the widest row of every slot. Rows start from the
+// on-site term: the diagonal of the on-site block of `dvals` (block index eself[p]), the
+// identity when dvals is null, or zero when the on-site block is a list entry.
 __device__ __forceinline__ void spmv(const double* __restrict__ vals, const Ent* __restrict__ ent,
                                      int kmax, int NS, const double* x, double* y, int lane,
-                                     bool onsite, const double* diag) {
+                                     bool onsite, const double* __restrict__ dvals, const int* eself) {
     for (int s = 0; s < NS; ++s) {
-        const int po = 4 * (s * 32 + lane);
+        const int p = s * 32 + lane, po = 4 * p;
         double2 o01 = make_double2(0.0, 0.0), o23 = make_double2(0.0, 0.0);
         if (onsite) {
             o01 = *reinterpret_cast<const double2*>(x + po);
             o23 = *reinterpret_cast<const double2*>(x + po + 2);
-            if (diag) {
-                const double2 d01 = *reinterpret_cast<const double2*>(diag + po);
-                const double2 d23 = *reinterpret_cast<const double2*>(diag + po + 2);
-                o01.x *= d01.x; o01.y *= d01.y; o23.x *= d23.x; o23.y *= d23.y;
+            const int es = eself[p];
+            if (dvals && es >= 0) {
+                const double* d = dvals + 16 * (size_t)es;
+                o01.x *= __ldg(d); o01.y *= __ldg(d + 5); o23.x *= __ldg(d + 10); o23.y *= __ldg(d + 15);
             }
         }
         *reinterpret_cast<double2*>(y + po) = o01;
@@ -126,13 +127,13 @@ __device__ __forceinline__ void st4(double* p, const double2 a, const double2 b)
 // fetched eight at a time before they are used, so their latency overlaps.
 __device__ __forceinline__ void sub_basis(const double* Ub, int NP, int p, const double* h, int n,
                                           double2& w0, double2& w1) {
-    for (int k0 = 0; k0 <= n; k0 += 8) {
-        double2 ua[8], ub[8];
+    for (int k0 = 0; k0 <= n; k0 += 6) {
+        double2 ua[6], ub[6];
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk)
+        for (int kk = 0; kk < 6; ++kk)
             if (k0 + kk <= n) ld4(Ub + 4 * ((size_t)(k0 + kk) * NP + p), ua[kk], ub[kk]);
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
+        for (int kk = 0; kk < 6; ++kk) {
             if (k0 + kk <= n) {
                 const double hk = h[k0 + kk];
                 w0.x = fma(-ua[kk].x, hk, w0.x);
@@ -144,29 +145,45 @@ __device__ __forceinline__ void sub_basis(const double* Ub, int NP, int p, const
     }
 }
 
+// Sum of 16 values held by every lane over the 32 lanes (recursive halving on lane bits 3..0,
+// then one exchange across bit 4): lanes l and l + 16 end with the sum of value l & 15.
+__device__ __forceinline__ double warp_sum16(double (&v)[16]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int w = 8; w >= 1; w >>= 1) {
+        const bool upper = (lane & w) != 0;
+#pragma unroll
+        for (int i = 0; i < w; ++i) {
+            double send = upper ? v[i] : v[i + w];
+            double keep = upper ? v[i + w] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+}
+
 size_t krylov_smem_bytes(int na_max, int deg_max) {
     size_t b = 0;
-    b += sizeof(double) * (size_t)kWarpsPerAtom * 3 * na_max * 4;   // u, hu/w, su per warp
+    b += sizeof(double) * (size_t)kWarpsPerAtom * 2 * na_max * 4;   // u and hu / w per warp
     b += sizeof(double) * (size_t)kWarpsPerAtom * kMaxNu;            // CGS coefficients
-    b += sizeof(double) * (size_t)na_max * 4;                        // on-site H diagonal
     b += sizeof(Ent) * (size_t)na_max * deg_max;                     // ELL
-    b += sizeof(int) * (size_t)(5 * na_max + 2);                     // lists
+    b += sizeof(int) * (size_t)(6 * na_max + 2);                     // lists
     return (b + 15) & ~(size_t)15;
 }
 
-__global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k_krylov(const KrylovArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int NA = a.na_max;
     double* vec = reinterpret_cast<double*>(smem_raw);
-    double* hbuf = vec + (size_t)kWarpsPerAtom * 3 * NA * 4;
-    double* hdiag = hbuf + kWarpsPerAtom * kMaxNu;
-    Ent* ell = reinterpret_cast<Ent*>(hdiag + (size_t)NA * 4);
+    double* hbuf = vec + (size_t)kWarpsPerAtom * 2 * NA * 4;
+    Ent* ell = reinterpret_cast<Ent*>(hbuf + kWarpsPerAtom * kMaxNu);
     const bool onsite = a.onsite_diag != 0;
     int* cl = reinterpret_cast<int*>(ell + (size_t)NA * a.deg_max);
     int* deg = cl + NA;
     int* pos_of = deg + NA;
     int* atom_of_rank = pos_of + NA;
     int* eoff = atom_of_rank + NA;        // first list entry of each position
+    int* eself = eoff + NA;               // on-site block of each position (-1: none)
     __shared__ int sh_atom, sh_bad, sh_kmax, sh_nent;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -174,13 +191,13 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
     const size_t warp_scratch = (size_t)2 * a.nu_max * NA * 4;
     double* Uw = a.scratch + (size_t)blockIdx.x * kWarpsPerAtom * warp_scratch + (size_t)warp * warp_scratch;
     double* SUw = Uw + (size_t)a.nu_max * NA * 4;
-    const int n_batch = a.atom_end - a.atom_begin;
+    const int n_batch = a.n_items;
 
     for (int iter = 0;; ++iter) {
         if (tid == 0) {
             const int idx = a.queue ? atomicAdd(a.queue, 1) : blockIdx.x + iter * gridDim.x;
             int atom = -1;
-            if (idx < n_batch) atom = a.order ? a.order[idx] : a.atom_begin + idx;
+            if (idx < n_batch) atom = a.order[idx];
             sh_atom = atom;
         }
         __syncthreads();
@@ -262,20 +279,20 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
             const int p = q >= 0 ? pos_of[q] : -1 - q;
             const int sl = p >> 5, l = p & 31;
             int k = eoff[p];
-            double hd[4] = {0.0, 0.0, 0.0, 0.0};
+            int es = -1;
             if (q >= 0) {
                 const int A = cl[q];
                 for (int e = a.row_ptr[A]; e < a.row_ptr[A + 1]; ++e) {
                     const int ce = a.col_idx[e];
                     if (onsite && ce == A) {
-                        for (int r = 0; r < 4; ++r) hd[r] = a.H[16 * (size_t)e + 5 * r];
+                        es = e;
                         continue;
                     }
                     const int b = bsearch_sorted(cl, n_at, ce);
                     if (b >= 0) ell[32 * (k++) + l] = Ent{(4 * pos_of[b]) | (sl << 16), e};
                 }
             }
-            for (int r = 0; r < 4; ++r) hdiag[4 * p + r] = hd[r];
+            eself[p] = es;
         }
         __syncthreads();
 
@@ -287,9 +304,8 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
             const int NP = NS * 32;
             const int nu = min(nu_for(a, n_at), a.nu_max);
             const int aJ = bsearch_sorted(cl, n_at, J);
-            double* A = vec + (size_t)(warp * 3) * NA * 4;
-            double* B = A + (size_t)NA * 4;
-            double* C = B + (size_t)NA * 4;
+            double* A = vec + (size_t)(warp * 2) * NA * 4;    // u_n (gather source of H u)
+            double* B = A + (size_t)NA * 4;                      // H u_n, then w
             double* h = hbuf + warp * kMaxNu;
             int eJJ = -1;
             for (int e = a.row_ptr[J]; e < a.row_ptr[J + 1]; ++e)
@@ -300,127 +316,117 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
                 break;   // leaves this warp's column (do-while below); the CTA barrier follows
             }
             const int jp = 4 * pos_of[aJ] + alpha;
+            const size_t vs = (size_t)NP * 4;                    // one basis vector
 
             for (int q = lane; q < NP * 4; q += 32) A[q] = 0.0;
             __syncwarp();
             if (lane == 0) A[jp] = 1.0 / sqrt(sjj);
             __syncwarp();
-            spmv(a.S, ell, kmax, NS, A, C, lane, onsite, nullptr);
-            for (int s = 0; s < NS; ++s) {
-                const int p = s * 32 + lane;
+            spmv(a.S, ell, kmax, NS, A, SUw, lane, onsite, nullptr, eself);   // S u_1 -> SU[0]
+            for (int sl = 0; sl < NS; ++sl) {
+                const int p = sl * 32 + lane;
                 double2 x0, x1;
                 ld4(A + 4 * p, x0, x1);
                 st4(Uw + 4 * (size_t)p, x0, x1);
-                ld4(C + 4 * p, x0, x1);
-                st4(SUw + 4 * (size_t)p, x0, x1);
             }
             __syncwarp();
 
             int nu_eff = nu;
             for (int n = 0; n < nu; ++n) {
-                spmv(a.H, ell, kmax, NS, A, B, lane, onsite, hdiag);
+                double* Un = Uw + (size_t)n * vs;
+                double* SUn = SUw + (size_t)n * vs;
+                spmv(a.H, ell, kmax, NS, A, B, lane, onsite, a.H, eself);
                 __syncwarp();
                 if (lane == 0) {
                     a.urow[(size_t)col * a.nu_max + n] = A[jp];
-                    a.surow[(size_t)col * a.nu_max + n] = C[jp];
+                    a.surow[(size_t)col * a.nu_max + n] = SUn[jp];
                     a.hurow[(size_t)col * a.nu_max + n] = B[jp];
                 }
-                // pass A: H'[k][n], S'[k][n] and the first CGS coefficients, k <= n
+                // pass A: H'[k][n], S'[k][n] and the first CGS coefficients, k <= n, five k at a time
                 double hh = 0.0;
-                for (int k0 = 0; k0 <= n; k0 += 10) {
-                    double acc[32];
+                for (int k0 = 0; k0 <= n; k0 += 5) {
+                    double acc[16];
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) acc[q] = 0.0;
-                    for (int s = 0; s < NS; ++s) {
-                        const int p = s * 32 + lane;
+                    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+                    for (int sl = 0; sl < NS; ++sl) {
+                        const int p = sl * 32 + lane;
                         double2 hu0, hu1, su0, su1;
                         ld4(B + 4 * p, hu0, hu1);
-                        ld4(C + 4 * p, su0, su1);
-                        if (k0 == 0) acc[30] = fma4(hu0, hu1, hu0, hu1, acc[30]);
+                        ld4(SUn + 4 * p, su0, su1);
+                        if (k0 == 0) acc[15] = fma4(hu0, hu1, hu0, hu1, acc[15]);
 #pragma unroll
-                        for (int kk = 0; kk < 10; ++kk) {
+                        for (int kk = 0; kk < 5; ++kk) {
                             const int k = k0 + kk;
                             if (k <= n) {
                                 double2 u0, u1, v0, v1;
-                                ld4(Uw + 4 * ((size_t)k * NP + p), u0, u1);
-                                ld4(SUw + 4 * ((size_t)k * NP + p), v0, v1);
+                                ld4(Uw + (size_t)k * vs + 4 * p, u0, u1);
+                                ld4(SUw + (size_t)k * vs + 4 * p, v0, v1);
                                 acc[kk] = fma4(u0, u1, hu0, hu1, acc[kk]);
-                                acc[10 + kk] = fma4(u0, u1, su0, su1, acc[10 + kk]);
-                                acc[20 + kk] = fma4(v0, v1, hu0, hu1, acc[20 + kk]);
+                                acc[5 + kk] = fma4(u0, u1, su0, su1, acc[5 + kk]);
+                                acc[10 + kk] = fma4(v0, v1, hu0, hu1, acc[10 + kk]);
                             }
                         }
                     }
-                    const double r = warp_sum32(acc);
-                    const int kk = lane % 10, kind = lane / 10, k = k0 + kk;
-                    if (lane < 30 && k <= n) {
+                    const double r = warp_sum16(acc);
+                    const int kk = lane % 5, kind = lane / 5, k = k0 + kk;
+                    if (lane < 15 && k <= n) {
                         const size_t pk = (size_t)col * PK + k + (size_t)n * (n + 1) / 2;
                         if (kind == 0) a.Hp[pk] = r;
                         else if (kind == 1) a.Sp[pk] = r;
                         else h[k] = r;
                     }
-                    if (k0 == 0) hh = __shfl_sync(0xffffffffu, r, 30);
+                    if (k0 == 0) hh = __shfl_sync(0xffffffffu, r, 15);
                 }
                 if (n == nu - 1) break;
                 __syncwarp();
-                // sweep B: w = hu - U h (first pass), then the second-pass coefficients SU^T w
-                double acc2[32];
+                // sweep B: w = hu - U h (first pass) and the second-pass coefficients SU^T w,
+                // sixteen k at a time (the first sixteen in the same sweep as the update)
+                for (int k0 = 0; k0 <= n; k0 += 16) {
+                    double acc2[16];
 #pragma unroll
-                for (int q = 0; q < 32; ++q) acc2[q] = 0.0;
-                for (int s = 0; s < NS; ++s) {
-                    const int p = s * 32 + lane;
-                    double2 w0, w1;
-                    ld4(B + 4 * p, w0, w1);
-                    sub_basis(Uw, NP, p, h, n, w0, w1);
-                    st4(B + 4 * p, w0, w1);
-#pragma unroll
-                    for (int kk = 0; kk < 32; ++kk) {
-                        if (kk <= n) {
-                            double2 v0, v1;
-                            ld4(SUw + 4 * ((size_t)kk * NP + p), v0, v1);
-                            acc2[kk] = fma4(v0, v1, w0, w1, acc2[kk]);
-                        }
-                    }
-                }
-                double r2 = warp_sum32(acc2);
-                __syncwarp();
-                if (lane <= n) h[lane] = r2;
-                if (n >= 32) {
-#pragma unroll
-                    for (int q = 0; q < 32; ++q) acc2[q] = 0.0;
-                    for (int s = 0; s < NS; ++s) {
-                        const int p = s * 32 + lane;
+                    for (int q = 0; q < 16; ++q) acc2[q] = 0.0;
+                    for (int sl = 0; sl < NS; ++sl) {
+                        const int p = sl * 32 + lane;
                         double2 w0, w1;
                         ld4(B + 4 * p, w0, w1);
+                        if (k0 == 0) {
+                            sub_basis(Uw, NP, p, h, n, w0, w1);
+                            st4(B + 4 * p, w0, w1);
+                        }
 #pragma unroll
-                        for (int kk = 0; kk < 32; ++kk) {
-                            if (32 + kk <= n) {
+                        for (int kk = 0; kk < 16; ++kk) {
+                            if (k0 + kk <= n) {
                                 double2 v0, v1;
-                                ld4(SUw + 4 * ((size_t)(32 + kk) * NP + p), v0, v1);
+                                ld4(SUw + (size_t)(k0 + kk) * vs + 4 * p, v0, v1);
                                 acc2[kk] = fma4(v0, v1, w0, w1, acc2[kk]);
                             }
                         }
                     }
-                    r2 = warp_sum32(acc2);
-                    if (32 + lane <= n) h[32 + lane] = r2;
+                    const double r2 = warp_sum16(acc2);
+                    // the first-pass coefficients were last read by the update of the first
+                    // chunk, so the second-pass ones replace them in place
+                    __syncwarp();
+                    if (lane < 16 && k0 + lane <= n) h[k0 + lane] = r2;
+                    __syncwarp();
                 }
-                __syncwarp();
                 // sweep C: w -= U h (second pass)
-                for (int s = 0; s < NS; ++s) {
-                    const int p = s * 32 + lane;
+                for (int sl = 0; sl < NS; ++sl) {
+                    const int p = sl * 32 + lane;
                     double2 w0, w1;
                     ld4(B + 4 * p, w0, w1);
                     sub_basis(Uw, NP, p, h, n, w0, w1);
                     st4(B + 4 * p, w0, w1);
                 }
                 __syncwarp();
-                // Sw and beta
-                spmv(a.S, ell, kmax, NS, B, C, lane, onsite, nullptr);
+                // Sw (into the next SU slot) and beta
+                double* SUn1 = SUw + (size_t)(n + 1) * vs;
+                spmv(a.S, ell, kmax, NS, B, SUn1, lane, onsite, nullptr, eself);
                 double part = 0.0;
-                for (int s = 0; s < NS; ++s) {
-                    const int p = s * 32 + lane;
+                for (int sl = 0; sl < NS; ++sl) {
+                    const int p = sl * 32 + lane;
                     double2 w0, w1, v0, v1;
                     ld4(B + 4 * p, w0, w1);
-                    ld4(C + 4 * p, v0, v1);
+                    ld4(SUn1 + 4 * p, v0, v1);
                     part = fma4(w0, w1, v0, v1, part);
                 }
                 const double beta2 = warp_sum(part);
@@ -435,17 +441,16 @@ __global__ void __launch_bounds__(kThreads) k_krylov(const KrylovArgs a) {
                     break;
                 }
                 const double inv = 1.0 / beta;
-                for (int s = 0; s < NS; ++s) {
-                    const int p = s * 32 + lane;
+                for (int sl = 0; sl < NS; ++sl) {
+                    const int p = sl * 32 + lane;
                     double2 w0, w1, v0, v1;
                     ld4(B + 4 * p, w0, w1);
-                    ld4(C + 4 * p, v0, v1);
+                    ld4(SUn1 + 4 * p, v0, v1);
                     w0.x *= inv; w0.y *= inv; w1.x *= inv; w1.y *= inv;
                     v0.x *= inv; v0.y *= inv; v1.x *= inv; v1.y *= inv;
                     st4(A + 4 * p, w0, w1);
-                    st4(C + 4 * p, v0, v1);
-                    st4(Uw + 4 * ((size_t)(n + 1) * NP + p), w0, w1);
-                    st4(SUw + 4 * ((size_t)(n + 1) * NP + p), v0, v1);
+                    st4(Uw + (size_t)(n + 1) * vs + 4 * p, w0, w1);
+                    st4(SUn1 + 4 * p, v0, v1);
                 }
                 __syncwarp();
             }

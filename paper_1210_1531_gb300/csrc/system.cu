@@ -102,7 +102,12 @@ struct elses_system_s {
     long long cl_total = 0;
     std::vector<int> h_row_ptr;
 
-    int nu_max = 0, na_max = 0, k3_grid = 0, batch_atoms = 0;
+    int nu_max = 0, na_max = 0, k3_grid = 0, batch_atoms = 0, deg_cap = 0, k3_bps = 0;
+    // Krylov launches: per batch of atoms, one launch per cluster size class (slots of 32 atoms),
+    // each with its own shared-memory footprint and resident-CTA count
+    struct K3Launch { int batch_begin, batch_end, item_begin, item_count, na, grid; };
+    std::vector<K3Launch> k3_launches;
+    std::vector<int> h_clsize;
     DevBuf<double> kscratch, Hp, Sp, urow, surow, hurow, etri, efac, erot_c, erot_s;
     DevBuf<unsigned char> erot_k;
     DevBuf<int> erot_n, eperm;
@@ -118,6 +123,7 @@ struct elses_system_s {
     elses_stats stats{};
     double mu = 0.0;
     bool have_mu = false;
+    bool have_rho = false;   // rho, rhoE of the current positions are in rho / rhoE
 
     // CUDA-event timing of kernel groups (params.timing = 1)
     struct EvPair { cudaEvent_t a, b; int cat; };
@@ -193,26 +199,58 @@ int prepare_columns(elses_system s) {
     s->nu_max = nu_of_params(s->p);
     s->na_max = ((s->max_cl + 31) / 32) * 32;
     const int nm = s->nu_max;
-    const size_t smem = krylov_smem_bytes(s->na_max, s->max_nb);
+    // list capacity per position: in-cluster neighbours, the on-site block excluded when it
+    // is applied as a diagonal (Slater-Koster systems)
+    s->deg_cap = s->user_hs ? s->max_nb : std::max(1, s->max_nb - 1);
     int dev = 0;
     cudaGetDevice(&dev);
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if ((int)smem > smem_optin)
+    const int kdeg = s->user_hs ? s->max_nb : s->deg_cap;
+    if ((int)krylov_smem_bytes(s->na_max, kdeg) > smem_optin)
         return fail(ELSES_ERR_CAPACITY, "cluster of %d atoms needs %zu B of shared memory (max %d)",
-                    s->max_cl, smem, smem_optin);
-    int bps = krylov_blocks_per_sm(s->na_max, s->max_nb);
-    if (bps < 1) return fail(ELSES_ERR_CAPACITY, "Krylov kernel cannot be resident (smem %zu B)", smem);
-    s->k3_grid = s->num_sms * bps;
-    s->k3_grid = std::min(s->k3_grid, std::max(1, s->n));
-    const size_t per_cta = (size_t)kWarpsPerAtom * 2 * nm * s->na_max * 4;
-    TRY(s->kscratch.ensure(per_cta * s->k3_grid));
+                    s->max_cl, krylov_smem_bytes(s->na_max, kdeg), smem_optin);
+    // batch of atoms for the Krylov -> eigensolver hand-off
+    {
+        const size_t PK0 = (size_t)nm * (nm + 1) / 2;
+        const size_t per_col0 = sizeof(double) * (2 * PK0 + 3 * (size_t)nm + eig_tri_doubles(nm) + eig_fac_doubles(nm) +
+                                                  2 * eig_rot_cap(nm)) + eig_rot_cap(nm) + sizeof(int) * (nm + 1);
+        const size_t cols0 = std::max<size_t>(128, (size_t)(1u << 30) / per_col0);   // ~1 GB of batch buffers
+        s->batch_atoms = (int)std::min<size_t>((size_t)s->n, std::max<size_t>(32, cols0 / 4));
+    }
+    // size classes: atoms grouped by slots of 32 cluster atoms, largest class first; inside a
+    // class the batched form orders atoms by decreasing cluster size, the plain form by index
+    std::vector<int> ord;
+    ord.reserve(s->n);
+    s->k3_launches.clear();
+    size_t scratch = 0;
+    int best_items = -1;
+    for (int b = 0; b < s->n; b += s->batch_atoms) {
+        const int e = std::min(s->n, b + s->batch_atoms);
+        for (int ns = s->na_max / 32; ns >= 1; --ns) {
+            const int begin = (int)ord.size();
+            for (int a = b; a < e; ++a)
+                if ((s->h_clsize[a] + 31) / 32 == ns) ord.push_back(a);
+            const int count = (int)ord.size() - begin;
+            if (count == 0) continue;
+            if (s->p.schedule == 1)
+                std::stable_sort(ord.begin() + begin, ord.end(),
+                                 [&](int x, int y) { return s->h_clsize[x] > s->h_clsize[y]; });
+            const int na = 32 * ns;
+            int bps = krylov_blocks_per_sm(na, kdeg);
+            if (bps < 1) return fail(ELSES_ERR_CAPACITY, "Krylov kernel cannot be resident (%d-atom class)", na);
+            if (s->p.k3_ctas_per_sm > 0) bps = std::min(bps, s->p.k3_ctas_per_sm);
+            const int grid = std::min(count, s->num_sms * bps);
+            s->k3_launches.push_back({b, e, begin, count, na, grid});
+            scratch = std::max(scratch, (size_t)grid * kWarpsPerAtom * 2 * nm * na * 4);
+            if (count > best_items) { best_items = count; s->k3_bps = bps; }
+        }
+    }
+    TRY(s->order.ensure(s->n));
+    CUDA_TRY(cudaMemcpy(s->order.p, ord.data(), sizeof(int) * s->n, cudaMemcpyHostToDevice));
+    TRY(s->kscratch.ensure(scratch));
     // batch of atoms for the Krylov -> eigensolver hand-off
     const size_t PK = (size_t)nm * (nm + 1) / 2;
-    const size_t per_col = sizeof(double) * (2 * PK + 3 * (size_t)nm + eig_tri_doubles(nm) + eig_fac_doubles(nm) +
-                                             2 * eig_rot_cap(nm)) + eig_rot_cap(nm) + sizeof(int) * (nm + 1);
-    size_t cols = std::max<size_t>(128, (size_t)(1u << 30) / per_col);   // ~1 GB of batch buffers
-    s->batch_atoms = (int)std::min<size_t>((size_t)s->n, std::max<size_t>(32, cols / 4));
     const size_t bc = 4 * (size_t)s->batch_atoms;
     const size_t bc_pad = ((bc + 31) / 32) * 32;
     TRY(s->Hp.ensure(bc * PK));
@@ -256,6 +294,7 @@ int prepare_columns(elses_system s) {
     s->atom_done.assign(s->n, 0);
     s->atoms_done = 0;
     s->have_mu = false;
+    s->have_rho = false;
     return 0;
 }
 
@@ -283,8 +322,7 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
     }
     ka.breakdown_tol = s->p.breakdown_tol;
     ka.onsite_diag = s->user_hs ? 0 : 1;   // Slater-Koster on-site blocks: S = I, H diagonal
-    ka.na_max = s->na_max;
-    ka.deg_max = s->max_nb;
+    ka.deg_max = s->user_hs ? s->max_nb : s->deg_cap;
     ka.scratch = s->kscratch.p;
     ka.Hp = s->Hp.p;
     ka.Sp = s->Sp.p;
@@ -302,18 +340,23 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
         ka.up_block0 = s->h_row_ptr[b];
     }
     if (!need_rows) ka.UP = nullptr;
-    if (s->p.schedule == 1) {
-        // batched form: persistent CTAs pull atoms from a queue ordered by cluster size
-        CUDA_TRY(cudaMemsetAsync(s->counters.p + 3, 0, sizeof(int), st));
-        ka.queue = s->counters.p + 3;
-        ka.order = s->order.p ? s->order.p + b : nullptr;
-    }
-    const int grid = std::min(s->k3_grid, e - b);
     s->tic(T_KRYLOV, st);
-    krylov_columns(ka, grid, st);
+    for (const auto& L : s->k3_launches) {
+        if (L.batch_begin != b) continue;
+        ka.na_max = L.na;
+        ka.order = s->order.p + L.item_begin;
+        ka.n_items = L.item_count;
+        ka.queue = nullptr;
+        if (s->p.schedule == 1) {
+            // batched form: persistent CTAs pull atoms from the size-sorted queue
+            CUDA_TRY(cudaMemsetAsync(s->counters.p + 3, 0, sizeof(int), st));
+            ka.queue = s->counters.p + 3;
+        }
+        krylov_columns(ka, L.grid, st);
+        s->stats.launches++;
+        s->stats.krylov_launches++;
+    }
     s->toc(st);
-    s->stats.launches++;
-    s->stats.krylov_launches++;
 
     EigArgs ea{};
     ea.ncols = 4 * (e - b);
@@ -546,6 +589,12 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
         if (s->max_cl > p.max_cluster)
             return fail(ELSES_ERR_CAPACITY, "a cluster has %d atoms (max_cluster %d)", s->max_cl, p.max_cluster);
         TRY(s->cl_idx.ensure(std::max(1, tot)));
+        {
+            std::vector<int> hp(n + 1);
+            CUDA_TRY(cudaMemcpy(hp.data(), s->cl_ptr.p, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost));
+            s->h_clsize.resize(n);
+            for (int i = 0; i < n; ++i) s->h_clsize[i] = hp[i + 1] - hp[i];
+        }
         fill_lists(s->pos.p, n, g, s->cell_of.p, s->cell_start.p, s->cell_atoms.p, p.r_cluster,
                    s->cl_ptr.p, s->cl_idx.p, p.max_cluster, s->counters.p + 2, st);
         s->stats.launches++;
@@ -554,6 +603,7 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
             return fail(ELSES_ERR_CAPACITY, "whole-system cluster of %d atoms exceeds max_cluster %d", n, p.max_cluster);
         s->max_cl = n;
         s->cl_total = (long long)n * n;
+        s->h_clsize.assign(n, n);
     }
 
     // Slater-Koster H and S
@@ -564,21 +614,6 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
     s->stats.launches += 2;
     TRY(check_status(s, st));
     TRY(prepare_columns(s));
-    // queue order for the batched form: largest clusters first inside each batch
-    if (p.schedule == 1 && p.r_cluster > 0) {
-        std::vector<int> cnt(n), hptr(n + 1);
-        CUDA_TRY(cudaMemcpy(hptr.data(), s->cl_ptr.p, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost));
-        std::vector<int> ord(n);
-        for (int b = 0; b < n; b += s->batch_atoms) {
-            const int e = std::min(n, b + s->batch_atoms);
-            for (int i = b; i < e; ++i) ord[i] = i;
-            std::stable_sort(ord.begin() + b, ord.begin() + e, [&](int x, int y) {
-                return hptr[x + 1] - hptr[x] > hptr[y + 1] - hptr[y];
-            });
-        }
-        TRY(s->order.ensure(n));
-        CUDA_TRY(cudaMemcpy(s->order.p, ord.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
-    }
     return ELSES_OK;
 }
 
@@ -589,6 +624,7 @@ int elses_set_hs(elses_system s, const double* H_dev, const double* S_dev, void*
     CUDA_TRY(cudaMemcpyAsync(s->H.p, H_dev, sizeof(double) * 16 * s->nnzb, cudaMemcpyDeviceToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(s->S.p, S_dev, sizeof(double) * 16 * s->nnzb, cudaMemcpyDeviceToDevice, st));
     s->user_hs = true;
+    s->have_rho = false;
     s->atom_done.assign(s->n, 0);
     s->atoms_done = 0;
     s->have_mu = false;
@@ -754,6 +790,7 @@ int elses_energy_force(elses_system s, double* mu_host, double* e_band_host, dou
     double mu = 0.0;
     TRY(elses_find_mu(s, &mu, nullptr, stream));
     TRY(density_impl(s, mu, s->rho.p, s->rhoE.p, st));
+    s->have_rho = true;
     ReduceArgs r = reduce_args(s);
     s->tic(T_BISECT, st);
     scalars_at(r, mu, st);
@@ -774,6 +811,21 @@ int elses_energy_force(elses_system s, double* mu_host, double* e_band_host, dou
     if (e_band_host) *e_band_host = h.e_band;
     if (f_free_host) *f_free_host = h.omega + mu * s->p.n_electrons;
     return warn > 0 ? warn : rc;
+}
+
+int elses_forces(elses_system s, double* forces_dev, void* stream) {
+    TRY(check_built(s));
+    if (!forces_dev) return fail(ELSES_ERR_ARG, "null forces");
+    if (s->user_hs) return fail(ELSES_ERR_STATE, "forces need the Slater-Koster H, S");
+    if (!s->have_rho) return fail(ELSES_ERR_STATE, "forces need rho from elses_energy_force");
+    cudaStream_t st = (cudaStream_t)stream;
+    s->tic(T_FORCE, st);
+    forces(s->pos.p, s->n, s->box, s->skd, s->row_ptr.p, s->col_idx.p, s->row_of.p, s->tmap.p, s->nnzb,
+           s->rho.p, s->rhoE.p, s->gblock.p, forces_dev, st);
+    s->toc(st);
+    s->stats.launches += 2;
+    CUDA_TRY(cudaGetLastError());
+    return ELSES_OK;
 }
 
 int elses_icohp(elses_system s, const double* rho_dev, double* B_dev, double* Bsig_dev, double* Bpi_dev,
@@ -840,6 +892,7 @@ int elses_get_spectra(elses_system s, int* nu_max_host, double* eps_dev, double*
 int elses_get_stats(elses_system s, elses_stats* out) {
     if (!s || !out) return fail(ELSES_ERR_ARG, "null argument");
     *out = s->stats;
+    out->k3_ctas_per_sm = s->k3_bps;
     if (s->flops_ctr.p) {
         unsigned long long f = 0;
         CUDA_TRY(cudaMemcpy(&f, s->flops_ctr.p, sizeof f, cudaMemcpyDeviceToHost));

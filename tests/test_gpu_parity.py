@@ -322,3 +322,25 @@ def test_icohp_matches_oracle_and_sums_to_band_energy(eg, d64):
     Bo, Bso, Bpo = cohp.icohp(w.pos, w.box, w.sk, d64["rp"], d64["ci"], d64["rho"])
     assert np.abs(B - Bo).max() < 1e-12 and np.abs(Bs - Bso).max() < 1e-12 and np.abs(Bp - Bpo).max() < 1e-12
     assert abs(B.sum() - d64["e_band"]) / w.n_atoms < 1e-9
+
+
+def test_autograd_free_energy_backward_is_minus_forces(eg, full):
+    """torch.autograd.Function over the library: dF_free/dR from the adjoint kernels equals
+    -forces of elses_energy_force, and matches central differences at full subspace."""
+    w = full[0]
+    s = eg.system_for(w)
+    pos = torch.tensor(w.pos, device="cuda", requires_grad=True)
+    f_free, e_band = eg.free_energy(pos, s)
+    f_free.backward()
+    _, e2, f2, F = s.energy_force()
+    assert f_free.item() == f2 and e_band.item() == e2
+    assert torch.equal(pos.grad, -F)
+    h = 1e-4
+    for (K, m) in ((1, 2), (9, 0)):
+        vals = []
+        for sgn in (1, -1):
+            p = torch.tensor(w.pos, device="cuda")
+            p[K, m] += sgn * h
+            vals.append(eg.free_energy(p, s)[0].item())
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - pos.grad[K, m].item()) <= 1e-5 * max(1.0, F.abs().max().item())
