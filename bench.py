@@ -33,7 +33,10 @@ WORKLOAD = "diamond_4096"
 FP64_NOMINAL_GFLOPS = 152 * 2 * 2 * 2.07     # SMs x FP64 FMA/clk/SM x 2 flops x GHz
 # DRAM bytes (read + write) of one k_krylov launch on the 4096-atom step, from the ncu capture in
 # profiles/k_krylov_diamond4096.md; valid only while krylov.cu is the source that was captured.
-KRYLOV_TRAFFIC = {"krylov_sha256_prefix": "66a1296f61c67c19", "bytes_per_launch": 155.9e9}
+# DRAM bytes (read + write) of the k_krylov launches of one 4096-atom step, from one ncu capture
+# of the source whose sha256 prefix is given; reported per launch, null once krylov.cu changes
+KRYLOV_TRAFFIC = {"krylov_sha256_prefix": "0cbc6bfc9345915d", "bytes_per_step": 179.24e9,
+                  "launches_per_step": 2}
 
 
 def parse():
@@ -163,7 +166,9 @@ def krylov_traffic():
     import hashlib
     path = os.path.join(ROOT, "paper_1210_1531_gb300", "csrc", "krylov.cu")
     h = hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
-    return KRYLOV_TRAFFIC["bytes_per_launch"] if h == KRYLOV_TRAFFIC["krylov_sha256_prefix"] else None
+    if h != KRYLOV_TRAFFIC["krylov_sha256_prefix"]:
+        return None
+    return KRYLOV_TRAFFIC["bytes_per_step"] / KRYLOV_TRAFFIC["launches_per_step"]
 
 
 def run_ours(args):
@@ -298,6 +303,7 @@ def run_ours(args):
                          "traffic": krylov_traffic() if args.workload == WORKLOAD else None,
                          "peak_probe": peak_probe, "flops_per_launch": flops_per_launch,
                          "launch_ms": k_launch_ms, "ctas_per_sm": batched.stats()["k3_ctas_per_sm"],
+                         "launches_per_step": stats["krylov_launches"] / args.steps,
                          "peak_note": "FP64 FMA pipe: 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s); peak_probe = measured FMA-chain throughput"},
             "clocks": clk.summary(),
             "result": {"mu": mu, "e_band": e_band, "f_free": f_free, "bisect_steps": stats["bisect_steps"]},

@@ -34,7 +34,7 @@ int probe_fp64(double* gflops, cudaStream_t st);   // returns a cudaError_t valu
 // ---------------------------------------------------------------- a2, a10 (sk_build.cu)
 void sk_build(const double* pos, int n, const double L[3], const SKDev& sk, const int* row_ptr,
               const int* col_idx, int nnzb, int* row_of, int* tmap, double* H, double* S,
-              cudaStream_t st);
+              double* skr, cudaStream_t st);
 void forces(const double* pos, int n, const double L[3], const SKDev& sk, const int* row_ptr,
             const int* col_idx, const int* row_of, const int* tmap, int nnzb, const double* rho,
             const double* rhoE, double* g_block, double* F, cudaStream_t st);
@@ -48,6 +48,7 @@ struct KrylovArgs {
     const int* col_idx;
     const double* H;
     const double* S;
+    const double* skr;      // two-centre records [nnzb][12] (u, H and S integrals) or nullptr
     const int* cl_ptr;      // nullptr: every cluster is the whole system
     const int* cl_idx;
     int atom_begin, atom_end;

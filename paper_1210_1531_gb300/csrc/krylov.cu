@@ -58,10 +58,13 @@ __device__ __forceinline__ double fma4(const double2 a0, const double2 a1, const
 // (entry.p4 low 16 bits: neighbour offset in x; high bits: the row's slot), so lanes stop after
 // their own entry count instead of after the widest row of every slot. Rows start from the
 // on-site term: the diagonal of the on-site block of `dvals` (block index eself[p]), the
-// identity when dvals is null, or zero when the on-site block is a list entry.
-__device__ __forceinline__ void spmv(const double* __restrict__ vals, const Ent* __restrict__ ent,
-                                     int kmax, int NS, const double* x, double* y, int lane,
-                                     bool onsite, const double* __restrict__ dvals, const int* eself) {
+// identity when dvals is null, or zero when the on-site block is a list entry. With `skr` the
+// off-site blocks are applied in their two-centre form (13 FP64 instructions instead of 16;
+// which = 0 selects the H integrals, 1 the S integrals).
+__device__ __forceinline__ void spmv(const double* __restrict__ vals, const double* __restrict__ skr,
+                                     int which, const Ent* __restrict__ ent, int kmax, int NS,
+                                     const double* x, double* y, int lane, bool onsite,
+                                     const double* __restrict__ dvals, const int* eself) {
     for (int s = 0; s < NS; ++s) {
         const int p = s * 32 + lane, po = 4 * p;
         double2 o01 = make_double2(0.0, 0.0), o23 = make_double2(0.0, 0.0);
@@ -94,15 +97,29 @@ __device__ __forceinline__ void spmv(const double* __restrict__ vals, const Ent*
                 const double2 i01 = yi[0], i23 = yi[1];
                 y0 = i01.x; y1 = i01.y; y2 = i23.x; y3 = i23.y;
             }
-            const double2* b2 = reinterpret_cast<const double2*>(vals + 16 * (size_t)en.blk);
-            const double2 a0 = __ldg(b2 + 0), a1 = __ldg(b2 + 1), a2 = __ldg(b2 + 2), a3 = __ldg(b2 + 3);
-            const double2 a4 = __ldg(b2 + 4), a5 = __ldg(b2 + 5), a6 = __ldg(b2 + 6), a7 = __ldg(b2 + 7);
             const double2 x01 = *reinterpret_cast<const double2*>(x + p4);
             const double2 x23 = *reinterpret_cast<const double2*>(x + p4 + 2);
-            y0 = fma(a0.x, x01.x, fma(a0.y, x01.y, fma(a1.x, x23.x, fma(a1.y, x23.y, y0))));
-            y1 = fma(a2.x, x01.x, fma(a2.y, x01.y, fma(a3.x, x23.x, fma(a3.y, x23.y, y1))));
-            y2 = fma(a4.x, x01.x, fma(a4.y, x01.y, fma(a5.x, x23.x, fma(a5.y, x23.y, y2))));
-            y3 = fma(a6.x, x01.x, fma(a6.y, x01.y, fma(a7.x, x23.x, fma(a7.y, x23.y, y3))));
+            if (skr) {
+                // two-centre block: t = u.x_p; y_s += V_ss x_s + V_sp t;
+                // y_p += V_pi x_p + (dV t - V_sp x_s) u,  dV = V_pp_sigma - V_pp_pi
+                const double2* q = reinterpret_cast<const double2*>(skr + 12 * (size_t)en.blk);
+                const double2 u01 = __ldg(q), u2_ = __ldg(q + 1);
+                const double2 v01 = __ldg(q + 2 + 2 * which), v23 = __ldg(q + 3 + 2 * which);
+                const double t = fma(u2_.x, x23.y, fma(u01.y, x23.x, u01.x * x01.y));
+                y0 = fma(v01.y, t, fma(v01.x, x01.x, y0));
+                const double aa = fma(v23.y, t, -v01.y * x01.x);
+                y1 = fma(aa, u01.x, fma(v23.x, x01.y, y1));
+                y2 = fma(aa, u01.y, fma(v23.x, x23.x, y2));
+                y3 = fma(aa, u2_.x, fma(v23.x, x23.y, y3));
+            } else {
+                const double2* b2 = reinterpret_cast<const double2*>(vals + 16 * (size_t)en.blk);
+                const double2 a0 = __ldg(b2 + 0), a1 = __ldg(b2 + 1), a2 = __ldg(b2 + 2), a3 = __ldg(b2 + 3);
+                const double2 a4 = __ldg(b2 + 4), a5 = __ldg(b2 + 5), a6 = __ldg(b2 + 6), a7 = __ldg(b2 + 7);
+                y0 = fma(a0.x, x01.x, fma(a0.y, x01.y, fma(a1.x, x23.x, fma(a1.y, x23.y, y0))));
+                y1 = fma(a2.x, x01.x, fma(a2.y, x01.y, fma(a3.x, x23.x, fma(a3.y, x23.y, y1))));
+                y2 = fma(a4.x, x01.x, fma(a4.y, x01.y, fma(a5.x, x23.x, fma(a5.y, x23.y, y2))));
+                y3 = fma(a6.x, x01.x, fma(a6.y, x01.y, fma(a7.x, x23.x, fma(a7.y, x23.y, y3))));
+            }
         }
     }
     if (cur >= 0) {
@@ -322,7 +339,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_krylov(const KrylovArgs a) {
             __syncwarp();
             if (lane == 0) A[jp] = 1.0 / sqrt(sjj);
             __syncwarp();
-            spmv(a.S, ell, kmax, NS, A, SUw, lane, onsite, nullptr, eself);   // S u_1 -> SU[0]
+            spmv(a.S, a.skr, 1, ell, kmax, NS, A, SUw, lane, onsite, nullptr, eself);   // S u_1 -> SU[0]
             for (int sl = 0; sl < NS; ++sl) {
                 const int p = sl * 32 + lane;
                 double2 x0, x1;
@@ -333,9 +350,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_krylov(const KrylovArgs a) {
 
             int nu_eff = nu;
             for (int n = 0; n < nu; ++n) {
-                double* Un = Uw + (size_t)n * vs;
                 double* SUn = SUw + (size_t)n * vs;
-                spmv(a.H, ell, kmax, NS, A, B, lane, onsite, a.H, eself);
+                spmv(a.H, a.skr, 0, ell, kmax, NS, A, B, lane, onsite, a.H, eself);
                 __syncwarp();
                 if (lane == 0) {
                     a.urow[(size_t)col * a.nu_max + n] = A[jp];
@@ -420,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_krylov(const KrylovArgs a) {
                 __syncwarp();
                 // Sw (into the next SU slot) and beta
                 double* SUn1 = SUw + (size_t)(n + 1) * vs;
-                spmv(a.S, ell, kmax, NS, B, SUn1, lane, onsite, nullptr, eself);
+                spmv(a.S, a.skr, 1, ell, kmax, NS, B, SUn1, lane, onsite, nullptr, eself);
                 double part = 0.0;
                 for (int sl = 0; sl < NS; ++sl) {
                     const int p = sl * 32 + lane;
@@ -458,12 +474,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_krylov(const KrylovArgs a) {
                 a.nu_eff[j] = nu_eff;
                 if (nu_eff < nu) flag(a.status, DEV_BREAKDOWN);
                 if (a.flops) {
-                    // sparse products: nu_eff with H (2 flops per stored entry, 4 per atom on-site
-                    // when diagonal) and nu_eff with S (identity on-site: no flops); dense CGS2 +
+                    // sparse products: nu_eff with H and nu_eff with S, per off-site block 24 flops
+                    // in the two-centre form (32 as a dense block), on-site H diagonal 4 per atom,
+                    // on-site S = I none; dense CGS2 +
                     // projection: sum_{n<nu}(6(n+1)+2) n_c + sum_{n<nu-1}(6(n+1)+4) n_c
                     const unsigned long long nent = (unsigned long long)sh_nent;
                     const unsigned long long nc = 4ull * n_at, v = (unsigned long long)nu_eff;
-                    const unsigned long long spm = onsite ? v * (64ull * nent + 4ull * n_at) : v * 64ull * nent;
+                    const unsigned long long per = a.skr ? 24ull : 32ull;   // flops per off-site block product
+                    const unsigned long long spm = onsite ? v * (2ull * per * nent + 4ull * n_at) : v * 2ull * per * nent;
                     const unsigned long long tri = v * (v + 1) / 2;          // sum_{n<v} (n+1)
                     const unsigned long long trim = v > 0 ? (v - 1) * v / 2 : 0;  // sum_{n<v-1} (n+1)
                     const unsigned long long dense = nc * (6 * tri + 2 * v) + (v > 0 ? nc * (6 * trim + 4 * (v - 1)) : 0);

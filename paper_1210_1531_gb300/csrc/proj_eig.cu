@@ -37,18 +37,16 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
     const int c = blockIdx.x * (blockDim.x >> 5) + wib;
     if (c >= a.ncols) return;
     const int nm = a.nu_max, ld = nm + 1;
-    double* A = sm + (size_t)wib * (2 * nm * ld + 4 * nm);
+    double* A = sm + (size_t)wib * (2 * nm * ld + 2 * nm);
     double* L = A + nm * ld;
     double* inv = L + nm * ld;     // 1 / L_ii
     double* P = inv + nm;          // Householder work vector
-    double* Y = P + nm;            // 2 * nm: scratch for the three vectors (nm each, 3 used: Y, Y+nm... see below)
     double* yv = a.tri + (size_t)c * eig_tri_doubles(nm);   // D, E, yc, yd, yg (global)
     const int j = a.col0 + c;
     const int nu = a.nu_eff[j];
     const int PK = nm * (nm + 1) / 2;
     const double* Hp = a.Hp + (size_t)c * PK;
     const double* Sp = a.Sp + (size_t)c * PK;
-    (void)Y;
 
     for (int q = lane; q < nu * nu; q += 32) {
         const int i = q / nu, k = q % nu;
@@ -339,7 +337,7 @@ __global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a) {
     }
 }
 
-size_t eig_smem_reduce(int nm) { return sizeof(double) * 2 * (2 * (size_t)nm * (nm + 1) + 4 * nm); }
+size_t eig_smem_reduce(int nm) { return sizeof(double) * 2 * (2 * (size_t)nm * (nm + 1) + 2 * nm); }
 size_t eig_smem_vectors(int nm) { return sizeof(double) * (3 * (size_t)nm * (nm + 1) + nm); }
 
 void projected_eig(const EigArgs& a, cudaStream_t st) {

@@ -33,7 +33,7 @@ __device__ __forceinline__ int find_in_row(const int* __restrict__ row_ptr, cons
 __global__ void k_sk_build(const double* __restrict__ pos, double Lx, double Ly, double Lz, SKDev sk,
                            const int* __restrict__ row_ptr, const int* __restrict__ col_idx,
                            const int* __restrict__ row_of, int nnzb, int* __restrict__ tmap,
-                           double* __restrict__ H, double* __restrict__ S) {
+                           double* __restrict__ H, double* __restrict__ S, double* __restrict__ skr) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nnzb) return;
     const int I = row_of[e], J = col_idx[e];
@@ -44,17 +44,28 @@ __global__ void k_sk_build(const double* __restrict__ pos, double Lx, double Ly,
         for (int q = 0; q < 16; ++q) { hb[q] = 0.0; sb[q] = 0.0; }
         hb[0] = sk.Es; hb[5] = sk.Ep; hb[10] = sk.Ep; hb[15] = sk.Ep;
         sb[0] = 1.0; sb[5] = 1.0; sb[10] = 1.0; sb[15] = 1.0;
+        // on-site record: u = 0 reduces the two-centre product to diag(ss, pi, pi, pi)
+        double* q = skr + 12 * (size_t)e;
+        q[0] = 0.0; q[1] = 0.0; q[2] = 0.0; q[3] = 0.0;
+        q[4] = sk.Es; q[5] = 0.0; q[6] = sk.Ep; q[7] = 0.0;
+        q[8] = 1.0; q[9] = 0.0; q[10] = 1.0; q[11] = 0.0;
     } else {
         const double dx = min_image(pos[3 * J] - pos[3 * I], Lx);
         const double dy = min_image(pos[3 * J + 1] - pos[3 * I + 1], Ly);
         const double dz = min_image(pos[3 * J + 2] - pos[3 * I + 2], Lz);
         const double r = sqrt(dx * dx + dy * dy + dz * dz);
         const double u[3] = {dx / r, dy / r, dz / r};
-        double V[4], dV[4];
+        double V[4], dV[4], W[4];
         sk_radial(sk, sk.V0, sk.qH, r, V, dV);
         sk_block(u, V, hb);
-        sk_radial(sk, sk.S0, sk.qS, r, V, dV);
-        sk_block(u, V, sb);
+        sk_radial(sk, sk.S0, sk.qS, r, W, dV);
+        sk_block(u, W, sb);
+        // two-centre record for the structured block products: u, then (ss, sp, pp_pi,
+        // pp_sigma - pp_pi) of H and of S
+        double* q = skr + 12 * (size_t)e;
+        q[0] = u[0]; q[1] = u[1]; q[2] = u[2]; q[3] = 0.0;
+        q[4] = V[0]; q[5] = V[1]; q[6] = V[3]; q[7] = V[2] - V[3];
+        q[8] = W[0]; q[9] = W[1]; q[10] = W[3]; q[11] = W[2] - W[3];
     }
     double2* H2 = reinterpret_cast<double2*>(H + 16 * (size_t)e);
     double2* S2 = reinterpret_cast<double2*>(S + 16 * (size_t)e);
@@ -67,11 +78,11 @@ __global__ void k_sk_build(const double* __restrict__ pos, double Lx, double Ly,
 
 void sk_build(const double* pos, int n, const double L[3], const SKDev& sk, const int* row_ptr,
               const int* col_idx, int nnzb, int* row_of, int* tmap, double* H, double* S,
-              cudaStream_t st) {
+              double* skr, cudaStream_t st) {
     const int T = 256;
     k_row_of<<<(n + T - 1) / T, T, 0, st>>>(n, row_ptr, row_of);
     k_sk_build<<<(nnzb + T - 1) / T, T, 0, st>>>(pos, L[0], L[1], L[2], sk, row_ptr, col_idx, row_of,
-                                                 nnzb, tmap, H, S);
+                                                 nnzb, tmap, H, S, skr);
 }
 
 // g_e for every off-diagonal block (zero on the diagonal).

@@ -97,7 +97,7 @@ struct elses_system_s {
     DevBuf<int> cl_cnt, cl_ptr, cl_idx;
     DevBuf<int> counters;   // [0] max neighbours, [1] max cluster, [2] status, [3] queue
     DevBuf<unsigned long long> flops_ctr;
-    DevBuf<double> H, S;
+    DevBuf<double> H, S, skr;
     int nnzb = 0, max_nb = 0, max_cl = 0;
     long long cl_total = 0;
     std::vector<int> h_row_ptr;
@@ -309,6 +309,7 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
     ka.col_idx = s->col_idx.p;
     ka.H = s->H.p;
     ka.S = s->S.p;
+    ka.skr = s->user_hs ? nullptr : s->skr.p;   // structured two-centre products for SK systems
     ka.cl_ptr = s->p.r_cluster > 0 ? s->cl_ptr.p : nullptr;
     ka.cl_idx = s->p.r_cluster > 0 ? s->cl_idx.p : nullptr;
     ka.atom_begin = b;
@@ -443,7 +444,7 @@ const char* elses_last_error(void) { return g_err.c_str(); }
 
 void elses_system_destroy(elses_system s) {
     if (!s) return;
-    DevBuf<double>* dbs[] = {&s->pos, &s->H, &s->S, &s->kscratch, &s->Hp, &s->Sp, &s->urow,
+    DevBuf<double>* dbs[] = {&s->pos, &s->H, &s->S, &s->skr, &s->kscratch, &s->Hp, &s->Sp, &s->urow,
                              &s->surow, &s->hurow, &s->etri, &s->efac, &s->erot_c, &s->erot_s,
                              &s->eps, &s->cc, &s->dd, &s->gg,
                              &s->V, &s->UP, &s->Vb, &s->UPb, &s->rho, &s->rhoE, &s->gblock,
@@ -609,8 +610,9 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
     // Slater-Koster H and S
     TRY(s->H.ensure((size_t)s->nnzb * 16));
     TRY(s->S.ensure((size_t)s->nnzb * 16));
+    TRY(s->skr.ensure((size_t)s->nnzb * 12));
     sk_build(s->pos.p, n, s->box, s->skd, s->row_ptr.p, s->col_idx.p, s->nnzb, s->row_of.p, s->tmap.p,
-             s->H.p, s->S.p, st);
+             s->H.p, s->S.p, s->skr.p, st);
     s->stats.launches += 2;
     TRY(check_status(s, st));
     TRY(prepare_columns(s));
