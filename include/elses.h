@@ -81,6 +81,10 @@ typedef struct elses_params {
     int    timing;          /* 1: time the kernels of each call with CUDA events (elses_stats) */
     int    k3_ctas_per_sm;  /* resident Krylov CTAs per SM (0: as many as fit); fewer CTAs keep
                                more of the per-CTA Krylov bases in L2                            */
+    int    force_mode;      /* forces of elses_energy_force: 0 = density-matrix adjoint
+                               (dF/dH = rho, dF/dS = -rhoE; exact when the Krylov space spans the
+                               cluster), 1 = exact gradient of the truncated method
+                               (elses_omega_gradient chained with dH/dR, dS/dR)                 */
 } elses_params;
 
 /* Counters and event timings of the calls since the last build (timing = 1 for the times). */
@@ -102,6 +106,7 @@ typedef struct elses_stats {
                                none) plus
                                CGS2 and projection sum_{n<nu}(6(n+1)+2) n_c
                                + sum_{n<nu-1}(6(n+1)+4) n_c, n_c = 4 |cluster|               */
+    double t_adjoint_ms;    /* exact-gradient kernels (elses_omega_gradient)                  */
 } elses_stats;
 
 typedef struct elses_system_s* elses_system;
@@ -152,8 +157,24 @@ int elses_energy_force(elses_system sys, double* mu_host, double* e_band_host,
 
 /* a10 alone: forces F_I = -dF_free/dR_I (double[N][3] device) from the rho and rhoE kept by the
  * last elses_energy_force on the current positions (the adjoint dF/dH = rho, dF/dS = -rhoE
- * chained with the Slater-Koster dH/dR, dS/dR); ERR_STATE if there are none. Asynchronous. */
+ * chained with the Slater-Koster dH/dR, dS/dR), or with force_mode = 1 from the exact gradient
+ * of elses_omega_gradient at that call's chemical potential; ERR_STATE if there are none.
+ * Asynchronous. */
 int elses_forces(elses_system sys, double* forces_dev, void* stream);
+
+/* Exact gradient of Omega = sum_j Omega_j at fixed mu through the truncated Krylov method:
+ * dOmega/dH and dOmega/dS with the motion of every column's Krylov space K_nu(H_C, e_j) with H
+ * included (Omega_j = sum_k d_k c_k w(e_k), w(e) = -2 kT ln(1 + exp(-(e - mu)/kT)); the paper
+ * gives forces from rho alone, the density-matrix adjoint, which this equals only when the
+ * Krylov space spans the cluster). Outputs double[nnzb][4][4] device, [e][a][b] =
+ * dOmega / dH_(I,a),(J,b) for block e = (I, J) (on-site blocks included), summed over the
+ * columns of atoms [atom_begin, atom_end); both are overwritten. The gradient of F_free at fixed
+ * N_e is this at the chemical potential. Needs every column computed at the current positions
+ * (elses_green_columns over all columns, or elses_energy_force); in the two-pass mode each
+ * batch's columns are recomputed first. ERR_ARG for a bad range or null outputs, ERR_STATE
+ * without the columns. Synchronises `stream` (device status check). */
+int elses_omega_gradient(elses_system sys, double mu, int atom_begin, int atom_end, double* dH_dev,
+                         double* dS_dev, void* stream);
 
 /* (pi)COHP analysis, Eqs. 4-8: the ICOHP of each block e = (I, J) of the pattern,
  * B_IJ = sum_ab H_(J,b);(I,a) rho_(I,a);(J,b) (the Fermi-weighted energy integral of the COHP of

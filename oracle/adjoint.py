@@ -118,7 +118,7 @@ def column_gradient(Hc, Sc, jl, nu, mu, kT):
     S = torch.tensor(Sc, dtype=_F64, requires_grad=True)
     om = column_omega(H, S, jl, nu, mu, kT)
     gH, gS = torch.autograd.grad(om, (H, S))
-    return float(om), gH.numpy(), gS.numpy()
+    return float(om.detach()), gH.numpy(), gS.numpy()
 
 
 def pattern_gradient(workload, mu, cols=None):

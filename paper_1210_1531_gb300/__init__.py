@@ -46,7 +46,8 @@ class Params(ctypes.Structure):
                 ("two_pass", ctypes.c_int), ("n_classes", ctypes.c_int),
                 ("class_max_atoms", ctypes.c_int * 4), ("class_nu", ctypes.c_int * 4),
                 ("max_neighbors", ctypes.c_int), ("max_cluster", ctypes.c_int),
-                ("schedule", ctypes.c_int), ("timing", ctypes.c_int), ("k3_ctas_per_sm", ctypes.c_int)]
+                ("schedule", ctypes.c_int), ("timing", ctypes.c_int), ("k3_ctas_per_sm", ctypes.c_int),
+                ("force_mode", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -55,12 +56,13 @@ class Stats(ctypes.Structure):
                 ("k3_ctas_per_sm", ctypes.c_int), ("t_krylov_ms", ctypes.c_double),
                 ("t_eig_ms", ctypes.c_double), ("t_bisect_ms", ctypes.c_double),
                 ("t_density_ms", ctypes.c_double), ("t_force_ms", ctypes.c_double),
-                ("krylov_flops", ctypes.c_double)]
+                ("krylov_flops", ctypes.c_double), ("t_adjoint_ms", ctypes.c_double)]
 
 
 EXPORTS = (
     "elses_build_clusters", "elses_set_hs", "elses_green_columns", "elses_find_mu",
-    "elses_density_matrix", "elses_energies", "elses_energy_force", "elses_forces", "elses_icohp",
+    "elses_density_matrix", "elses_energies", "elses_energy_force", "elses_forces",
+    "elses_omega_gradient", "elses_icohp",
     "elses_get_pattern",
     "elses_get_hs", "elses_get_clusters", "elses_get_spectra", "elses_get_stats",
     "elses_reset_stats", "elses_probe_fp64", "elses_find_mu_static", "elses_system_destroy",
@@ -90,6 +92,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "elses_energy_force": [P, pD, pD, pD, P, V],
         "elses_icohp": [P, P, P, P, P, V],
         "elses_forces": [P, P, V],
+        "elses_omega_gradient": [P, D, I, I, P, P, V],
         "elses_get_pattern": [P, pI, P, P, V],
         "elses_get_hs": [P, P, P, V],
         "elses_get_clusters": [P, pLL, pI, P, P, V],
@@ -141,7 +144,7 @@ def make_sk(p) -> SK:
 
 def make_params(r_cluster, nu, kT, n_electrons, two_pass=False, nu_classes=(), schedule=0,
                 max_neighbors=0, max_cluster=0, breakdown_tol=0.0, mu_tol=0.0,
-                max_bisect=0, timing=False, k3_ctas_per_sm=0) -> Params:
+                max_bisect=0, timing=False, k3_ctas_per_sm=0, exact_forces=False) -> Params:
     p = Params()
     p.r_cluster, p.kT, p.n_electrons = float(r_cluster), float(kT), float(n_electrons)
     p.breakdown_tol, p.mu_tol = float(breakdown_tol), float(mu_tol)
@@ -153,6 +156,7 @@ def make_params(r_cluster, nu, kT, n_electrons, two_pass=False, nu_classes=(), s
     p.max_neighbors, p.max_cluster, p.schedule = int(max_neighbors), int(max_cluster), int(schedule)
     p.timing = int(bool(timing))
     p.k3_ctas_per_sm = int(k3_ctas_per_sm)
+    p.force_mode = 1 if exact_forces else 0
     return p
 
 
@@ -161,7 +165,7 @@ class System:
 
     def __init__(self, pos, box, sk, r_cluster, nu, kT, n_electrons, two_pass=False,
                  nu_classes=(), schedule=0, max_neighbors=0, max_cluster=0, timing=False,
-                 k3_ctas_per_sm=0, stream=None):
+                 k3_ctas_per_sm=0, exact_forces=False, stream=None):
         self._L = load_library()
         self._h = ctypes.c_void_p(None)
         self.n = int(pos.shape[0])
@@ -169,7 +173,7 @@ class System:
         self.sk = make_sk(sk)
         self.params = make_params(r_cluster, nu, kT, n_electrons, two_pass, nu_classes, schedule,
                                   max_neighbors, max_cluster, timing=timing,
-                                  k3_ctas_per_sm=k3_ctas_per_sm)
+                                  k3_ctas_per_sm=k3_ctas_per_sm, exact_forces=exact_forces)
         self.box = (ctypes.c_double * 3)(*[float(b) for b in box])
         self.rebuild(pos, stream)
 
@@ -229,6 +233,16 @@ class System:
         out = torch.empty((self.n, 3), dtype=torch.float64, device="cuda") if out is None else out
         _check(self._L.elses_forces(self._h, _ptr(out), _stream(stream)))
         return out
+
+    def omega_gradient(self, mu, atom_begin=0, atom_end=None, stream=None):
+        """Exact dOmega/dH, dOmega/dS at mu through the truncated Krylov method (elses_omega_gradient),
+        summed over the columns of atoms [atom_begin, atom_end): CUDA float64 [nnzb, 4, 4] each."""
+        atom_end = self.n if atom_end is None else atom_end
+        dH = torch.empty((self.nnzb, 4, 4), dtype=torch.float64, device="cuda")
+        dS = torch.empty_like(dH)
+        _check(self._L.elses_omega_gradient(self._h, float(mu), int(atom_begin), int(atom_end), _ptr(dH),
+                                            _ptr(dS), _stream(stream)))
+        return dH, dS
 
     def icohp(self, rho, stream=None):
         """(pi)COHP integrals per pattern block: (B, B_sigma, B_pi), CUDA float64 [nnzb] each."""
@@ -302,7 +316,8 @@ class FreeEnergy(torch.autograd.Function):
 
     forward: rebuild at R, then the whole path through elses_energy_force without forces;
     backward: the library's adjoint kernels (elses_forces: dF/dH = rho, dF/dS = -rhoE chained
-    with dH/dR, dS/dR), grad_R = -F * grad_out. Returns (F_free, E_band); E_band is not
+    with dH/dR, dS/dR, or the exact gradient of the truncated method for a System built with
+    exact_forces=True), grad_R = -F * grad_out. Returns (F_free, E_band); E_band is not
     differentiable."""
 
     @staticmethod

@@ -24,6 +24,22 @@ constexpr int kWarpsPerAtom = 4;    // one warp per orbital column of an atom
 
 __device__ __forceinline__ void flag(int* st, int f) { atomicOr(st, f); }
 
+// Fermi-Dirac occupation f = 1 / (1 + exp(x)), x = (e - mu) / kT, without overflow.
+__device__ __forceinline__ double fermi(double x) {
+    if (x > 0.0) {
+        const double t = exp(-x);
+        return t / (1.0 + t);
+    }
+    return 1.0 / (1.0 + exp(x));
+}
+
+// Grand-potential weight w(e) = -2 kT ln(1 + exp(-(e - mu)/kT)); dw/de = 2 f.
+__device__ __forceinline__ double omega_w(double e, double mu, double kT) {
+    const double x = (e - mu) / kT;
+    if (x >= 0.0) return -2.0 * kT * log1p(exp(-x));
+    return 2.0 * (x * kT) - 2.0 * kT * log1p(exp(x));
+}
+
 // Minimum image with one IEEE operation per step, in the fixed order d - L*rint(d/L). No FMA
 // contraction: the integer outputs (neighbour lists) must be reproducible bit for bit.
 __device__ __forceinline__ double min_image(double d, double L) {

@@ -13,14 +13,6 @@
 
 namespace elses {
 
-__device__ __forceinline__ double fermi_d(double x) {
-    if (x > 0.0) {
-        const double t = exp(-x);
-        return t / (1.0 + t);
-    }
-    return 1.0 / (1.0 + exp(x));
-}
-
 __global__ void __launch_bounds__(128) k_density(const DensityArgs a) {
     __shared__ double wc[4][kMaxNu], wec[4][kMaxNu], t[4][kMaxNu], tE[4][kMaxNu];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -31,7 +23,7 @@ __global__ void __launch_bounds__(128) k_density(const DensityArgs a) {
     const int nu = a.nu_eff[j];
     for (int k = lane; k < nu; k += 32) {
         const double e = a.eps[(size_t)j * nm + k];
-        const double f2 = 2.0 * fermi_d((e - a.mu) / a.kT) * a.c[(size_t)j * nm + k];
+        const double f2 = 2.0 * fermi((e - a.mu) / a.kT) * a.c[(size_t)j * nm + k];
         wc[warp][k] = f2;
         wec[warp][k] = f2 * e;
     }

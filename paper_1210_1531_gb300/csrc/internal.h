@@ -76,8 +76,27 @@ struct KrylovArgs {
     int* status;
     unsigned long long* flops;   // algorithmic FP64 flops of the columns, accumulated
 };
+
+// Exact-gradient pass (adjoint.cu) over the columns of a batch; the KrylovArgs of the same batch
+// drive the recomputed forward recursion.
+struct AdjointArgs {
+    const double* V;        // [col - v_col0][nu_max][nu_max] eigenvectors (rows: Krylov index)
+    int v_col0;
+    const double* eps;      // [M][nu_max] poles ascending, and the spectra c, d
+    const double* c;
+    const double* d;
+    double mu, kT;
+    double* gH;             // [nnzb][16] accumulated dOmega/dH
+    double* gS;             // [nnzb][16] accumulated s_scale * dOmega/dS
+    double s_scale;
+    double* scratch;        // per resident CTA: 4 warps x adjoint_warp_doubles(nu_max, na_max)
+    int atom_lo, atom_hi;   // only atoms in [atom_lo, atom_hi) are accumulated
+};
 size_t krylov_smem_bytes(int na_max, int deg_max);
 int krylov_blocks_per_sm(int na_max, int deg_max);
+__host__ __device__ size_t adjoint_warp_doubles(int nu_max, int na_max);
+int adjoint_blocks_per_sm(int na_max, int deg_max);
+void adjoint_columns(const KrylovArgs& a, const AdjointArgs& g, int grid, cudaStream_t st);
 void krylov_columns(const KrylovArgs& a, int grid, cudaStream_t st);
 
 // ---------------------------------------------------------------- a5, a6 (proj_eig.cu)

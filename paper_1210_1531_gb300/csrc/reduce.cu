@@ -18,20 +18,6 @@ namespace elses {
 
 constexpr int kRedThreads = 256;
 
-__device__ __forceinline__ double fermi(double x) {   // x = (e - mu) / kT
-    if (x > 0.0) {
-        const double t = exp(-x);
-        return t / (1.0 + t);
-    }
-    return 1.0 / (1.0 + exp(x));
-}
-
-__device__ __forceinline__ double omega_w(double e, double mu, double kT) {
-    const double x = (e - mu) / kT;
-    if (x >= 0.0) return -2.0 * kT * log1p(exp(-x));
-    return 2.0 * (x * kT) - 2.0 * kT * log1p(exp(x));
-}
-
 int reduce_grid() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);

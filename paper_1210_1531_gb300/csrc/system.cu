@@ -114,6 +114,8 @@ struct elses_system_s {
     DevBuf<double> eps, cc, dd, gg, V, UP, Vb, UPb;
     DevBuf<int> nu_eff, order;
     DevBuf<double> rho, rhoE, gblock;
+    DevBuf<double> ascratch, adjH, adjS;   // exact-gradient scratch and its pattern gradients
+    std::vector<int> adj_bps;              // resident adjoint CTAs per SM, by cluster slots
     DevBuf<double> partials, zbuf;
     DevBuf<BisectState> bstate;
     DevBuf<unsigned> ticket;
@@ -149,8 +151,9 @@ struct elses_system_s {
         for (auto& q : pending) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
-                double* t = &stats.t_krylov_ms;
-                t[q.cat] += ms;
+                double* slot[] = {&stats.t_krylov_ms, &stats.t_eig_ms, &stats.t_bisect_ms,
+                                  &stats.t_density_ms, &stats.t_force_ms, &stats.t_adjoint_ms};
+                *slot[q.cat] += ms;
             }
             pool.push_back(q.a);
             pool.push_back(q.b);
@@ -164,7 +167,7 @@ struct elses_system_s {
     }
 };
 
-enum { T_KRYLOV = 0, T_EIG = 1, T_BISECT = 2, T_DENSITY = 3, T_FORCE = 4 };
+enum { T_KRYLOV = 0, T_EIG = 1, T_BISECT = 2, T_DENSITY = 3, T_FORCE = 4, T_ADJOINT = 5 };
 
 namespace {
 
@@ -300,8 +303,8 @@ int prepare_columns(elses_system s) {
 
 // Krylov build + projected eigenproblem for atoms [b, e). Writes V and UP either to the stored
 // arrays or to the batch buffers (two-pass), returning the pointers used.
-int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_col0,
-              double** UP_out, int* up_block0, cudaStream_t st, bool need_rows = true) {
+// Krylov-kernel arguments for atoms [b, e) (the launch fields are set per size class).
+KrylovArgs krylov_args(elses_system s, int b, int e) {
     const int nm = s->nu_max;
     KrylovArgs ka{};
     ka.n_atoms = s->n;
@@ -333,6 +336,13 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
     ka.nu_eff = s->nu_eff.p;
     ka.status = s->counters.p + 2;
     ka.flops = s->flops_ctr.p;
+    return ka;
+}
+
+int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_col0,
+              double** UP_out, int* up_block0, cudaStream_t st, bool need_rows = true) {
+    const int nm = s->nu_max;
+    KrylovArgs ka = krylov_args(s, b, e);
     if (stored) {
         ka.UP = s->UP.p;
         ka.up_block0 = 0;
@@ -394,6 +404,73 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
     return 0;
 }
 
+// Exact dOmega/dH and s_scale * dOmega/dS at mu of the columns of atoms [lo, hi) into gH, gS
+// ([nnzb][16], overwritten): per batch, the adjoint kernel per size class, after the batch's
+// Krylov columns are recomputed when V is not kept (two-pass mode).
+int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* gS, double s_scale,
+                 cudaStream_t st) {
+    const int nm = s->nu_max;
+    const int kdeg = s->user_hs ? s->max_nb : s->deg_cap;
+    CUDA_TRY(cudaMemsetAsync(gH, 0, sizeof(double) * 16 * (size_t)s->nnzb, st));
+    CUDA_TRY(cudaMemsetAsync(gS, 0, sizeof(double) * 16 * (size_t)s->nnzb, st));
+    // launch shapes and scratch: the Krylov kernel's size classes, the adjoint's own residency
+    if ((int)s->adj_bps.size() != s->na_max / 32 + 1) s->adj_bps.assign(s->na_max / 32 + 1, 0);
+    size_t need = 0;
+    std::vector<int> grid(s->k3_launches.size(), 0);
+    for (size_t i = 0; i < s->k3_launches.size(); ++i) {
+        const auto& L = s->k3_launches[i];
+        int& bps = s->adj_bps[L.na / 32];
+        if (bps == 0) bps = adjoint_blocks_per_sm(L.na, kdeg);
+        if (bps < 1) return fail(ELSES_ERR_CAPACITY, "adjoint kernel cannot be resident (%d-atom class)", L.na);
+        grid[i] = std::min(L.item_count, s->num_sms * bps);
+        need = std::max(need, (size_t)grid[i] * kWarpsPerAtom * adjoint_warp_doubles(nm, L.na));
+    }
+    TRY(s->ascratch.ensure(need));
+    for (int b = 0; b < s->n; b += s->batch_atoms) {
+        const int e = std::min(s->n, b + s->batch_atoms);
+        if (e <= lo || b >= hi) continue;
+        AdjointArgs ga{};
+        ga.V = s->V.p;
+        ga.v_col0 = 0;
+        if (s->p.two_pass) {
+            double *Vb = nullptr, *UPb = nullptr;
+            int c0 = 0, ub0 = 0;
+            TRY(run_batch(s, b, e, false, &Vb, &c0, &UPb, &ub0, st, false));
+            ga.V = Vb;
+            ga.v_col0 = c0;
+        }
+        ga.eps = s->eps.p;
+        ga.c = s->cc.p;
+        ga.d = s->dd.p;
+        ga.mu = mu;
+        ga.kT = s->p.kT;
+        ga.gH = gH;
+        ga.gS = gS;
+        ga.s_scale = s_scale;
+        ga.scratch = s->ascratch.p;
+        ga.atom_lo = lo;
+        ga.atom_hi = hi;
+        KrylovArgs ka = krylov_args(s, b, e);
+        ka.flops = nullptr;
+        ka.UP = nullptr;
+        s->tic(T_ADJOINT, st);
+        for (size_t i = 0; i < s->k3_launches.size(); ++i) {
+            const auto& L = s->k3_launches[i];
+            if (L.batch_begin != b) continue;
+            ka.na_max = L.na;
+            ka.order = s->order.p + L.item_begin;
+            ka.n_items = L.item_count;
+            CUDA_TRY(cudaMemsetAsync(s->counters.p + 3, 0, sizeof(int), st));
+            ka.queue = s->counters.p + 3;
+            adjoint_columns(ka, ga, grid[i], st);
+            s->stats.launches++;
+        }
+        s->toc(st);
+    }
+    CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
 int check_built(elses_system s) {
     if (!s) return fail(ELSES_ERR_ARG, "null system");
     if (s->n <= 0 || !s->H.p) return fail(ELSES_ERR_STATE, "system not built");
@@ -444,7 +521,7 @@ const char* elses_last_error(void) { return g_err.c_str(); }
 
 void elses_system_destroy(elses_system s) {
     if (!s) return;
-    DevBuf<double>* dbs[] = {&s->pos, &s->H, &s->S, &s->skr, &s->kscratch, &s->Hp, &s->Sp, &s->urow,
+    DevBuf<double>* dbs[] = {&s->pos, &s->H, &s->S, &s->skr, &s->ascratch, &s->adjH, &s->adjS, &s->kscratch, &s->Hp, &s->Sp, &s->urow,
                              &s->surow, &s->hurow, &s->etri, &s->efac, &s->erot_c, &s->erot_s,
                              &s->eps, &s->cc, &s->dd, &s->gg,
                              &s->V, &s->UP, &s->Vb, &s->UPb, &s->rho, &s->rhoE, &s->gblock,
@@ -479,6 +556,7 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
     for (int c = 0; c < p.n_classes; ++c)
         if (p.class_nu[c] < 1 || p.class_nu[c] > kMaxNu) return fail(ELSES_ERR_ARG, "class_nu out of range");
     if (!(p.kT > 0)) return fail(ELSES_ERR_ARG, "kT must be positive");
+    if (p.force_mode < 0 || p.force_mode > 1) return fail(ELSES_ERR_ARG, "force_mode must be 0 or 1");
     if (!(sk->r_cut > sk->r_on) || !(sk->r_on > 0)) return fail(ELSES_ERR_ARG, "need 0 < r_on < r_cut");
     for (int d = 0; d < 3; ++d) {
         if (!(box_host[d] > 2.0 * sk->r_cut)) return fail(ELSES_ERR_ARG, "box must exceed 2*r_cut");
@@ -799,9 +877,18 @@ int elses_energy_force(elses_system s, double* mu_host, double* e_band_host, dou
     s->toc(st);
     s->stats.launches++;
     if (forces_dev) {
+        const double* gh = s->rho.p;
+        const double* gs = s->rhoE.p;
+        if (s->p.force_mode == 1) {   // exact gradient of the truncated method: dF/dH, -dF/dS
+            TRY(s->adjH.ensure((size_t)s->nnzb * 16));
+            TRY(s->adjS.ensure((size_t)s->nnzb * 16));
+            TRY(adjoint_impl(s, mu, 0, s->n, s->adjH.p, s->adjS.p, -1.0, st));
+            gh = s->adjH.p;
+            gs = s->adjS.p;
+        }
         s->tic(T_FORCE, st);
         forces(s->pos.p, s->n, s->box, s->skd, s->row_ptr.p, s->col_idx.p, s->row_of.p, s->tmap.p, s->nnzb,
-               s->rho.p, s->rhoE.p, s->gblock.p, forces_dev, st);
+               gh, gs, s->gblock.p, forces_dev, st);
         s->toc(st);
         s->stats.launches += 2;
     }
@@ -815,15 +902,39 @@ int elses_energy_force(elses_system s, double* mu_host, double* e_band_host, dou
     return warn > 0 ? warn : rc;
 }
 
+int elses_omega_gradient(elses_system s, double mu, int atom_begin, int atom_end, double* dH_dev,
+                         double* dS_dev, void* stream) {
+    TRY(check_built(s));
+    if (!dH_dev || !dS_dev) return fail(ELSES_ERR_ARG, "null gradient outputs");
+    if (atom_begin < 0 || atom_end > s->n || atom_begin > atom_end)
+        return fail(ELSES_ERR_ARG, "atom range [%d, %d) outside [0, %d)", atom_begin, atom_end, s->n);
+    if (s->atoms_done != s->n) return fail(ELSES_ERR_STATE, "the gradient needs every column computed");
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(clear_status(s, st));
+    TRY(adjoint_impl(s, mu, atom_begin, atom_end, dH_dev, dS_dev, 1.0, st));
+    const int rc = check_status(s, st);
+    s->collect();
+    return rc;
+}
+
 int elses_forces(elses_system s, double* forces_dev, void* stream) {
     TRY(check_built(s));
     if (!forces_dev) return fail(ELSES_ERR_ARG, "null forces");
     if (s->user_hs) return fail(ELSES_ERR_STATE, "forces need the Slater-Koster H, S");
     if (!s->have_rho) return fail(ELSES_ERR_STATE, "forces need rho from elses_energy_force");
     cudaStream_t st = (cudaStream_t)stream;
+    const double* gh = s->rho.p;
+    const double* gs = s->rhoE.p;
+    if (s->p.force_mode == 1) {
+        TRY(s->adjH.ensure((size_t)s->nnzb * 16));
+        TRY(s->adjS.ensure((size_t)s->nnzb * 16));
+        TRY(adjoint_impl(s, s->mu, 0, s->n, s->adjH.p, s->adjS.p, -1.0, st));
+        gh = s->adjH.p;
+        gs = s->adjS.p;
+    }
     s->tic(T_FORCE, st);
     forces(s->pos.p, s->n, s->box, s->skd, s->row_ptr.p, s->col_idx.p, s->row_of.p, s->tmap.p, s->nnzb,
-           s->rho.p, s->rhoE.p, s->gblock.p, forces_dev, st);
+           gh, gs, s->gblock.p, forces_dev, st);
     s->toc(st);
     s->stats.launches += 2;
     CUDA_TRY(cudaGetLastError());
