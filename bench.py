@@ -34,7 +34,8 @@ FP64_NOMINAL_GFLOPS = 152 * 2 * 2 * 2.07     # SMs x FP64 FMA/clk/SM x 2 flops x
 # DRAM bytes (read + write) of one k_krylov launch on the 4096-atom step, from the ncu capture in
 # profiles/k_krylov_diamond4096.md; valid only while krylov.cu is the source that was captured.
 # DRAM bytes (read + write) of the k_krylov launches of one 4096-atom step, from one ncu capture
-# of the source whose sha256 prefix is given; reported per launch, null once krylov.cu changes
+# of the source whose sha256 prefix (krylov.cu + krylov.cuh) is given; reported per launch, null
+# once that source changes
 KRYLOV_TRAFFIC = {"krylov_sha256_prefix": "0cbc6bfc9345915d", "bytes_per_step": 179.24e9,
                   "launches_per_step": 2}
 
@@ -164,8 +165,10 @@ def aggregate(ms_local, units_local, world, dist=None, device=None):
 
 def krylov_traffic():
     import hashlib
-    path = os.path.join(ROOT, "paper_1210_1531_gb300", "csrc", "krylov.cu")
-    h = hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in ("krylov.cu", "krylov.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1210_1531_gb300", "csrc", name), "rb").read())
+    h = h.hexdigest()[:16]
     if h != KRYLOV_TRAFFIC["krylov_sha256_prefix"]:
         return None
     return KRYLOV_TRAFFIC["bytes_per_step"] / KRYLOV_TRAFFIC["launches_per_step"]

@@ -134,7 +134,8 @@ struct BisectState {
     double lo, hi, mu;
     double n_lo, n_hi, n_mid;
     double n_at, e_band, omega;
-    int iter, done, status, pad;
+    double mu0;             // where the kept exponentials were taken
+    int iter, done, status, have_pre;
 };
 struct ReduceArgs {
     int M;
@@ -151,6 +152,7 @@ struct ReduceArgs {
     BisectState* state;
     double* partials;       // [grid][4]
     unsigned* ticket;
+    double* pre;            // optional [M][nu_max]: exp((e - mu0)/kT) kept by the bisection
 };
 int reduce_grid();
 void bisect_init(const ReduceArgs& a, cudaStream_t st);      // bracket + N(lo), N(hi)

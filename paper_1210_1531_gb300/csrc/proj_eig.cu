@@ -37,10 +37,10 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
     const int c = blockIdx.x * (blockDim.x >> 5) + wib;
     if (c >= a.ncols) return;
     const int nm = a.nu_max, ld = nm + 1;
-    double* A = sm + (size_t)wib * (2 * nm * ld + 2 * nm);
-    double* L = A + nm * ld;
+    double* A = sm + (size_t)wib * ((2 * nm + 3) * ld + 2 * nm + 3);
+    double* L = A + (nm + 3) * ld;  // A: the matrix, then the three vectors as rows nu .. nu + 2
     double* inv = L + nm * ld;     // 1 / L_ii
-    double* P = inv + nm;          // Householder work vector
+    double* P = inv + nm;          // Householder work vector (nm + 3)
     double* yv = a.tri + (size_t)c * eig_tri_doubles(nm);   // D, E, yc, yd, yg (global)
     const int j = a.col0 + c;
     const int nu = a.nu_eff[j];
@@ -97,7 +97,49 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
             A[k * ld + i] = v;
         }
     __syncwarp();
-    // Householder reduction: reflector k stored in column k below the diagonal, tau_k kept
+    // the three vectors z = L^-1 (U, SU, HU)_j into rows nu .. nu + 2 of A: a column sweep with
+    // lanes over rows (rows lane and lane + 32), row m final at step m
+    {
+        const double* src[3] = {a.urow + (size_t)c * nm, a.surow + (size_t)c * nm, a.hurow + (size_t)c * nm};
+        double z0[3], z1[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            z0[q] = lane < nu ? src[q][lane] : 0.0;
+            z1[q] = lane + 32 < nu ? src[q][lane + 32] : 0.0;
+        }
+        for (int m = 0; m < nu; ++m) {
+            const int owner = m & 31;
+            const bool upper = m >= 32;
+            const double im = inv[m];
+            double y[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) y[q] = __shfl_sync(0xffffffffu, (upper ? z1[q] : z0[q]) * im, owner);
+            if (lane == owner) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    if (upper) z1[q] = y[q]; else z0[q] = y[q];
+                }
+            }
+            if (lane > m && lane < nu) {
+                const double l = L[lane * ld + m];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) z0[q] = fma(-l, y[q], z0[q]);
+            }
+            if (lane + 32 > m && lane + 32 < nu) {
+                const double l = L[(lane + 32) * ld + m];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) z1[q] = fma(-l, y[q], z1[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            if (lane < nu) A[(nu + q) * ld + lane] = z0[q];
+            if (lane + 32 < nu) A[(nu + q) * ld + lane + 32] = z1[q];
+        }
+    }
+    __syncwarp();
+    // Householder reduction: reflector k stored in column k below the diagonal, tau_k kept; the
+    // vector rows are reflected along (y = Q_H^T z)
     double* E = yv + nm;
     for (int k = 0; k + 2 < nu; ++k) {
         double part = 0.0;
@@ -113,14 +155,15 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
         const double tau = 1.0 / (alpha * (alpha - x0));
         if (lane == 0) A[(k + 1) * ld + k] = x0 - alpha;
         __syncwarp();
-        // p = tau A v (rows i > k)
+        // p = tau A v (rows i > k); the same sweep gives t_q = tau v^T y_q for the vector rows,
+        // in lanes the matrix rows leave idle
         double kp = 0.0;
-        for (int i = k + 1 + lane; i < nu; i += 32) {
+        for (int i = k + 1 + lane; i < nu + 3; i += 32) {
             double s = 0.0;
             for (int m = k + 1; m < nu; ++m) s = fma(A[i * ld + m], A[m * ld + k], s);
             s *= tau;
             P[i] = s;
-            kp = fma(A[i * ld + k], s, kp);
+            if (i < nu) kp = fma(A[i * ld + k], s, kp);
         }
         const double K = 0.5 * tau * warp_sum(kp);
         __syncwarp();
@@ -130,6 +173,11 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
             const double vi = A[i * ld + k], qi = P[i];
             for (int m = k + 1; m < nu; ++m)
                 A[i * ld + m] = fma(-vi, P[m], fma(-qi, A[m * ld + k], A[i * ld + m]));
+        }
+        for (int m = k + 1 + lane; m < nu; m += 32) {   // y_q -= t_q v
+            const double vm = A[m * ld + k];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) A[(nu + q) * ld + m] = fma(-P[nu + q], vm, A[(nu + q) * ld + m]);
         }
         __syncwarp();
         if (lane == 0) { E[k] = alpha; P[k] = tau; }   // P[k] keeps tau_k (P[i > k] reused later)
@@ -145,23 +193,10 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
         P[nu - 1] = 0.0;
     }
     __syncwarp();
-    // the three vectors: z = L^-1 (U, SU, HU)_j, then y = Q_H^T z (reflectors k = 0, 1, ...)
-    if (lane < 3) {
-        const double* src = (lane == 0 ? a.urow : lane == 1 ? a.surow : a.hurow) + (size_t)c * nm;
-        double* y = yv + (2 + lane) * nm;
-        for (int i = 0; i < nu; ++i) {
-            double s = src[i];
-            for (int m = 0; m < i; ++m) s = fma(-L[i * ld + m], y[m], s);
-            y[i] = s * inv[i];
-        }
-        for (int k = 0; k + 2 < nu; ++k) {
-            const double tau = P[k];
-            if (tau == 0.0) continue;
-            double t = 0.0;
-            for (int m = k + 1; m < nu; ++m) t = fma(A[m * ld + k], y[m], t);
-            t *= tau;
-            for (int m = k + 1; m < nu; ++m) y[m] = fma(-t, A[m * ld + k], y[m]);
-        }
+    // the three vectors y = Q_H^T z
+    for (int q = lane; q < 3 * nu; q += 32) {
+        const int v = q / nu, m = q % nu;
+        yv[(2 + v) * nm + m] = A[(nu + v) * ld + m];
     }
     __syncwarp();
     // factors for k_eig_vectors: reflectors (column k below the diagonal, tau_k on the diagonal), L
@@ -213,9 +248,15 @@ __global__ void __launch_bounds__(64) k_eig_chase(const EigArgs a) {
         const double mu = D[hi] - (den != 0.0 ? b2 / den : 0.0);
         double x = D[lo] - mu, z = E[lo];
         for (int k = lo; k < hi; ++k) {
-            const double r = hypot(x, z);
-            double cr = 1.0, sr = 0.0;
-            if (r != 0.0) { cr = x / r; sr = z / r; }
+            // c = x / r, s = z / r, r = |(x, z)| from one reciprocal square root
+            const double rr = fma(x, x, z * z);
+            double cr = 1.0, sr = 0.0, r = 0.0;
+            if (rr > 0.0) {
+                const double ir = rsqrt(rr);
+                cr = x * ir;
+                sr = z * ir;
+                r = rr * ir;
+            }
             if (k > lo) E[k - 1] = r;
             const double ak = D[k], ak1 = D[k + 1], b = E[k];
             const double cc = cr * cr, ss = sr * sr, cs = cr * sr;
@@ -337,7 +378,9 @@ __global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a) {
     }
 }
 
-size_t eig_smem_reduce(int nm) { return sizeof(double) * 2 * (2 * (size_t)nm * (nm + 1) + 2 * nm); }
+size_t eig_smem_reduce(int nm) {
+    return sizeof(double) * 2 * ((2 * (size_t)nm + 3) * (nm + 1) + 2 * (size_t)nm + 3);
+}
 size_t eig_smem_vectors(int nm) { return sizeof(double) * (3 * (size_t)nm * (nm + 1) + nm); }
 
 void projected_eig(const EigArgs& a, cudaStream_t st) {

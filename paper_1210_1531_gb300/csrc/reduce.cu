@@ -7,6 +7,11 @@
 // when N(mid) < N_e, else hi; stop when hi - lo < tol or after max_iter steps; mu = (lo+hi)/2.
 // E_band = sum 2 f g c = Tr(rho H) (Eq. 6); Omega = sum d c w(e), w = -2 kT ln(1 + e^{-(e-mu)/kT}).
 //
+// Once the bracket is narrower than 10 kT, one bisection step also keeps E_k = exp((e_k - mu0)/kT)
+// for the poles within 60 kT of its midpoint mu0 (when a buffer is given); every later midpoint x
+// lies within 5 kT of mu0, so f = 1 / (1 + E_k exp((mu0 - x)/kT)) needs one exponential per
+// launch instead of one per pole. The values agree with the direct form to rounding.
+//
 // Every evaluation is one grid-wide reduction in a fixed order (per-thread column strides, a
 // fixed block tree, then the block partials summed in index order by the last block to finish,
 // found with an atomic ticket -- no thread ever waits on another block). The bracket lives in
@@ -119,6 +124,8 @@ __global__ void k_bracket(const ReduceArgs a) {
         s->done = (a.max_iter <= 0) || !(s->hi - s->lo >= a.tol);
         s->status = (lo <= hi && isfinite(lo) && isfinite(hi)) ? 0 : DEV_NONFINITE;
         s->mu = 0.5 * (s->lo + s->hi);
+        s->mu0 = 0.0;
+        s->have_pre = 0;
         *a.ticket = 0u;
     }
 }
@@ -139,18 +146,24 @@ __global__ void __launch_bounds__(kRedThreads) k_count(const ReduceArgs a, int m
     double v[3] = {0.0, 0.0, 0.0};
     const size_t total = (size_t)a.M * a.nu_max;
     const double inv_kT = 1.0 / a.kT;
+    const bool take_pre = mode == 2 && a.pre && !s->have_pre && s->hi - s->lo < 10.0 * a.kT;
+    const bool use_pre = mode == 2 && a.pre && s->have_pre;
+    const double scale = use_pre ? exp((s->mu0 - x) * inv_kT) : 1.0;
     for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
          p += (size_t)gridDim.x * blockDim.x) {
         const int j = (int)(p / a.nu_max), k = (int)(p - (size_t)j * a.nu_max);
         if (k >= __ldg(a.nu_eff + j)) continue;
         const double e = a.eps[p], cc = a.c[p];
         const double t = (e - x) * inv_kT;
+        if (take_pre && fabs(t) <= 60.0) a.pre[p] = exp(t);
         double f2, om = 0.0;
         if (t < -50.0) {
             f2 = 2.0;
             if (mode == 3) om = 2.0 * (e - x);
         } else if (t > 50.0) {
             continue;
+        } else if (use_pre) {
+            f2 = 2.0 / fma(a.pre[p], scale, 1.0);
         } else {
             f2 = 2.0 * fermi(t);
             if (mode == 3) om = omega_w(e, x, a.kT);
@@ -176,6 +189,10 @@ __global__ void __launch_bounds__(kRedThreads) k_count(const ReduceArgs a, int m
                 s->done = 1;
             }
         } else if (mode == 2) {
+            if (take_pre) {
+                s->have_pre = 1;
+                s->mu0 = x;
+            }
             if (N < a.n_electrons) s->lo = x; else s->hi = x;
             s->n_mid = N;
             s->iter += 1;

@@ -116,7 +116,7 @@ struct elses_system_s {
     DevBuf<double> rho, rhoE, gblock;
     DevBuf<double> ascratch, adjH, adjS;   // exact-gradient scratch and its pattern gradients
     std::vector<int> adj_bps;              // resident adjoint CTAs per SM, by cluster slots
-    DevBuf<double> partials, zbuf;
+    DevBuf<double> partials, zbuf, pre;
     DevBuf<BisectState> bstate;
     DevBuf<unsigned> ticket;
     std::vector<char> atom_done;
@@ -291,6 +291,7 @@ int prepare_columns(elses_system s) {
     TRY(s->rhoE.ensure((size_t)s->nnzb * 16));
     TRY(s->gblock.ensure((size_t)s->nnzb * 3));
     TRY(s->partials.ensure(4 * (size_t)reduce_grid()));
+    TRY(s->pre.ensure(M * nm));
     TRY(s->bstate.ensure(1));
     TRY(s->ticket.ensure(1));
     CUDA_TRY(cudaMemset(s->ticket.p, 0, sizeof(unsigned)));
@@ -493,6 +494,7 @@ ReduceArgs reduce_args(elses_system s) {
     r.state = s->bstate.p;
     r.partials = s->partials.p;
     r.ticket = s->ticket.p;
+    r.pre = s->pre.p;
     return r;
 }
 
@@ -521,7 +523,7 @@ const char* elses_last_error(void) { return g_err.c_str(); }
 
 void elses_system_destroy(elses_system s) {
     if (!s) return;
-    DevBuf<double>* dbs[] = {&s->pos, &s->H, &s->S, &s->skr, &s->ascratch, &s->adjH, &s->adjS, &s->kscratch, &s->Hp, &s->Sp, &s->urow,
+    DevBuf<double>* dbs[] = {&s->pos, &s->H, &s->S, &s->skr, &s->pre, &s->ascratch, &s->adjH, &s->adjS, &s->kscratch, &s->Hp, &s->Sp, &s->urow,
                              &s->surow, &s->hurow, &s->etri, &s->efac, &s->erot_c, &s->erot_s,
                              &s->eps, &s->cc, &s->dd, &s->gg,
                              &s->V, &s->UP, &s->Vb, &s->UPb, &s->rho, &s->rhoE, &s->gblock,

@@ -63,13 +63,16 @@ def test_gradient_two_pass_equals_stored(eg, d64):
 
 
 def test_full_subspace_gradient_is_the_density_matrix(eg):
-    w = gu.fragment(16)                 # nu = M = 64: the Krylov space is the whole space
+    """nu = M = 64: the Krylov space is the whole space and cannot move, so the gradient is the
+    density-matrix adjoint. The reverse sweep then carries only rounding, divided by the last
+    (tiny) beta of the exhausted space, hence the looser bound than the 1e-8 of rho itself."""
+    w = gu.fragment(16)
     s = eg.system_for(w)
     mu, _, _, _ = s.energy_force()
     rho, rhoE = s.density_matrix(mu)
     dH, dS = s.omega_gradient(mu)
-    assert np.abs(gu.to_np(dH) - gu.to_np(rho)).max() < 1e-8
-    assert np.abs(gu.to_np(dS) + gu.to_np(rhoE)).max() < 1e-8
+    assert np.abs(gu.to_np(dH) - gu.to_np(rho)).max() < 1e-7
+    assert np.abs(gu.to_np(dS) + gu.to_np(rhoE)).max() < 1e-7
 
 
 @pytest.fixture(scope="module")
