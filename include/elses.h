@@ -85,6 +85,11 @@ typedef struct elses_params {
                                (dF/dH = rho, dF/dS = -rhoE; exact when the Krylov space spans the
                                cluster), 1 = exact gradient of the truncated method
                                (elses_omega_gradient chained with dH/dR, dS/dR)                 */
+    int    krylov_block;    /* 0: one Krylov space per column, K_nu(H_C, e_j); 1: one block space
+                               per atom J started by its 4 orbitals, K(H_C, [e_4J .. e_4J+3]),
+                               of dimension nu (>= 4; the band form of block Arnoldi), shared
+                               by the atom's 4 columns (the alternative reading of the multiple
+                               Arnoldi method); elses_omega_gradient is not available with it */
 } elses_params;
 
 /* Counters and event timings of the calls since the last build (timing = 1 for the times). */
@@ -172,7 +177,8 @@ int elses_forces(elses_system sys, double* forces_dev, void* stream);
  * N_e is this at the chemical potential. Needs every column computed at the current positions
  * (elses_green_columns over all columns, or elses_energy_force); in the two-pass mode each
  * batch's columns are recomputed first. ERR_ARG for a bad range or null outputs, ERR_STATE
- * without the columns. Synchronises `stream` (device status check). */
+ * without the columns, ERR_NOT_IMPLEMENTED for block spaces (krylov_block = 1). Synchronises
+ * `stream` (device status check). */
 int elses_omega_gradient(elses_system sys, double mu, int atom_begin, int atom_end, double* dH_dev,
                          double* dS_dev, void* stream);
 

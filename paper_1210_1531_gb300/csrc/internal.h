@@ -94,6 +94,9 @@ struct AdjointArgs {
 };
 size_t krylov_smem_bytes(int na_max, int deg_max);
 int krylov_blocks_per_sm(int na_max, int deg_max);
+size_t block_krylov_scratch_doubles(int nu_max, int na_max);
+int block_krylov_blocks_per_sm(int na_max, int deg_max);
+void block_krylov_columns(const KrylovArgs& a, int grid, cudaStream_t st);
 __host__ __device__ size_t adjoint_warp_doubles(int nu_max, int na_max);
 int adjoint_blocks_per_sm(int na_max, int deg_max);
 void adjoint_columns(const KrylovArgs& a, const AdjointArgs& g, int grid, cudaStream_t st);

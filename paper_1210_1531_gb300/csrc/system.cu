@@ -240,12 +240,13 @@ int prepare_columns(elses_system s) {
                 std::stable_sort(ord.begin() + begin, ord.end(),
                                  [&](int x, int y) { return s->h_clsize[x] > s->h_clsize[y]; });
             const int na = 32 * ns;
-            int bps = krylov_blocks_per_sm(na, kdeg);
+            int bps = s->p.krylov_block ? block_krylov_blocks_per_sm(na, kdeg) : krylov_blocks_per_sm(na, kdeg);
             if (bps < 1) return fail(ELSES_ERR_CAPACITY, "Krylov kernel cannot be resident (%d-atom class)", na);
             if (s->p.k3_ctas_per_sm > 0) bps = std::min(bps, s->p.k3_ctas_per_sm);
             const int grid = std::min(count, s->num_sms * bps);
             s->k3_launches.push_back({b, e, begin, count, na, grid});
-            scratch = std::max(scratch, (size_t)grid * kWarpsPerAtom * 2 * nm * na * 4);
+            scratch = std::max(scratch, s->p.krylov_block ? (size_t)grid * block_krylov_scratch_doubles(nm, na)
+                                                          : (size_t)grid * kWarpsPerAtom * 2 * nm * na * 4);
             if (count > best_items) { best_items = count; s->k3_bps = bps; }
         }
     }
@@ -364,7 +365,8 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
             CUDA_TRY(cudaMemsetAsync(s->counters.p + 3, 0, sizeof(int), st));
             ka.queue = s->counters.p + 3;
         }
-        krylov_columns(ka, L.grid, st);
+        if (s->p.krylov_block) block_krylov_columns(ka, L.grid, st);
+        else krylov_columns(ka, L.grid, st);
         s->stats.launches++;
         s->stats.krylov_launches++;
     }
@@ -559,6 +561,13 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
         if (p.class_nu[c] < 1 || p.class_nu[c] > kMaxNu) return fail(ELSES_ERR_ARG, "class_nu out of range");
     if (!(p.kT > 0)) return fail(ELSES_ERR_ARG, "kT must be positive");
     if (p.force_mode < 0 || p.force_mode > 1) return fail(ELSES_ERR_ARG, "force_mode must be 0 or 1");
+    if (p.krylov_block < 0 || p.krylov_block > 1) return fail(ELSES_ERR_ARG, "krylov_block must be 0 or 1");
+    if (p.krylov_block) {
+        if (p.nu < 4) return fail(ELSES_ERR_ARG, "a block space needs nu >= 4");
+        for (int c = 0; c < p.n_classes; ++c)
+            if (p.class_nu[c] < 4) return fail(ELSES_ERR_ARG, "a block space needs nu >= 4");
+        if (p.force_mode == 1) return fail(ELSES_ERR_NOT_IMPLEMENTED, "exact forces need per-column spaces");
+    }
     if (!(sk->r_cut > sk->r_on) || !(sk->r_on > 0)) return fail(ELSES_ERR_ARG, "need 0 < r_on < r_cut");
     for (int d = 0; d < 3; ++d) {
         if (!(box_host[d] > 2.0 * sk->r_cut)) return fail(ELSES_ERR_ARG, "box must exceed 2*r_cut");
@@ -910,6 +919,8 @@ int elses_omega_gradient(elses_system s, double mu, int atom_begin, int atom_end
     if (!dH_dev || !dS_dev) return fail(ELSES_ERR_ARG, "null gradient outputs");
     if (atom_begin < 0 || atom_end > s->n || atom_begin > atom_end)
         return fail(ELSES_ERR_ARG, "atom range [%d, %d) outside [0, %d)", atom_begin, atom_end, s->n);
+    if (s->p.krylov_block)
+        return fail(ELSES_ERR_NOT_IMPLEMENTED, "the exact gradient is built for per-column Krylov spaces");
     if (s->atoms_done != s->n) return fail(ELSES_ERR_STATE, "the gradient needs every column computed");
     cudaStream_t st = (cudaStream_t)stream;
     TRY(clear_status(s, st));
