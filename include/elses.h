@@ -192,6 +192,19 @@ int elses_omega_gradient(elses_system sys, double mu, int atom_begin, int atom_e
 int elses_icohp(elses_system sys, const double* rho_dev, double* B_dev, double* Bsig_dev,
                 double* Bpi_dev, void* stream);
 
+/* Energy-resolved COHP (Eq. 4) and density of states at the complex energies z_host[n_z][2]
+ * (z = e + i eta, eta > 0: each pole's delta function of Im G(e + i0) becomes a Lorentzian of
+ * half-width eta): C_IJ(z) = -(1/pi) Im sum_ab H_(J,b);(I,a) G_(I,a);(J,b)(z) per block e = (I, J)
+ * of the pattern, with G from the poles and residues of the columns (elses_green_columns), its
+ * sigma and pi parts as in elses_icohp (off-site only), and DOS(z) = -(1/pi) Im Tr(G(z) S)
+ * = -(1/pi) Im sum_j sum_k d_k c_k / (z - e_k). Outputs: device double[nnzb][n_z] (C, C_sigma,
+ * C_pi; any may be NULL; sigma / pi need the Slater-Koster H) and host double[n_z] (dos, may be
+ * NULL). Needs every column computed; in the two-pass mode the batches are recomputed. Summed
+ * over blocks, C(z) is -(1/pi) Im sum_j sum_k g_k c_k / (z - e_k), the band-energy spectrum.
+ * Synchronises `stream`. */
+int elses_cohp_spectrum(elses_system sys, int n_z, const double* z_host, double* C_dev,
+                        double* Csig_dev, double* Cpi_dev, double* dos_host, void* stream);
+
 /* Copy-out accessors: each copies library data into caller-owned device buffers (any of which
  * may be NULL to skip it) on `stream`; sizes are returned through the host pointers first
  * (call once with NULL buffers to learn them). */

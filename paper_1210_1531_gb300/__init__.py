@@ -13,6 +13,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -62,7 +63,7 @@ class Stats(ctypes.Structure):
 EXPORTS = (
     "elses_build_clusters", "elses_set_hs", "elses_green_columns", "elses_find_mu",
     "elses_density_matrix", "elses_energies", "elses_energy_force", "elses_forces",
-    "elses_omega_gradient", "elses_icohp",
+    "elses_omega_gradient", "elses_icohp", "elses_cohp_spectrum",
     "elses_get_pattern",
     "elses_get_hs", "elses_get_clusters", "elses_get_spectra", "elses_get_stats",
     "elses_reset_stats", "elses_probe_fp64", "elses_find_mu_static", "elses_system_destroy",
@@ -93,6 +94,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "elses_icohp": [P, P, P, P, P, V],
         "elses_forces": [P, P, V],
         "elses_omega_gradient": [P, D, I, I, P, P, V],
+        "elses_cohp_spectrum": [P, I, pD, P, P, P, pD, V],
         "elses_get_pattern": [P, pI, P, P, V],
         "elses_get_hs": [P, P, P, V],
         "elses_get_clusters": [P, pLL, pI, P, P, V],
@@ -246,6 +248,20 @@ class System:
         _check(self._L.elses_omega_gradient(self._h, float(mu), int(atom_begin), int(atom_end), _ptr(dH),
                                             _ptr(dS), _stream(stream)))
         return dH, dS
+
+    def cohp_spectrum(self, z, sigma_pi=True, stream=None):
+        """Energy-resolved COHP per pattern block and the DOS at complex energies z (Eq. 4,
+        elses_cohp_spectrum): (C, C_sigma, C_pi) CUDA float64 [nnzb, n_z] (sigma / pi None unless
+        requested) and dos, a numpy array [n_z]."""
+        zs = [complex(v) for v in z]
+        zh = (ctypes.c_double * (2 * len(zs)))(*[x for v in zs for x in (v.real, v.imag)])
+        C = torch.empty((self.nnzb, len(zs)), dtype=torch.float64, device="cuda")
+        Cs = torch.empty_like(C) if sigma_pi else None
+        Cp = torch.empty_like(C) if sigma_pi else None
+        dos = (ctypes.c_double * len(zs))()
+        _check(self._L.elses_cohp_spectrum(self._h, len(zs), zh, _ptr(C), _ptr(Cs), _ptr(Cp), dos,
+                                           _stream(stream)))
+        return C, Cs, Cp, np.array(dos[:])
 
     def icohp(self, rho, stream=None):
         """(pi)COHP integrals per pattern block: (B, B_sigma, B_pi), CUDA float64 [nnzb] each."""

@@ -40,6 +40,9 @@ void forces(const double* pos, int n, const double L[3], const SKDev& sk, const 
             const double* rhoE, double* g_block, double* F, cudaStream_t st);
 void icohp(const double* pos, const double L[3], const SKDev& sk, const int* col_idx, const int* row_of,
            int nnzb, const double* H, const double* rho, double* B, double* Bsig, double* Bpi, cudaStream_t st);
+void cohp_spectrum(const double* pos, const double L[3], const SKDev& sk, const int* col_idx, const int* row_of,
+                   int nnzb, const double* H, const double* G, int n_zc, int iz0, int n_z, double* C,
+                   double* Csig, double* Cpi, cudaStream_t st);
 
 // ---------------------------------------------------------------- a3, a4 (krylov.cu)
 struct KrylovArgs {
@@ -161,6 +164,7 @@ int reduce_grid();
 void bisect_init(const ReduceArgs& a, cudaStream_t st);      // bracket + N(lo), N(hi)
 void bisect_step(const ReduceArgs& a, cudaStream_t st);      // one bisection step (no-op when done)
 void scalars_at(const ReduceArgs& a, double mu, cudaStream_t st);  // N, E_band, Omega at mu
+void dos_at(const ReduceArgs& a, const double* z_dev, int n_z, double* out_dev, cudaStream_t st);
 
 // ---------------------------------------------------------------- a8, G(z) (density.cu)
 struct DensityArgs {

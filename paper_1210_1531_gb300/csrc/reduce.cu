@@ -222,4 +222,32 @@ void scalars_at(const ReduceArgs& a, double mu, cudaStream_t st) {
     k_count<<<reduce_grid(), kRedThreads, 0, st>>>(a, 3, mu);
 }
 
+// Density of states -(1/pi) Im sum_j sum_k d_k c_k / (z - e_k) at the energies z[iz] (grid
+// (blocks, n_z)): per block a fixed-order tree, then one atomic addition per block into out[iz].
+__global__ void __launch_bounds__(kRedThreads) k_dos(const ReduceArgs a, const double* __restrict__ z, double* out) {
+    const int iz = blockIdx.y;
+    const double zr = z[2 * iz], zi = z[2 * iz + 1];
+    const size_t total = (size_t)a.M * a.nu_max;
+    double v = 0.0;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(p / a.nu_max), k = (int)(p - (size_t)j * a.nu_max);
+        if (k >= __ldg(a.nu_eff + j)) continue;
+        const double dr = zr - a.eps[p];
+        v = fma(a.d[p] * a.c[p], zi / fma(dr, dr, zi * zi), v);    // -Im 1/(z - e) = zi / |z - e|^2
+    }
+    __shared__ double sv[kRedThreads];
+    sv[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sv[threadIdx.x] += sv[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(out + iz, sv[0] * 0.31830988618379067154);
+}
+
+void dos_at(const ReduceArgs& a, const double* z_dev, int n_z, double* out_dev, cudaStream_t st) {
+    const dim3 grid(reduce_grid(), n_z);
+    k_dos<<<grid, kRedThreads, 0, st>>>(a, z_dev, out_dev);
+}
+
 }  // namespace elses

@@ -176,11 +176,59 @@ __global__ void k_icohp(const double* __restrict__ pos, double Lx, double Ly, do
     if (Bsig) Bsig[e] = (I != J) ? b - bpi : 0.0;
 }
 
+// Eq. 4 at complex energies: C_e(z) = -(1/pi) Im sum_ab H_e[a][b] G_e[a][b](z) for block e = (I, J)
+// (H symmetric: H_(J,b);(I,a) = H_e[a][b]) and its pi part from the V_pp_pi term of the p-p block,
+// for the n_zc energies of a chunk of G ([e*16 + q][n_zc][2]); outputs [e][n_z] from column iz0.
+__global__ void k_cohp(const double* __restrict__ pos, double Lx, double Ly, double Lz, SKDev sk,
+                       const int* __restrict__ col_idx, const int* __restrict__ row_of, int nnzb,
+                       const double* __restrict__ H, const double* __restrict__ G, int n_zc, int iz0, int n_z,
+                       double* __restrict__ C, double* __restrict__ Csig, double* __restrict__ Cpi) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)nnzb * n_zc) return;
+    const int e = (int)(t / n_zc), iz = (int)(t - (size_t)e * n_zc);
+    const double* g = G + (16 * (size_t)e * n_zc + iz) * 2 + 1;    // Im G_e[q], stride 2 n_zc
+    const size_t st = 2 * (size_t)n_zc;
+    double c = 0.0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) c = fma(H[16 * (size_t)e + q], g[q * st], c);
+    const double inv_pi = 0.31830988618379067154;
+    const size_t o = (size_t)e * n_z + iz0 + iz;
+    if (C) C[o] = -inv_pi * c;
+    if (!Csig && !Cpi) return;
+    const int I = row_of[e], J = col_idx[e];
+    double cpi = 0.0;
+    if (I != J) {
+        const double dx = min_image(pos[3 * J] - pos[3 * I], Lx);
+        const double dy = min_image(pos[3 * J + 1] - pos[3 * I + 1], Ly);
+        const double dz = min_image(pos[3 * J + 2] - pos[3 * I + 2], Lz);
+        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+        const double u[3] = {dx / r, dy / r, dz / r};
+        double V[4], dV[4];
+        sk_radial(sk, sk.V0, sk.qH, r, V, dV);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                cpi = fma(V[3] * ((i == k ? 1.0 : 0.0) - u[i] * u[k]), g[(4 * (1 + i) + 1 + k) * st], cpi);
+    }
+    if (Cpi) Cpi[o] = -inv_pi * cpi;
+    if (Csig) Csig[o] = (I != J) ? -inv_pi * (c - cpi) : 0.0;
+}
+
 void icohp(const double* pos, const double L[3], const SKDev& sk, const int* col_idx, const int* row_of,
            int nnzb, const double* H, const double* rho, double* B, double* Bsig, double* Bpi, cudaStream_t st) {
     const int T = 256;
     k_icohp<<<(nnzb + T - 1) / T, T, 0, st>>>(pos, L[0], L[1], L[2], sk, col_idx, row_of, nnzb, H, rho, B,
                                               Bsig, Bpi);
+}
+
+void cohp_spectrum(const double* pos, const double L[3], const SKDev& sk, const int* col_idx, const int* row_of,
+                   int nnzb, const double* H, const double* G, int n_zc, int iz0, int n_z, double* C,
+                   double* Csig, double* Cpi, cudaStream_t st) {
+    const int T = 256;
+    const size_t n = (size_t)nnzb * n_zc;
+    k_cohp<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(pos, L[0], L[1], L[2], sk, col_idx, row_of, nnzb, H, G,
+                                                      n_zc, iz0, n_z, C, Csig, Cpi);
 }
 
 }  // namespace elses

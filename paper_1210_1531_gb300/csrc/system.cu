@@ -116,7 +116,7 @@ struct elses_system_s {
     DevBuf<double> rho, rhoE, gblock;
     DevBuf<double> ascratch, adjH, adjS;   // exact-gradient scratch and its pattern gradients
     std::vector<int> adj_bps;              // resident adjoint CTAs per SM, by cluster slots
-    DevBuf<double> partials, zbuf, pre;
+    DevBuf<double> partials, zbuf, pre, gbuf, dosbuf;
     DevBuf<BisectState> bstate;
     DevBuf<unsigned> ticket;
     std::vector<char> atom_done;
@@ -525,7 +525,7 @@ const char* elses_last_error(void) { return g_err.c_str(); }
 
 void elses_system_destroy(elses_system s) {
     if (!s) return;
-    DevBuf<double>* dbs[] = {&s->pos, &s->H, &s->S, &s->skr, &s->pre, &s->ascratch, &s->adjH, &s->adjS, &s->kscratch, &s->Hp, &s->Sp, &s->urow,
+    DevBuf<double>* dbs[] = {&s->pos, &s->H, &s->S, &s->skr, &s->pre, &s->gbuf, &s->dosbuf, &s->ascratch, &s->adjH, &s->adjS, &s->kscratch, &s->Hp, &s->Sp, &s->urow,
                              &s->surow, &s->hurow, &s->etri, &s->efac, &s->erot_c, &s->erot_s,
                              &s->eps, &s->cc, &s->dd, &s->gg,
                              &s->V, &s->UP, &s->Vb, &s->UPb, &s->rho, &s->rhoE, &s->gblock,
@@ -911,6 +911,70 @@ int elses_energy_force(elses_system s, double* mu_host, double* e_band_host, dou
     if (e_band_host) *e_band_host = h.e_band;
     if (f_free_host) *f_free_host = h.omega + mu * s->p.n_electrons;
     return warn > 0 ? warn : rc;
+}
+
+int elses_cohp_spectrum(elses_system s, int n_z, const double* z_host, double* C_dev, double* Csig_dev,
+                        double* Cpi_dev, double* dos_host, void* stream) {
+    TRY(check_built(s));
+    if (n_z <= 0 || !z_host) return fail(ELSES_ERR_ARG, "need n_z > 0 energies");
+    if (!C_dev && !Csig_dev && !Cpi_dev && !dos_host) return fail(ELSES_ERR_ARG, "no output requested");
+    if ((Csig_dev || Cpi_dev) && s->user_hs)
+        return fail(ELSES_ERR_STATE, "the sigma / pi split needs the Slater-Koster H");
+    if (s->atoms_done != s->n) return fail(ELSES_ERR_STATE, "the spectra need every column");
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(clear_status(s, st));
+    TRY(s->zbuf.ensure(2 * (size_t)n_z));
+    CUDA_TRY(cudaMemcpyAsync(s->zbuf.p, z_host, sizeof(double) * 2 * n_z, cudaMemcpyHostToDevice, st));
+    if (dos_host) {
+        TRY(s->dosbuf.ensure(n_z));
+        CUDA_TRY(cudaMemsetAsync(s->dosbuf.p, 0, sizeof(double) * n_z, st));
+        dos_at(reduce_args(s), s->zbuf.p, n_z, s->dosbuf.p, st);
+        s->stats.launches++;
+    }
+    if (C_dev || Csig_dev || Cpi_dev) {
+        // G on the pattern for a chunk of energies at a time (at most 256 MB), then Eq. 4
+        const size_t per_z = (size_t)s->nnzb * 16 * 2;
+        const int chunk = (int)std::max<size_t>(1, std::min<size_t>(n_z, (size_t(1) << 25) / per_z));
+        TRY(s->gbuf.ensure(per_z * chunk));
+        for (int iz0 = 0; iz0 < n_z; iz0 += chunk) {
+            const int nzc = std::min(chunk, n_z - iz0);
+            for (int b = 0; b < s->n; b += s->batch_atoms) {
+                const int e = std::min(s->n, b + s->batch_atoms);
+                DensityArgs d = density_args(s, 0.0, nullptr, nullptr);
+                d.atom_begin = b;
+                d.atom_end = e;
+                if (s->p.two_pass) {   // the second calculation of G for this batch
+                    double *V = nullptr, *UP = nullptr;
+                    int v0 = 0, u0 = 0;
+                    TRY(run_batch(s, b, e, false, &V, &v0, &UP, &u0, st));
+                    d.V = V;
+                    d.v_col0 = v0;
+                    d.UP = UP;
+                    d.up_block0 = u0;
+                } else {
+                    d.V = s->V.p;
+                    d.v_col0 = 0;
+                    d.UP = s->UP.p;
+                    d.up_block0 = 0;
+                }
+                d.n_z = nzc;
+                d.z = s->zbuf.p + 2 * (size_t)iz0;
+                d.G = s->gbuf.p;
+                green_columns_eval(d, st);
+                s->stats.launches++;
+            }
+            cohp_spectrum(s->pos.p, s->box, s->skd, s->col_idx.p, s->row_of.p, s->nnzb, s->H.p, s->gbuf.p, nzc,
+                          iz0, n_z, C_dev, Csig_dev, Cpi_dev, st);
+            s->stats.launches++;
+        }
+    }
+    int rc = check_status(s, st);
+    if (rc < 0) return rc;
+    if (dos_host) {
+        CUDA_TRY(cudaMemcpyAsync(dos_host, s->dosbuf.p, sizeof(double) * n_z, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return rc;
 }
 
 int elses_omega_gradient(elses_system s, double mu, int atom_begin, int atom_end, double* dH_dev,
