@@ -49,7 +49,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=2048)
-    ap.add_argument("--k3-ctas", type=int, default=0, help="Krylov CTAs per SM (0: autotuned)")
+    ap.add_argument("--k3-ctas", type=int, default=0, help="Krylov CTAs per SM (0: as many as fit)")
+    ap.add_argument("--no-exact", action="store_true",
+                    help="skip the energy + exact-force step (gradient through the truncated Krylov build)")
     return ap.parse_args()
 
 
@@ -204,17 +206,17 @@ def run_ours(args):
     forces = torch.empty((w.n_atoms, 3), dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def make(schedule):
+    def make(schedule, exact_forces=False):
         return eg.System(pos_dev, w.box, w.sk, w.r_cluster, w.nu, w.kT, w.n_electrons,
                          nu_classes=w.nu_classes, schedule=schedule, timing=True,
-                         k3_ctas_per_sm=args.k3_ctas)
+                         k3_ctas_per_sm=args.k3_ctas, exact_forces=exact_forces)
 
     def step(s):
         s.rebuild(pos_dev)
         return s.energy_force(forces)
 
     keys = ("launches", "krylov_launches", "t_krylov_ms", "t_eig_ms", "t_bisect_ms",
-            "t_density_ms", "t_force_ms", "krylov_flops")
+            "t_density_ms", "t_force_ms", "krylov_flops", "t_adjoint_ms")
 
     def timed(s, k, w_steps, barrier=False):
         """w_steps untimed steps, then k steps each timed with CUDA events on the stream; the
@@ -282,6 +284,18 @@ def run_ours(args):
             e2e_times.append(a.elapsed_time(b))
     e2e_ms = sum(e2e_times) / len(e2e_times)
 
+    # the same step with exact forces (the gradient through the truncated Krylov build)
+    exact = None
+    if not args.no_exact:
+        ex = make(1, exact_forces=True)
+        xt, xst, _ = timed(ex, 2, 1)
+        x_ms = sum(xt) / len(xt)
+        exact = {"ms_per_step": x_ms, "value": M / (x_ms * 1e-3), "unit": "columns/s",
+                 "t_adjoint_ms": xst["t_adjoint_ms"] / 2,
+                 "note": "forces = exact gradient of Omega through the truncated Krylov build "
+                         "(finite-difference gated at 1e-5); 2 timed steps after 1 warm-up"}
+        ex.close()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "columns/s",
@@ -294,6 +308,7 @@ def run_ours(args):
                        "l2": "256 MB buffer written between timed steps",
                        "parallelism": f"replicas x{world}"},
             "plain": {"ms_per_step": plain_ms, "value": M / (plain_ms * 1e-3), "unit": "columns/s"},
+            "exact_forces": exact,
             "phases_ms_per_step": {k: stats[k] / args.steps for k in
                                    ("t_krylov_ms", "t_eig_ms", "t_bisect_ms", "t_density_ms", "t_force_ms")},
             "e2e": {"value": world * M / (e2e_ms * 1e-3), "unit": "columns/s", "ms_per_step": e2e_ms,
