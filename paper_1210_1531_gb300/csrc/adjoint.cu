@@ -35,9 +35,10 @@
 //  sampled on the blocks of the cluster (the 4 columns of the atom summed) and added atomically
 //  into the [nnzb][4][4] outputs.
 //
-// The forward recursion is recomputed here by the Krylov kernel's own code (column_forward with
-// kAdj: it also keeps HU and the Gram-Schmidt coefficients); V, e, c, d come from the columns
-// already computed for the same positions. One CTA of 4 warps per atom; the lanes own cluster
+// The bases come from the energy pass when it kept them (the Krylov kernel's store form),
+// otherwise the forward recursion is recomputed here by the Krylov kernel's own code
+// (column_forward with kAdj: it also keeps HU and the Gram-Schmidt coefficients); V, e, c, d
+// come from the columns already computed for the same positions. One CTA of 4 warps per atom; the lanes own cluster
 // rows as in the Krylov kernel; the bases and factors live in per-warp global scratch.
 #include "krylov.cuh"
 
@@ -279,20 +280,23 @@ __device__ __forceinline__ void reverse_sweep(const KrylovArgs& a, const Cluster
 }
 
 // dOmega/dH and dOmega/dS of block blk between cluster rows at rp4 = 4 p and columns at
-// cp4 = 4 p': sum over the atom's columns and n of Y[p][a][n] U[p'][b][n].
-__device__ __forceinline__ void sampled_block(const AdjointArgs& g, const int* nvw, int nm, int NA, size_t vs,
+// cp4 = 4 p': sum over the atom's columns and n of Y[p][a][n] U[p'][b][n] (Uw, YHw, YSw: the
+// warps' bases and factors).
+__device__ __forceinline__ void sampled_block(const AdjointArgs& g, const int* nvw, const double* const* Uw,
+                                              const double* const* YHw, const double* const* YSw, size_t vs,
                                               int rp4, int cp4, int blk) {
     double aH[16], aS[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) { aH[q] = 0.0; aS[q] = 0.0; }
-    const size_t wsz = adjoint_warp_doubles(nm, NA);
     for (int wi = 0; wi < kWarpsPerAtom; ++wi) {
-        const WarpScratch w = warp_scratch(g.scratch + ((size_t)blockIdx.x * kWarpsPerAtom + wi) * wsz, nm, NA);
+        const double* U = Uw[wi];
+        const double* YH = YHw[wi];
+        const double* YS = YSw[wi];
         for (int n = 0; n < nvw[wi]; ++n) {
             double2 x0, x1, y0, y1, z0, z1;
-            ld4(w.U + (size_t)n * vs + cp4, x0, x1);
-            ld4(w.YH + (size_t)n * vs + rp4, y0, y1);
-            ld4(w.YS + (size_t)n * vs + rp4, z0, z1);
+            ld4(U + (size_t)n * vs + cp4, x0, x1);
+            ld4(YH + (size_t)n * vs + rp4, y0, y1);
+            ld4(YS + (size_t)n * vs + rp4, z0, z1);
             const double xs[4] = {x0.x, x0.y, x1.x, x1.y};
             const double ys[4] = {y0.x, y0.y, y1.x, y1.y};
             const double zs[4] = {z0.x, z0.y, z1.x, z1.y};
@@ -329,9 +333,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_adjoint(const KrylovArgs a, con
     ClusterView v;
     carve_view(reinterpret_cast<unsigned char*>(hbuf + kWarpsPerAtom * kMaxNu), NA, a.deg_max, v);
     __shared__ int sh_atom, sh_nv[kWarpsPerAtom];
+    __shared__ const double* sh_U[kWarpsPerAtom];
+    __shared__ const double* sh_YH[kWarpsPerAtom];
+    __shared__ const double* sh_YS[kWarpsPerAtom];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const WarpScratch w =
+    const WarpScratch ws =
         warp_scratch(g.scratch + ((size_t)blockIdx.x * kWarpsPerAtom + warp) * adjoint_warp_doubles(nm, NA), nm, NA);
 
     for (int iter = 0;; ++iter) {
@@ -358,20 +365,39 @@ __global__ void __launch_bounds__(kThreads, 2) k_adjoint(const KrylovArgs a, con
         }
         const size_t vs = (size_t)v.NS * 32 * 4;
         int nv = 0;
+        WarpScratch w = ws;
         do {
             const int alpha = warp, j = 4 * J + alpha;
             double* A = vec + (size_t)(warp * 2) * NA * 4;
             double* B = A + (size_t)NA * 4;
             double* hb = hbuf + warp * kMaxNu;
-            int nu = 0, jp = 0;
-            nv = column_forward<true>(a, v, J, alpha, A, B, hb, w.U, w.SU, w.HU, w.hess, nu, jp);
-            if (nv <= 0) {
-                nv = 0;
-                break;
+            int jp = 0;
+            const double* Hpc;
+            if (g.bstore) {   // the bases the energy pass kept
+                const int aJ = bsearch_sorted(v.cl, v.n_at, J);
+                nv = aJ >= 0 ? a.nu_eff[j] : 0;
+                if (nv <= 0) {
+                    nv = 0;
+                    break;
+                }
+                jp = 4 * v.pos_of[aJ] + alpha;
+                double* col = const_cast<double*>(g.bstore) + (size_t)j * g.bstride;
+                w.U = col;
+                w.SU = col + g.bvec;
+                w.HU = col + 2 * g.bvec;
+                w.hess = col + 3 * g.bvec;
+                Hpc = w.hess + (size_t)nm * nm;
+            } else {
+                int nu = 0;
+                nv = column_forward<true>(a, v, J, alpha, A, B, hb, w.U, w.SU, w.HU, w.hess, nu, jp);
+                if (nv <= 0) {
+                    nv = 0;
+                    break;
+                }
+                Hpc = a.Hp + (size_t)(j - 4 * a.atom_begin) * (nm * (nm + 1) / 2);
             }
             __syncwarp();
             const double sq = 1.0 / w.U[jp];                   // sqrt(S_jj): u_1 = e_j / sqrt(S_jj)
-            const double* Hpc = a.Hp + (size_t)(j - 4 * a.atom_begin) * (nm * (nm + 1) / 2);
             rayleigh_ritz_gradient(g, g.V + (size_t)(j - g.v_col0) * nm * nm, g.eps + (size_t)j * nm,
                                    g.c + (size_t)j * nm, g.d + (size_t)j * nm, Hpc, w, nv, nm, vs, jp, sq, lane);
             // G_U = 2 (HU Hh + SU Sg) + e_j abar^T into Ubar
@@ -403,20 +429,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_adjoint(const KrylovArgs a, con
                 });
             }
         } while (0);
-        if (lane == 0) sh_nv[warp] = nv;
+        if (lane == 0) {
+            sh_nv[warp] = nv;
+            sh_U[warp] = w.U;
+            sh_YH[warp] = w.YH;
+            sh_YS[warp] = w.YS;
+        }
         __syncthreads();
         // sampled products over the cluster's blocks: lane l's list entries, every 4th from `warp`
         for (int k = warp; k < v.kmax; k += kWarpsPerAtom) {
             const Ent en = v.ell[32 * k + lane];
             if (en.blk < 0) continue;
             const int p = (en.p4 >> 16) * 32 + lane;
-            sampled_block(g, sh_nv, nm, NA, vs, 4 * p, en.p4 & 0xffff, en.blk);
+            sampled_block(g, sh_nv, sh_U, sh_YH, sh_YS, vs, 4 * p, en.p4 & 0xffff, en.blk);
         }
         if (a.onsite_diag) {   // on-site blocks are not list entries then
             for (int sl = warp; sl < v.NS; sl += kWarpsPerAtom) {
                 const int p = sl * 32 + lane;
                 const int es = v.eself[p];
-                if (es >= 0) sampled_block(g, sh_nv, nm, NA, vs, 4 * p, 4 * p, es);
+                if (es >= 0) sampled_block(g, sh_nv, sh_U, sh_YH, sh_YS, vs, 4 * p, 4 * p, es);
             }
         }
         __syncthreads();

@@ -78,6 +78,11 @@ struct KrylovArgs {
     int up_block0;
     int* status;
     unsigned long long* flops;   // algorithmic FP64 flops of the columns, accumulated
+    // optional per-column store of the bases for the exact gradient (nullptr: not kept):
+    // column j at bstore + j * bstride holds U, SU, HU (bvec doubles apart), then the
+    // Gram-Schmidt coefficients [nu_max][nu_max] and H' packed upper
+    double* bstore;
+    size_t bstride, bvec;
 };
 
 // Exact-gradient pass (adjoint.cu) over the columns of a batch; the KrylovArgs of the same batch
@@ -94,6 +99,8 @@ struct AdjointArgs {
     double s_scale;
     double* scratch;        // per resident CTA: 4 warps x adjoint_warp_doubles(nu_max, na_max)
     int atom_lo, atom_hi;   // only atoms in [atom_lo, atom_hi) are accumulated
+    const double* bstore;   // bases kept by the energy pass (KrylovArgs layout), or nullptr:
+    size_t bstride, bvec;   // then the forward recursion is recomputed
 };
 size_t krylov_smem_bytes(int na_max, int deg_max);
 int krylov_blocks_per_sm(int na_max, int deg_max);

@@ -31,6 +31,9 @@ size_t krylov_smem_bytes(int na_max, int deg_max) {
     return (b + 15) & ~(size_t)15;
 }
 
+// kStore: the bases of every column are kept in a.bstore (with HU, the Gram-Schmidt
+// coefficients and H') for the exact-gradient kernel, instead of the per-CTA scratch.
+template <bool kStore>
 __global__ void __launch_bounds__(kThreads, 3) k_krylov(const KrylovArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int NA = a.na_max;
@@ -70,9 +73,23 @@ __global__ void __launch_bounds__(kThreads, 3) k_krylov(const KrylovArgs a) {
             double* A = vec + (size_t)(warp * 2) * NA * 4;    // u_n (gather source of H u)
             double* B = A + (size_t)NA * 4;                      // H u_n, then w
             int nu = 0, jp = 0;
-            const int nu_eff = column_forward<false>(a, v, J, alpha, A, B, hbuf + warp * kMaxNu, Uw, SUw,
-                                                     nullptr, nullptr, nu, jp);
+            double *Ucol = Uw, *SUcol = SUw, *HUcol = nullptr, *hess = nullptr;
+            if constexpr (kStore) {
+                Ucol = a.bstore + (size_t)j * a.bstride;
+                SUcol = Ucol + a.bvec;
+                HUcol = SUcol + a.bvec;
+                hess = HUcol + a.bvec;
+            }
+            const int nu_eff = column_forward<kStore>(a, v, J, alpha, A, B, hbuf + warp * kMaxNu, Ucol, SUcol,
+                                                      HUcol, hess, nu, jp);
             if (nu_eff <= 0) break;   // bad input (flagged); the CTA barrier follows
+            if constexpr (kStore) {   // H' of the column beside its bases
+                __syncwarp();
+                const int PK = a.nu_max * (a.nu_max + 1) / 2;
+                const double* hp = a.Hp + (size_t)(j - 4 * a.atom_begin) * PK;
+                double* out = hess + (size_t)a.nu_max * a.nu_max;
+                for (int q = lane; q < PK; q += 32) out[q] = hp[q];
+            }
             if (lane == 0) {
                 a.nu_eff[j] = nu_eff;
                 if (nu_eff < nu) flag(a.status, DEV_BREAKDOWN);
@@ -101,7 +118,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_krylov(const KrylovArgs a) {
                     const int b = bsearch_sorted(v.cl, n_at, a.col_idx[e]);
                     const int p = v.pos_of[b];
                     double* out = a.UP + ((size_t)((e - a.up_block0) * 4 + alpha) * 4 + r) * a.nu_max;
-                    for (int k = 0; k < nu_eff; ++k) out[k] = Uw[4 * ((size_t)k * NP + p) + r];
+                    for (int k = 0; k < nu_eff; ++k) out[k] = Ucol[4 * ((size_t)k * NP + p) + r];
                 }
             }
         } while (0);
@@ -111,16 +128,21 @@ __global__ void __launch_bounds__(kThreads, 3) k_krylov(const KrylovArgs a) {
 
 int krylov_blocks_per_sm(int na_max, int deg_max) {
     const size_t smem = krylov_smem_bytes(na_max, deg_max);
-    cudaFuncSetAttribute(k_krylov, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_krylov<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_krylov, kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_krylov<false>, kThreads, smem);
     return nb;
 }
 
 void krylov_columns(const KrylovArgs& a, int grid, cudaStream_t st) {
     const size_t smem = krylov_smem_bytes(a.na_max, a.deg_max);
-    cudaFuncSetAttribute(k_krylov, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_krylov<<<grid, kThreads, smem, st>>>(a);
+    if (a.bstore) {
+        cudaFuncSetAttribute(k_krylov<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_krylov<true><<<grid, kThreads, smem, st>>>(a);
+    } else {
+        cudaFuncSetAttribute(k_krylov<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_krylov<false><<<grid, kThreads, smem, st>>>(a);
+    }
 }
 
 }  // namespace elses

@@ -115,6 +115,9 @@ struct elses_system_s {
     DevBuf<int> nu_eff, order;
     DevBuf<double> rho, rhoE, gblock;
     DevBuf<double> ascratch, adjH, adjS;   // exact-gradient scratch and its pattern gradients
+    DevBuf<double> bstore;                 // per-column bases kept for the exact gradient
+    size_t bstride = 0, bvec = 0;
+    bool use_store = false;
     std::vector<int> adj_bps;              // resident adjoint CTAs per SM, by cluster slots
     DevBuf<double> partials, zbuf, pre, gbuf, dosbuf;
     DevBuf<BisectState> bstate;
@@ -290,6 +293,18 @@ int prepare_columns(elses_system s) {
     }
     TRY(s->rho.ensure((size_t)s->nnzb * 16));
     TRY(s->rhoE.ensure((size_t)s->nnzb * 16));
+    // exact forces in the stored workflow: the Krylov pass keeps every column's bases (when they
+    // fit in 48 GB) so that the adjoint does not recompute them
+    s->use_store = false;
+    if (s->p.force_mode == 1 && !s->p.two_pass && !s->p.krylov_block) {
+        s->bvec = (size_t)nm * s->na_max * 4;
+        s->bstride = (3 * s->bvec + (size_t)nm * nm + (size_t)nm * (nm + 1) / 2 + 3) & ~(size_t)3;
+        const size_t need = M * s->bstride;
+        if (need * sizeof(double) <= (size_t(48) << 30)) {
+            TRY(s->bstore.ensure(need));
+            s->use_store = true;
+        }
+    }
     TRY(s->gblock.ensure((size_t)s->nnzb * 3));
     TRY(s->partials.ensure(4 * (size_t)reduce_grid()));
     TRY(s->pre.ensure(M * nm));
@@ -338,6 +353,9 @@ KrylovArgs krylov_args(elses_system s, int b, int e) {
     ka.nu_eff = s->nu_eff.p;
     ka.status = s->counters.p + 2;
     ka.flops = s->flops_ctr.p;
+    ka.bstore = s->use_store ? s->bstore.p : nullptr;
+    ka.bstride = s->bstride;
+    ka.bvec = s->bvec;
     return ka;
 }
 
@@ -453,6 +471,9 @@ int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* 
         ga.scratch = s->ascratch.p;
         ga.atom_lo = lo;
         ga.atom_hi = hi;
+        ga.bstore = s->use_store ? s->bstore.p : nullptr;
+        ga.bstride = s->bstride;
+        ga.bvec = s->bvec;
         KrylovArgs ka = krylov_args(s, b, e);
         ka.flops = nullptr;
         ka.UP = nullptr;
@@ -525,7 +546,7 @@ const char* elses_last_error(void) { return g_err.c_str(); }
 
 void elses_system_destroy(elses_system s) {
     if (!s) return;
-    DevBuf<double>* dbs[] = {&s->pos, &s->H, &s->S, &s->skr, &s->pre, &s->gbuf, &s->dosbuf, &s->ascratch, &s->adjH, &s->adjS, &s->kscratch, &s->Hp, &s->Sp, &s->urow,
+    DevBuf<double>* dbs[] = {&s->pos, &s->H, &s->S, &s->skr, &s->pre, &s->gbuf, &s->dosbuf, &s->bstore, &s->ascratch, &s->adjH, &s->adjS, &s->kscratch, &s->Hp, &s->Sp, &s->urow,
                              &s->surow, &s->hurow, &s->etri, &s->efac, &s->erot_c, &s->erot_s,
                              &s->eps, &s->cc, &s->dd, &s->gg,
                              &s->V, &s->UP, &s->Vb, &s->UPb, &s->rho, &s->rhoE, &s->gblock,

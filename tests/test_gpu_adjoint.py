@@ -124,3 +124,14 @@ def test_diamond4096_exact_forces_match_finite_differences(eg, d4096):
         checked += 1
     assert checked >= 3
     assert hf_gap > 1e-3
+
+
+def test_kept_bases_equal_recomputed_bases(eg, d64):
+    """With exact forces the Krylov pass keeps every column's bases and the adjoint reads them;
+    the gradient is the one of the recomputing path (d64 was built without exact forces)."""
+    s = eg.system_for(d64["w"], exact_forces=True)
+    mu, _, _, _ = s.energy_force()
+    assert mu == d64["mu"]
+    dH, dS = s.omega_gradient(mu)
+    assert np.abs(gu.to_np(dH) - d64["dH"]).max() <= 1e-12 * np.abs(d64["dH"]).max()
+    assert np.abs(gu.to_np(dS) - d64["dS"]).max() <= 1e-12 * np.abs(d64["dS"]).max()
