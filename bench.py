@@ -30,6 +30,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Green's-fn columns/sec & energy+force steps/sec at |drho|<=1e-10, batched vs plain"
 WORKLOAD = "diamond_4096"
+DESCRIPTION = {"diamond_4096": "disordered diamond (8x8x8 cells, sigma 0.1 A)",
+               "composite_32768": "graphite with diamond grains (sp2-sp3 composite)",
+               "amorphous_1m": "dense disordered carbon (3.0 g/cm3, sigma 0.3 A)",
+               "diamond_64": "disordered diamond (2x2x2 cells, sigma 0.05 A)"}
 FP64_NOMINAL_GFLOPS = 152 * 2 * 2 * 2.07     # SMs x FP64 FMA/clk/SM x 2 flops x GHz
 # DRAM bytes (read + write) of one k_krylov launch on the 4096-atom step, from the ncu capture in
 # profiles/k_krylov_diamond4096.md; valid only while krylov.cu is the source that was captured.
@@ -302,11 +306,7 @@ def run_ours(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "steps_per_s": 1e3 / ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: 4096-atom disordered diamond, sigma 0.1 A, "
-                                   f"cluster 6 A, nu {w.nu}, {M} columns, kT {w.kT} eV, full energy+force step",
-                       "columns_per_step": M, "schedule": "batched (persistent, size-sorted queue)",
-                       "l2": "256 MB buffer written between timed steps",
-                       "parallelism": f"replicas x{world}"},
+            "config": bench_config(args, w, world),
             "plain": {"ms_per_step": plain_ms, "value": M / (plain_ms * 1e-3), "unit": "columns/s"},
             "exact_forces": exact,
             "phases_ms_per_step": {k: stats[k] / args.steps for k in
@@ -333,6 +333,19 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def bench_config(args, w, world):
+    """The workload configuration both arms report."""
+    M = 4 * w.n_atoms
+    nu = "/".join(str(v) for _, v in w.nu_classes) + " by cluster size" if w.nu_classes else str(w.nu)
+    cl = f"{w.r_cluster:g} A" if w.r_cluster > 0 else "= whole system"
+    return {"workload": f"{args.workload}: {DESCRIPTION.get(args.workload, 'synthetic system')}, "
+                        f"{w.n_atoms} atoms, cluster {cl}, nu {nu}, {M} columns, "
+                        f"kT {w.kT} eV, full energy+force step",
+            "columns_per_step": M, "schedule": "batched (persistent, size-sorted queue)",
+            "l2": "256 MB buffer written between timed steps",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", 0))
     if rank != 0:
@@ -352,7 +365,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": M / v * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: oracle on a bounded sample per step"},
+        "config": bench_config(args, w, args.gpus),
         "cpu_baseline": {"value": v, "unit": "columns/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "columns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
