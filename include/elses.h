@@ -90,6 +90,8 @@ typedef struct elses_params {
                                of dimension nu (>= 4; the band form of block Arnoldi), shared
                                by the atom's 4 columns (the alternative reading of the multiple
                                Arnoldi method); elses_omega_gradient is not available with it */
+    int    batch_atoms;     /* atoms per Krylov -> eigensolver batch (0: automatic, sized by a
+                               memory budget); smaller batches need less device memory          */
 } elses_params;
 
 /* Counters and event timings of the calls since the last build (timing = 1 for the times). */

@@ -48,7 +48,8 @@ class Params(ctypes.Structure):
                 ("class_max_atoms", ctypes.c_int * 4), ("class_nu", ctypes.c_int * 4),
                 ("max_neighbors", ctypes.c_int), ("max_cluster", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("timing", ctypes.c_int), ("k3_ctas_per_sm", ctypes.c_int),
-                ("force_mode", ctypes.c_int), ("krylov_block", ctypes.c_int)]
+                ("force_mode", ctypes.c_int), ("krylov_block", ctypes.c_int),
+                ("batch_atoms", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -147,7 +148,7 @@ def make_sk(p) -> SK:
 def make_params(r_cluster, nu, kT, n_electrons, two_pass=False, nu_classes=(), schedule=0,
                 max_neighbors=0, max_cluster=0, breakdown_tol=0.0, mu_tol=0.0,
                 max_bisect=0, timing=False, k3_ctas_per_sm=0, exact_forces=False,
-                krylov_block=False) -> Params:
+                krylov_block=False, batch_atoms=0) -> Params:
     p = Params()
     p.r_cluster, p.kT, p.n_electrons = float(r_cluster), float(kT), float(n_electrons)
     p.breakdown_tol, p.mu_tol = float(breakdown_tol), float(mu_tol)
@@ -161,6 +162,7 @@ def make_params(r_cluster, nu, kT, n_electrons, two_pass=False, nu_classes=(), s
     p.k3_ctas_per_sm = int(k3_ctas_per_sm)
     p.force_mode = 1 if exact_forces else 0
     p.krylov_block = 1 if krylov_block else 0
+    p.batch_atoms = int(batch_atoms)
     return p
 
 
@@ -169,7 +171,8 @@ class System:
 
     def __init__(self, pos, box, sk, r_cluster, nu, kT, n_electrons, two_pass=False,
                  nu_classes=(), schedule=0, max_neighbors=0, max_cluster=0, timing=False,
-                 k3_ctas_per_sm=0, exact_forces=False, krylov_block=False, stream=None):
+                 k3_ctas_per_sm=0, exact_forces=False, krylov_block=False, batch_atoms=0,
+                 stream=None):
         self._L = load_library()
         self._h = ctypes.c_void_p(None)
         self.n = int(pos.shape[0])
@@ -178,7 +181,7 @@ class System:
         self.params = make_params(r_cluster, nu, kT, n_electrons, two_pass, nu_classes, schedule,
                                   max_neighbors, max_cluster, timing=timing,
                                   k3_ctas_per_sm=k3_ctas_per_sm, exact_forces=exact_forces,
-                                  krylov_block=krylov_block)
+                                  krylov_block=krylov_block, batch_atoms=batch_atoms)
         self.box = (ctypes.c_double * 3)(*[float(b) for b in box])
         self.rebuild(pos, stream)
 

@@ -24,6 +24,8 @@ namespace elses {
 __host__ __device__ size_t eig_tri_doubles(int nm) { return 5 * (size_t)nm; }        // D, E, yc, yd, yg
 __host__ __device__ size_t eig_fac_doubles(int nm) { return 2 * (size_t)nm * nm; }   // reflectors + tau, L
 __host__ __device__ size_t eig_rot_cap(int nm) { return 2 * (size_t)nm * nm + 64; }  // Givens rotations per column
+constexpr int kRotStage = 128;   // rotations staged in shared memory at a time (k_eig_vectors)
+constexpr int kChaseThreads = 64;  // columns per CTA of k_eig_chase
 
 // packed upper storage: element (i, k), i <= k, at i + k (k + 1) / 2
 __device__ __forceinline__ double packed(const double* P, int i, int k) {
@@ -209,18 +211,35 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
 }
 
 // ----------------------------------------------------------------------------- k_eig_chase
-__global__ void __launch_bounds__(64) k_eig_chase(const EigArgs a) {
+// A thread's array in shared memory, element i at p[i * kChaseThreads] (conflict-free: the
+// threads of a warp touch consecutive words for equal i).
+struct ThreadArray {
+    double* p;
+    __device__ __forceinline__ double& operator[](int i) const { return p[(size_t)i * kChaseThreads]; }
+};
+
+__global__ void __launch_bounds__(kChaseThreads) k_eig_chase(const EigArgs a) {
+    extern __shared__ double csm[];
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= a.ncols) return;
     const int nm = a.nu_max;
     const int j = a.col0 + c;
     const int nu = a.nu_eff[j];
-    double* t = a.tri + (size_t)c * eig_tri_doubles(nm);
-    double* D = t;
-    double* E = t + nm;
-    double* yc = t + 2 * nm;
-    double* yd = t + 3 * nm;
-    double* yg = t + 4 * nm;
+    // the thread's tridiagonal and three vectors move to shared memory for the chase: the
+    // latency of every access stays that of shared memory however many columns are in flight
+    double* base = csm + threadIdx.x;
+    const ThreadArray D{base}, E{base + (size_t)nm * kChaseThreads}, yc{base + 2 * (size_t)nm * kChaseThreads},
+        yd{base + 3 * (size_t)nm * kChaseThreads}, yg{base + 4 * (size_t)nm * kChaseThreads};
+    {
+        const double* t = a.tri + (size_t)c * eig_tri_doubles(nm);
+        for (int k = 0; k < nu; ++k) {
+            D[k] = t[k];
+            if (k + 1 < nu) E[k] = t[nm + k];
+            yc[k] = t[2 * nm + k];
+            yd[k] = t[3 * nm + k];
+            yg[k] = t[4 * nm + k];
+        }
+    }
     double* rc = a.rot_c + (size_t)c * eig_rot_cap(nm);
     double* rs = a.rot_s + (size_t)c * eig_rot_cap(nm);
     unsigned char* rk = a.rot_k + (size_t)c * eig_rot_cap(nm);
@@ -340,28 +359,40 @@ __global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a) {
         }
         __syncwarp();
     }
-    // Q <- Q R^T for every recorded rotation (columns k, k+1; lanes over rows)
+    // Q <- Q R^T for every recorded rotation (columns k, k+1; lanes over rows), the rotation list
+    // staged through shared memory 128 at a time with coalesced loads
     const int nrot = a.rot_n[c];
     const double* rc = a.rot_c + (size_t)c * eig_rot_cap(nm);
     const double* rs = a.rot_s + (size_t)c * eig_rot_cap(nm);
     const unsigned char* rk = a.rot_k + (size_t)c * eig_rot_cap(nm);
-    for (int r = 0; r < nrot; ++r) {
-        const double cr = __ldg(rc + r), sr = __ldg(rs + r);
-        const int k = __ldg(rk + r);
-        if (lane < nu) {
-            const double q0 = Q[lane * ld + k], q1 = Q[lane * ld + k + 1];
-            Q[lane * ld + k] = fma(cr, q0, sr * q1);
-            Q[lane * ld + k + 1] = fma(cr, q1, -sr * q0);
+    __shared__ double sc[kRotStage], ss[kRotStage];
+    __shared__ int sk[kRotStage];
+    for (int r0 = 0; r0 < nrot; r0 += kRotStage) {
+        const int cnt = min(kRotStage, nrot - r0);
+        for (int q = lane; q < cnt; q += 32) {
+            sc[q] = __ldg(rc + r0 + q);
+            ss[q] = __ldg(rs + r0 + q);
+            sk[q] = __ldg(rk + r0 + q);
         }
-        if (nu > 32) {
-            for (int q = lane + 32; q < nu; q += 32) {
-                const double q0 = Q[q * ld + k], q1 = Q[q * ld + k + 1];
-                Q[q * ld + k] = fma(cr, q0, sr * q1);
-                Q[q * ld + k + 1] = fma(cr, q1, -sr * q0);
+        __syncwarp();
+        for (int r = 0; r < cnt; ++r) {
+            const double cr = sc[r], sr = ss[r];
+            const int k = sk[r];
+            if (lane < nu) {
+                const double q0 = Q[lane * ld + k], q1 = Q[lane * ld + k + 1];
+                Q[lane * ld + k] = fma(cr, q0, sr * q1);
+                Q[lane * ld + k + 1] = fma(cr, q1, -sr * q0);
+            }
+            if (nu > 32) {
+                for (int q = lane + 32; q < nu; q += 32) {
+                    const double q0 = Q[q * ld + k], q1 = Q[q * ld + k + 1];
+                    Q[q * ld + k] = fma(cr, q0, sr * q1);
+                    Q[q * ld + k + 1] = fma(cr, q1, -sr * q0);
+                }
             }
         }
+        __syncwarp();
     }
-    __syncwarp();
     // V = L^-T Q in place (lanes over columns m, rows bottom-up)
     for (int m = lane; m < nu; m += 32)
         for (int i = nu - 1; i >= 0; --i) {
@@ -388,7 +419,9 @@ void projected_eig(const EigArgs& a, cudaStream_t st) {
     cudaFuncSetAttribute(k_eig_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
     cudaFuncSetAttribute(k_eig_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s3);
     k_eig_reduce<<<(a.ncols + 1) / 2, 64, s1, st>>>(a);
-    k_eig_chase<<<(a.ncols + 63) / 64, 64, 0, st>>>(a);
+    const size_t s2 = sizeof(double) * 5 * (size_t)a.nu_max * kChaseThreads;
+    cudaFuncSetAttribute(k_eig_chase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2);
+    k_eig_chase<<<(a.ncols + kChaseThreads - 1) / kChaseThreads, kChaseThreads, s2, st>>>(a);
     k_eig_vectors<<<a.ncols, 32, s3, st>>>(a);
 }
 

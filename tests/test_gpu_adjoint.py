@@ -135,3 +135,19 @@ def test_kept_bases_equal_recomputed_bases(eg, d64):
     dH, dS = s.omega_gradient(mu)
     assert np.abs(gu.to_np(dH) - d64["dH"]).max() <= 1e-12 * np.abs(d64["dH"]).max()
     assert np.abs(gu.to_np(dS) - d64["dS"]).max() <= 1e-12 * np.abs(d64["dS"]).max()
+
+
+@pytest.mark.slow
+def test_composite_sampled_atoms_match_oracle(eg):
+    """sp2-sp3 composite with nu by cluster size (20 / 30 / 40): sampled atoms of each class."""
+    w = wl.make("composite_32768")
+    s = eg.system_for(w, exact_forces=True)
+    mu, _, _, _ = s.energy_force()
+    cp, cidx, _ = s.clusters()
+    sizes = np.diff(gu.to_np(cp))
+    picks = [int(np.argmin(sizes)), int(np.argmax(sizes)), int(np.argmin(np.abs(sizes - 150)))]
+    for J in picks:
+        dH, dS = s.omega_gradient(mu, J, J + 1)
+        _, _, oH, oS, _ = adjoint.pattern_gradient(w, mu, cols=np.arange(4 * J, 4 * J + 4))
+        assert _rel(gu.to_np(dH), oH) < GRAD_TOL, (J, sizes[J])
+        assert _rel(gu.to_np(dS), oS) < GRAD_TOL, (J, sizes[J])
