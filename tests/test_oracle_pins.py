@@ -383,3 +383,15 @@ def test_icohp_pi_part_equals_pp_pi_only_hamiltonian(diamond64):
     Bp_ref = np.einsum("eab,eab->e", Hpi, res["rho"])
     assert np.abs(Bp[off] - Bp_ref[off]).max() < 1e-12
     assert np.abs(Bp[~off]).max() == 0.0 and np.abs(Bs[~off]).max() == 0.0
+
+
+def test_single_atom_closed_forms():
+    """One isolated atom: every column is an invariant one-dimensional space with the on-site
+    energy as its pole; with 4 electrons the s level holds 2 and the three p levels share 2, so
+    f(Ep - mu) = 1/3, mu = Ep - kT ln 2 and E_band = 2 Es + 2 Ep (to e^-(Ep - Es)/kT)."""
+    w = wl.Workload("atom", np.array([[10.0, 10.0, 10.0]]), np.full(3, 20.0), SK, r_cluster=0.0, nu=8)
+    res = pipeline.run(w)
+    assert [c.nu_eff for c in res["columns"]] == [1, 1, 1, 1]
+    assert abs(res["mu"] - (SK.Ep - w.kT * np.log(2.0))) < 1e-12
+    assert abs(res["E_band"] - (2 * SK.Es + 2 * SK.Ep)) < 1e-11
+    assert np.abs(res["forces"]).max() == 0.0
