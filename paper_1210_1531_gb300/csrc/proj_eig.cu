@@ -16,7 +16,8 @@
 //                 bulge chase) -- the sequential part -- rotating the three vectors along, so
 //                 that they become c, d, g; the rotations are recorded.
 //   k_eig_vectors one warp per column: Q_H from the Householder reflectors, the recorded
-//                 rotations applied to its columns (lanes over rows), V = L^-T Q.
+//                 rotations applied to its columns (lanes over rows) in their fast (scaled)
+//                 form, two FMAs per row each, then the column scales, V = L^-T Q.
 #include "internal.h"
 
 namespace elses {
@@ -26,6 +27,22 @@ __host__ __device__ size_t eig_fac_doubles(int nm) { return 2 * (size_t)nm * nm;
 __host__ __device__ size_t eig_rot_cap(int nm) { return 2 * (size_t)nm * nm + 64; }  // Givens rotations per column
 constexpr int kRotStage = 128;   // rotations staged in shared memory at a time (k_eig_vectors)
 constexpr int kChaseThreads = 64;  // columns per CTA of k_eig_chase
+
+// The lower-triangle pairs (i, m), lo <= m <= i < hi, in row-major order, 32 at a time from
+// `lane`: f(i, m) for each pair the lane owns. Trailing-block updates spread this way keep all
+// lanes busy (lanes over rows leave most of them idle as the block shrinks), and on this part an
+// FP64 warp instruction costs the same whatever the number of active lanes.
+template <typename F>
+__device__ __forceinline__ void lower_pairs(int lo, int hi, int lane, F f) {
+    const int n = hi - lo;
+    int r = 0, q = lane;                       // row r = i - lo holds the r + 1 pairs q = 0 .. r
+    while (r < n && q > r) { q -= r + 1; ++r; }
+    while (r < n) {
+        f(lo + r, lo + q);
+        q += 32;
+        while (r < n && q > r) { q -= r + 1; ++r; }
+    }
+}
 
 // packed upper storage: element (i, k), i <= k, at i + k (k + 1) / 2
 __device__ __forceinline__ double packed(const double* P, int i, int k) {
@@ -66,10 +83,9 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
         for (int i = k + 1 + lane; i < nu; i += 32) L[i * ld + k] *= ik;
         if (lane == 0) { L[k * ld + k] = lkk; inv[k] = ik; }
         __syncwarp();
-        for (int i = k + 1 + lane; i < nu; i += 32) {
-            const double lik = L[i * ld + k];
-            for (int m = k + 1; m <= i; ++m) L[i * ld + m] = fma(-lik, L[m * ld + k], L[i * ld + m]);
-        }
+        lower_pairs(k + 1, nu, lane, [&](int i, int m) {
+            L[i * ld + m] = fma(-L[i * ld + k], L[m * ld + k], L[i * ld + m]);
+        });
         __syncwarp();
     }
     if (!spd) {
@@ -141,7 +157,8 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
     }
     __syncwarp();
     // Householder reduction: reflector k stored in column k below the diagonal, tau_k kept; the
-    // vector rows are reflected along (y = Q_H^T z)
+    // vector rows are reflected along (y = Q_H^T z). The trailing block is kept in its lower
+    // triangle only (read symmetrically).
     double* E = yv + nm;
     for (int k = 0; k + 2 < nu; ++k) {
         double part = 0.0;
@@ -162,7 +179,7 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
         double kp = 0.0;
         for (int i = k + 1 + lane; i < nu + 3; i += 32) {
             double s = 0.0;
-            for (int m = k + 1; m < nu; ++m) s = fma(A[i * ld + m], A[m * ld + k], s);
+            for (int m = k + 1; m < nu; ++m) s = fma(m <= i ? A[i * ld + m] : A[m * ld + i], A[m * ld + k], s);
             s *= tau;
             P[i] = s;
             if (i < nu) kp = fma(A[i * ld + k], s, kp);
@@ -171,11 +188,9 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
         __syncwarp();
         for (int i = k + 1 + lane; i < nu; i += 32) P[i] = fma(-K, A[i * ld + k], P[i]);
         __syncwarp();
-        for (int i = k + 1 + lane; i < nu; i += 32) {
-            const double vi = A[i * ld + k], qi = P[i];
-            for (int m = k + 1; m < nu; ++m)
-                A[i * ld + m] = fma(-vi, P[m], fma(-qi, A[m * ld + k], A[i * ld + m]));
-        }
+        lower_pairs(k + 1, nu, lane, [&](int i, int m) {
+            A[i * ld + m] = fma(-A[i * ld + k], P[m], fma(-P[i], A[m * ld + k], A[i * ld + m]));
+        });
         for (int m = k + 1 + lane; m < nu; m += 32) {   // y_q -= t_q v
             const double vm = A[m * ld + k];
 #pragma unroll
@@ -229,13 +244,15 @@ __global__ void __launch_bounds__(kChaseThreads) k_eig_chase(const EigArgs a) {
     // latency of every access stays that of shared memory however many columns are in flight
     double* base = csm + threadIdx.x;
     const ThreadArray D{base}, E{base + (size_t)nm * kChaseThreads}, yc{base + 2 * (size_t)nm * kChaseThreads},
-        yd{base + 3 * (size_t)nm * kChaseThreads}, yg{base + 4 * (size_t)nm * kChaseThreads};
+        yd{base + 3 * (size_t)nm * kChaseThreads}, yg{base + 4 * (size_t)nm * kChaseThreads},
+        dl{base + 5 * (size_t)nm * kChaseThreads};
     {
         const double* t = a.tri + (size_t)c * eig_tri_doubles(nm);
         for (int k = 0; k < nu; ++k) {
             D[k] = t[k];
             if (k + 1 < nu) E[k] = t[nm + k];
             yc[k] = t[2 * nm + k];
+            dl[k] = 1.0;
             yd[k] = t[3 * nm + k];
             yg[k] = t[4 * nm + k];
         }
@@ -295,14 +312,37 @@ __global__ void __launch_bounds__(kChaseThreads) k_eig_chase(const EigArgs a) {
             yd[k] = cr * u0 + sr * u1; yd[k + 1] = cr * u1 - sr * u0;
             u0 = yg[k]; u1 = yg[k + 1];
             yg[k] = cr * u0 + sr * u1; yg[k + 1] = cr * u1 - sr * u0;
-            rc[nrot] = cr;
-            rs[nrot] = sr;
-            rk[nrot] = (unsigned char)k;
+            // the rotation in fast (scaled) form for the eigenvector kernel, Q = Qs diag(dl):
+            //   |c| >= |s|: qs_k += a qs_k+1,  qs_k+1 += b qs_k             (dl_k, dl_k+1 *= c)
+            //   otherwise:  qs_k = a qs_k + qs_k+1,  qs_k+1 = b qs_k+1 - qs_k  (dl_k, dl_k+1 = s dl_k+1, s dl_k)
+            const double d0 = dl[k], d1 = dl[k + 1];
+            double fa, fb;
+            unsigned char form;
+            if (fabs(cr) >= fabs(sr)) {
+                fa = (sr * d1) / (cr * d0);
+                fb = -(sr * d0) / (cr * d1);
+                dl[k] = d0 * cr;
+                dl[k + 1] = d1 * cr;
+                form = 0;
+            } else {
+                fa = (cr * d0) / (sr * d1);
+                fb = (cr * d1) / (sr * d0);
+                dl[k] = d1 * sr;
+                dl[k + 1] = d0 * sr;
+                form = 0x80;
+            }
+            rc[nrot] = fa;
+            rs[nrot] = fb;
+            rk[nrot] = (unsigned char)k | form;
             ++nrot;
         }
     }
     if (!ok) flag(a.status, DEV_TIMEOUT);
     a.rot_n[c] = ok ? (int)nrot : 0;
+    {   // the column scales of the fast rotations, where D was (D is not read after the chase)
+        double* t = a.tri + (size_t)c * eig_tri_doubles(nm);
+        for (int k = 0; k < nu; ++k) t[k] = ok ? dl[k] : 1.0;
+    }
     // ascending order; perm[out] = index into the unsorted arrays
     int* perm = a.perm + (size_t)c * nm;
     for (int k = 0; k < nu; ++k) perm[k] = k;
@@ -376,23 +416,31 @@ __global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a) {
         }
         __syncwarp();
         for (int r = 0; r < cnt; ++r) {
-            const double cr = sc[r], sr = ss[r];
-            const int k = sk[r];
-            if (lane < nu) {
-                const double q0 = Q[lane * ld + k], q1 = Q[lane * ld + k + 1];
-                Q[lane * ld + k] = fma(cr, q0, sr * q1);
-                Q[lane * ld + k + 1] = fma(cr, q1, -sr * q0);
-            }
-            if (nu > 32) {
-                for (int q = lane + 32; q < nu; q += 32) {
+            const double fa = sc[r], fb = ss[r];
+            const int k = sk[r] & 0x7f;
+            const bool swapped = (sk[r] & 0x80) != 0;
+            if (swapped) {   // the form is the same for every lane
+                for (int q = lane; q < nu; q += 32) {
                     const double q0 = Q[q * ld + k], q1 = Q[q * ld + k + 1];
-                    Q[q * ld + k] = fma(cr, q0, sr * q1);
-                    Q[q * ld + k + 1] = fma(cr, q1, -sr * q0);
+                    Q[q * ld + k] = fma(fa, q0, q1);
+                    Q[q * ld + k + 1] = fma(fb, q1, -q0);
+                }
+            } else {
+                for (int q = lane; q < nu; q += 32) {
+                    const double q0 = Q[q * ld + k], q1 = Q[q * ld + k + 1];
+                    Q[q * ld + k] = fma(fa, q1, q0);
+                    Q[q * ld + k + 1] = fma(fb, q0, q1);
                 }
             }
         }
         __syncwarp();
     }
+    {   // Q = Qs diag(dl)
+        const double* dl = a.tri + (size_t)c * eig_tri_doubles(nm);
+        for (int i = lane; i < nu; i += 32)
+            for (int n = 0; n < nu; ++n) Q[i * ld + n] *= dl[n];
+    }
+    __syncwarp();
     // V = L^-T Q in place (lanes over columns m, rows bottom-up)
     for (int m = lane; m < nu; m += 32)
         for (int i = nu - 1; i >= 0; --i) {
@@ -419,7 +467,7 @@ void projected_eig(const EigArgs& a, cudaStream_t st) {
     cudaFuncSetAttribute(k_eig_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
     cudaFuncSetAttribute(k_eig_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s3);
     k_eig_reduce<<<(a.ncols + 1) / 2, 64, s1, st>>>(a);
-    const size_t s2 = sizeof(double) * 5 * (size_t)a.nu_max * kChaseThreads;
+    const size_t s2 = sizeof(double) * 6 * (size_t)a.nu_max * kChaseThreads;
     cudaFuncSetAttribute(k_eig_chase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2);
     k_eig_chase<<<(a.ncols + kChaseThreads - 1) / kChaseThreads, kChaseThreads, s2, st>>>(a);
     k_eig_vectors<<<a.ncols, 32, s3, st>>>(a);
