@@ -10,19 +10,17 @@
 // of active lanes, so every FP64 instruction must carry work on all lanes:
 //   k_eig_reduce  one warp per column, matrices in shared memory: Cholesky, the reduction
 //                 A = L^-1 H' L^-T and the Householder reduction of A to tridiagonal form T
-//                 (lanes over rows / columns); the three vectors L^-1 (U, SU, HU)_j are taken
-//                 to the tridiagonal basis.
+//                 (lanes over rows / columns); the three vectors z = L^-1 (U, SU, HU)_j.
 //   k_eig_chase   one thread per column: implicit-shift QR sweeps on T (Wilkinson shift, Givens
-//                 bulge chase) -- the sequential part -- rotating the three vectors along, so
-//                 that they become c, d, g; the rotations are recorded.
+//                 bulge chase) -- the sequential part; the rotations are recorded.
 //   k_eig_vectors one warp per column: Q_H from the Householder reflectors, the recorded
-//                 rotations applied to its columns (lanes over rows) in their fast (scaled)
-//                 form, two FMAs per row each, then the column scales, V = L^-T Q.
+//                 rotations applied to its columns (lanes over rows), the spectra c, d, g = Q^T z
+//                 of the three vectors, V = L^-T Q.
 #include "internal.h"
 
 namespace elses {
 
-__host__ __device__ size_t eig_tri_doubles(int nm) { return 5 * (size_t)nm; }        // D, E, yc, yd, yg
+__host__ __device__ size_t eig_tri_doubles(int nm) { return 5 * (size_t)nm; }        // D, E, z (3 vectors)
 __host__ __device__ size_t eig_fac_doubles(int nm) { return 2 * (size_t)nm * nm; }   // reflectors + tau, L
 __host__ __device__ size_t eig_rot_cap(int nm) { return 2 * (size_t)nm * nm + 64; }  // Givens rotations per column
 constexpr int kRotStage = 128;   // rotations staged in shared memory at a time (k_eig_vectors)
@@ -56,10 +54,10 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
     const int c = blockIdx.x * (blockDim.x >> 5) + wib;
     if (c >= a.ncols) return;
     const int nm = a.nu_max, ld = nm + 1;
-    double* A = sm + (size_t)wib * ((2 * nm + 3) * ld + 2 * nm + 3);
-    double* L = A + (nm + 3) * ld;  // A: the matrix, then the three vectors as rows nu .. nu + 2
+    double* A = sm + (size_t)wib * (2 * nm * ld + 2 * nm);
+    double* L = A + nm * ld;
     double* inv = L + nm * ld;     // 1 / L_ii
-    double* P = inv + nm;          // Householder work vector (nm + 3)
+    double* P = inv + nm;          // Householder work vector
     double* yv = a.tri + (size_t)c * eig_tri_doubles(nm);   // D, E, yc, yd, yg (global)
     const int j = a.col0 + c;
     const int nu = a.nu_eff[j];
@@ -115,8 +113,8 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
             A[k * ld + i] = v;
         }
     __syncwarp();
-    // the three vectors z = L^-1 (U, SU, HU)_j into rows nu .. nu + 2 of A: a column sweep with
-    // lanes over rows (rows lane and lane + 32), row m final at step m
+    // the three vectors z = L^-1 (U, SU, HU)_j for k_eig_vectors (which forms c, d, g = Q^T z):
+    // a column sweep with lanes over rows (rows lane and lane + 32), row m final at step m
     {
         const double* src[3] = {a.urow + (size_t)c * nm, a.surow + (size_t)c * nm, a.hurow + (size_t)c * nm};
         double z0[3], z1[3];
@@ -151,14 +149,13 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
         }
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            if (lane < nu) A[(nu + q) * ld + lane] = z0[q];
-            if (lane + 32 < nu) A[(nu + q) * ld + lane + 32] = z1[q];
+            if (lane < nu) yv[(2 + q) * nm + lane] = z0[q];
+            if (lane + 32 < nu) yv[(2 + q) * nm + lane + 32] = z1[q];
         }
     }
     __syncwarp();
-    // Householder reduction: reflector k stored in column k below the diagonal, tau_k kept; the
-    // vector rows are reflected along (y = Q_H^T z). The trailing block is kept in its lower
-    // triangle only (read symmetrically).
+    // Householder reduction: reflector k stored in column k below the diagonal, tau_k kept. The
+    // trailing block is kept in its lower triangle only (read symmetrically).
     double* E = yv + nm;
     for (int k = 0; k + 2 < nu; ++k) {
         double part = 0.0;
@@ -174,15 +171,14 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
         const double tau = 1.0 / (alpha * (alpha - x0));
         if (lane == 0) A[(k + 1) * ld + k] = x0 - alpha;
         __syncwarp();
-        // p = tau A v (rows i > k); the same sweep gives t_q = tau v^T y_q for the vector rows,
-        // in lanes the matrix rows leave idle
+        // p = tau A v (rows i > k)
         double kp = 0.0;
-        for (int i = k + 1 + lane; i < nu + 3; i += 32) {
+        for (int i = k + 1 + lane; i < nu; i += 32) {
             double s = 0.0;
             for (int m = k + 1; m < nu; ++m) s = fma(m <= i ? A[i * ld + m] : A[m * ld + i], A[m * ld + k], s);
             s *= tau;
             P[i] = s;
-            if (i < nu) kp = fma(A[i * ld + k], s, kp);
+            kp = fma(A[i * ld + k], s, kp);
         }
         const double K = 0.5 * tau * warp_sum(kp);
         __syncwarp();
@@ -191,11 +187,6 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
         lower_pairs(k + 1, nu, lane, [&](int i, int m) {
             A[i * ld + m] = fma(-A[i * ld + k], P[m], fma(-P[i], A[m * ld + k], A[i * ld + m]));
         });
-        for (int m = k + 1 + lane; m < nu; m += 32) {   // y_q -= t_q v
-            const double vm = A[m * ld + k];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) A[(nu + q) * ld + m] = fma(-P[nu + q], vm, A[(nu + q) * ld + m]);
-        }
         __syncwarp();
         if (lane == 0) { E[k] = alpha; P[k] = tau; }   // P[k] keeps tau_k (P[i > k] reused later)
         __syncwarp();
@@ -208,12 +199,6 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
         // the last two reflector slots are unused: mark them
         P[nu - 2] = 0.0;
         P[nu - 1] = 0.0;
-    }
-    __syncwarp();
-    // the three vectors y = Q_H^T z
-    for (int q = lane; q < 3 * nu; q += 32) {
-        const int v = q / nu, m = q % nu;
-        yv[(2 + v) * nm + m] = A[(nu + v) * ld + m];
     }
     __syncwarp();
     // factors for k_eig_vectors: reflectors (column k below the diagonal, tau_k on the diagonal), L
@@ -240,21 +225,15 @@ __global__ void __launch_bounds__(kChaseThreads) k_eig_chase(const EigArgs a) {
     const int nm = a.nu_max;
     const int j = a.col0 + c;
     const int nu = a.nu_eff[j];
-    // the thread's tridiagonal and three vectors move to shared memory for the chase: the
-    // latency of every access stays that of shared memory however many columns are in flight
+    // the thread's tridiagonal moves to shared memory for the chase: the latency of every access
+    // stays that of shared memory however many columns are in flight
     double* base = csm + threadIdx.x;
-    const ThreadArray D{base}, E{base + (size_t)nm * kChaseThreads}, yc{base + 2 * (size_t)nm * kChaseThreads},
-        yd{base + 3 * (size_t)nm * kChaseThreads}, yg{base + 4 * (size_t)nm * kChaseThreads},
-        dl{base + 5 * (size_t)nm * kChaseThreads};
+    const ThreadArray D{base}, E{base + (size_t)nm * kChaseThreads};
     {
         const double* t = a.tri + (size_t)c * eig_tri_doubles(nm);
         for (int k = 0; k < nu; ++k) {
             D[k] = t[k];
             if (k + 1 < nu) E[k] = t[nm + k];
-            yc[k] = t[2 * nm + k];
-            dl[k] = 1.0;
-            yd[k] = t[3 * nm + k];
-            yg[k] = t[4 * nm + k];
         }
     }
     double* rc = a.rot_c + (size_t)c * eig_rot_cap(nm);
@@ -305,44 +284,14 @@ __global__ void __launch_bounds__(kChaseThreads) k_eig_chase(const EigArgs a) {
                 E[k + 1] = cr * bn;
                 x = E[k];
             }
-            // the three vectors follow P^T: y <- R y on rows k, k+1
-            double u0 = yc[k], u1 = yc[k + 1];
-            yc[k] = cr * u0 + sr * u1; yc[k + 1] = cr * u1 - sr * u0;
-            u0 = yd[k]; u1 = yd[k + 1];
-            yd[k] = cr * u0 + sr * u1; yd[k + 1] = cr * u1 - sr * u0;
-            u0 = yg[k]; u1 = yg[k + 1];
-            yg[k] = cr * u0 + sr * u1; yg[k + 1] = cr * u1 - sr * u0;
-            // the rotation in fast (scaled) form for the eigenvector kernel, Q = Qs diag(dl):
-            //   |c| >= |s|: qs_k += a qs_k+1,  qs_k+1 += b qs_k             (dl_k, dl_k+1 *= c)
-            //   otherwise:  qs_k = a qs_k + qs_k+1,  qs_k+1 = b qs_k+1 - qs_k  (dl_k, dl_k+1 = s dl_k+1, s dl_k)
-            const double d0 = dl[k], d1 = dl[k + 1];
-            double fa, fb;
-            unsigned char form;
-            if (fabs(cr) >= fabs(sr)) {
-                fa = (sr * d1) / (cr * d0);
-                fb = -(sr * d0) / (cr * d1);
-                dl[k] = d0 * cr;
-                dl[k + 1] = d1 * cr;
-                form = 0;
-            } else {
-                fa = (cr * d0) / (sr * d1);
-                fb = (cr * d1) / (sr * d0);
-                dl[k] = d1 * sr;
-                dl[k + 1] = d0 * sr;
-                form = 0x80;
-            }
-            rc[nrot] = fa;
-            rs[nrot] = fb;
-            rk[nrot] = (unsigned char)k | form;
+            rc[nrot] = cr;
+            rs[nrot] = sr;
+            rk[nrot] = (unsigned char)k;
             ++nrot;
         }
     }
     if (!ok) flag(a.status, DEV_TIMEOUT);
     a.rot_n[c] = ok ? (int)nrot : 0;
-    {   // the column scales of the fast rotations, where D was (D is not read after the chase)
-        double* t = a.tri + (size_t)c * eig_tri_doubles(nm);
-        for (int k = 0; k < nu; ++k) t[k] = ok ? dl[k] : 1.0;
-    }
     // ascending order; perm[out] = index into the unsorted arrays
     int* perm = a.perm + (size_t)c * nm;
     for (int k = 0; k < nu; ++k) perm[k] = k;
@@ -352,17 +301,7 @@ __global__ void __launch_bounds__(kChaseThreads) k_eig_chase(const EigArgs a) {
             if (D[perm[q]] < D[perm[m]]) m = q;
         const int tmp = perm[k]; perm[k] = perm[m]; perm[m] = tmp;
     }
-    for (int k = 0; k < nm; ++k) {
-        double e = 0.0, cv = 0.0, dv = 0.0, gv = 0.0;
-        if (k < nu && ok) {
-            const int p = perm[k];
-            e = D[p]; cv = yc[p]; dv = yd[p]; gv = yg[p];
-        }
-        a.eps[(size_t)j * nm + k] = e;
-        a.c[(size_t)j * nm + k] = cv;
-        a.d[(size_t)j * nm + k] = dv;
-        a.g[(size_t)j * nm + k] = gv;
-    }
+    for (int k = 0; k < nm; ++k) a.eps[(size_t)j * nm + k] = (k < nu && ok) ? D[perm[k]] : 0.0;
 }
 
 // ----------------------------------------------------------------------------- k_eig_vectors
@@ -416,31 +355,40 @@ __global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a) {
         }
         __syncwarp();
         for (int r = 0; r < cnt; ++r) {
-            const double fa = sc[r], fb = ss[r];
-            const int k = sk[r] & 0x7f;
-            const bool swapped = (sk[r] & 0x80) != 0;
-            if (swapped) {   // the form is the same for every lane
-                for (int q = lane; q < nu; q += 32) {
-                    const double q0 = Q[q * ld + k], q1 = Q[q * ld + k + 1];
-                    Q[q * ld + k] = fma(fa, q0, q1);
-                    Q[q * ld + k + 1] = fma(fb, q1, -q0);
-                }
-            } else {
-                for (int q = lane; q < nu; q += 32) {
-                    const double q0 = Q[q * ld + k], q1 = Q[q * ld + k + 1];
-                    Q[q * ld + k] = fma(fa, q1, q0);
-                    Q[q * ld + k + 1] = fma(fb, q0, q1);
-                }
+            const double cr = sc[r], sr = ss[r];
+            const int k = sk[r];
+            for (int q = lane; q < nu; q += 32) {
+                const double q0 = Q[q * ld + k], q1 = Q[q * ld + k + 1];
+                Q[q * ld + k] = fma(cr, q0, sr * q1);
+                Q[q * ld + k + 1] = fma(cr, q1, -sr * q0);
             }
         }
         __syncwarp();
     }
-    {   // Q = Qs diag(dl)
-        const double* dl = a.tri + (size_t)c * eig_tri_doubles(nm);
-        for (int i = lane; i < nu; i += 32)
-            for (int n = 0; n < nu; ++n) Q[i * ld + n] *= dl[n];
+    // spectra c, d, g = Q^T z of the three vectors z = L^-1 (U, SU, HU)_j, in ascending order of
+    // the poles (lanes over poles)
+    {
+        const double* z = a.tri + (size_t)c * eig_tri_doubles(nm) + 2 * nm;
+        double* zs = inv + nm;
+        for (int q = lane; q < 3 * nu; q += 32) zs[(q / nu) * nm + q % nu] = z[(q / nu) * nm + q % nu];
+        __syncwarp();
+        const int* pm = a.perm + (size_t)c * nm;
+        for (int k = lane; k < nm; k += 32) {
+            double sc_ = 0.0, sd = 0.0, sg = 0.0;
+            if (k < nu) {
+                const int p = pm[k];
+                for (int n = 0; n < nu; ++n) {
+                    const double q = Q[n * ld + p];
+                    sc_ = fma(q, zs[n], sc_);
+                    sd = fma(q, zs[nm + n], sd);
+                    sg = fma(q, zs[2 * nm + n], sg);
+                }
+            }
+            a.c[(size_t)j * nm + k] = sc_;
+            a.d[(size_t)j * nm + k] = sd;
+            a.g[(size_t)j * nm + k] = sg;
+        }
     }
-    __syncwarp();
     // V = L^-T Q in place (lanes over columns m, rows bottom-up)
     for (int m = lane; m < nu; m += 32)
         for (int i = nu - 1; i >= 0; --i) {
@@ -457,17 +405,15 @@ __global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a) {
     }
 }
 
-size_t eig_smem_reduce(int nm) {
-    return sizeof(double) * 2 * ((2 * (size_t)nm + 3) * (nm + 1) + 2 * (size_t)nm + 3);
-}
-size_t eig_smem_vectors(int nm) { return sizeof(double) * (3 * (size_t)nm * (nm + 1) + nm); }
+size_t eig_smem_reduce(int nm) { return sizeof(double) * 2 * (2 * (size_t)nm * (nm + 1) + 2 * (size_t)nm); }
+size_t eig_smem_vectors(int nm) { return sizeof(double) * (3 * (size_t)nm * (nm + 1) + 4 * (size_t)nm); }
 
 void projected_eig(const EigArgs& a, cudaStream_t st) {
     const size_t s1 = eig_smem_reduce(a.nu_max), s3 = eig_smem_vectors(a.nu_max);
     cudaFuncSetAttribute(k_eig_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
     cudaFuncSetAttribute(k_eig_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s3);
     k_eig_reduce<<<(a.ncols + 1) / 2, 64, s1, st>>>(a);
-    const size_t s2 = sizeof(double) * 6 * (size_t)a.nu_max * kChaseThreads;
+    const size_t s2 = sizeof(double) * 2 * (size_t)a.nu_max * kChaseThreads;
     cudaFuncSetAttribute(k_eig_chase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2);
     k_eig_chase<<<(a.ncols + kChaseThreads - 1) / kChaseThreads, kChaseThreads, s2, st>>>(a);
     k_eig_vectors<<<a.ncols, 32, s3, st>>>(a);
