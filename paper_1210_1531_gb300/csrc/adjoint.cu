@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adjoint(const KrylovArgs a, con
 
 int adjoint_blocks_per_sm(int na_max, int deg_max) {
     const size_t smem = krylov_smem_bytes(na_max, deg_max);
-    cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_at_least(k_adjoint, smem);
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adjoint, kThreads, smem);
     return nb;
@@ -464,7 +464,7 @@ int adjoint_blocks_per_sm(int na_max, int deg_max) {
 
 void adjoint_columns(const KrylovArgs& a, const AdjointArgs& g, int grid, cudaStream_t st) {
     const size_t smem = krylov_smem_bytes(a.na_max, a.deg_max);
-    cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_at_least(k_adjoint, smem);
     k_adjoint<<<grid, kThreads, smem, st>>>(a, g);
 }
 

@@ -361,7 +361,7 @@ size_t block_krylov_scratch_doubles(int nu_max, int na_max) {
 
 int block_krylov_blocks_per_sm(int na_max, int deg_max) {
     const size_t smem = krylov_smem_bytes(na_max, deg_max);
-    cudaFuncSetAttribute(k_block_krylov, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_at_least(k_block_krylov, smem);
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_block_krylov, kThreads, smem);
     return nb;
@@ -369,7 +369,7 @@ int block_krylov_blocks_per_sm(int na_max, int deg_max) {
 
 void block_krylov_columns(const KrylovArgs& a, int grid, cudaStream_t st) {
     const size_t smem = krylov_smem_bytes(a.na_max, a.deg_max);
-    cudaFuncSetAttribute(k_block_krylov, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_at_least(k_block_krylov, smem);
     k_block_krylov<<<grid, kThreads, smem, st>>>(a);
 }
 

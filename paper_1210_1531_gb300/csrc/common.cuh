@@ -22,6 +22,20 @@ enum : int {
 constexpr int kMaxNu = 64;          // Krylov dimension limit (registers / shared arrays)
 constexpr int kWarpsPerAtom = 4;    // one warp per orbital column of an atom
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` and never lowers it: the limit
+// is a property of the function, shared by every system on the device, and after the first
+// launches no attribute call stays on the launch path (where it could order launches that are
+// meant to overlap).
+template <typename Kernel>
+inline void smem_at_least(Kernel kernel, size_t bytes) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes >= bytes) return;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    // the whole L1 / shared split as shared memory: launches of the same kernel with different
+    // footprints (the cluster size classes) then share one SM configuration and can co-reside
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+}
+
 __device__ __forceinline__ void flag(int* st, int f) { atomicOr(st, f); }
 
 // Fermi-Dirac occupation f = 1 / (1 + exp(x)), x = (e - mu) / kT, without overflow.

@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_krylov(const KrylovArgs a) {
 
 int krylov_blocks_per_sm(int na_max, int deg_max) {
     const size_t smem = krylov_smem_bytes(na_max, deg_max);
-    cudaFuncSetAttribute(k_krylov<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_at_least(k_krylov<false>, smem);
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_krylov<false>, kThreads, smem);
     return nb;
@@ -137,10 +137,10 @@ int krylov_blocks_per_sm(int na_max, int deg_max) {
 void krylov_columns(const KrylovArgs& a, int grid, cudaStream_t st) {
     const size_t smem = krylov_smem_bytes(a.na_max, a.deg_max);
     if (a.bstore) {
-        cudaFuncSetAttribute(k_krylov<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        smem_at_least(k_krylov<true>, smem);
         k_krylov<true><<<grid, kThreads, smem, st>>>(a);
     } else {
-        cudaFuncSetAttribute(k_krylov<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        smem_at_least(k_krylov<false>, smem);
         k_krylov<false><<<grid, kThreads, smem, st>>>(a);
     }
 }

@@ -271,7 +271,7 @@ void fill_lists(const double* pos, int n, const CellGrid& g, const int* cell_of,
     const int W = 8;
     const size_t smem = sizeof(int) * (size_t)cap * W;
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_lists<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        smem_at_least(k_lists<true>, smem);
     k_lists<true><<<(n + W - 1) / W, 32 * W, smem, st>>>(pos, n, g, cell_of, cell_start, cell_atoms, r,
                                                          reach[0], reach[1], reach[2], nullptr, nullptr,
                                                          ptr, idx, cap, status);

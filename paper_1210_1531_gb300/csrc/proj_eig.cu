@@ -410,11 +410,11 @@ size_t eig_smem_vectors(int nm) { return sizeof(double) * (3 * (size_t)nm * (nm 
 
 void projected_eig(const EigArgs& a, cudaStream_t st) {
     const size_t s1 = eig_smem_reduce(a.nu_max), s3 = eig_smem_vectors(a.nu_max);
-    cudaFuncSetAttribute(k_eig_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
-    cudaFuncSetAttribute(k_eig_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s3);
+    smem_at_least(k_eig_reduce, s1);
+    smem_at_least(k_eig_vectors, s3);
     k_eig_reduce<<<(a.ncols + 1) / 2, 64, s1, st>>>(a);
     const size_t s2 = sizeof(double) * 2 * (size_t)a.nu_max * kChaseThreads;
-    cudaFuncSetAttribute(k_eig_chase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2);
+    smem_at_least(k_eig_chase, s2);
     k_eig_chase<<<(a.ncols + kChaseThreads - 1) / kChaseThreads, kChaseThreads, s2, st>>>(a);
     k_eig_vectors<<<a.ncols, 32, s3, st>>>(a);
 }

@@ -95,7 +95,7 @@ struct elses_system_s {
     DevBuf<int> cell_of, cell_count, cell_start, cursor, cell_atoms;
     DevBuf<int> row_cnt, row_ptr, col_idx, row_of, tmap;
     DevBuf<int> cl_cnt, cl_ptr, cl_idx;
-    DevBuf<int> counters;   // [0] max neighbours, [1] max cluster, [2] status, [3] queue
+    DevBuf<int> counters;   // see kCounters
     DevBuf<unsigned long long> flops_ctr;
     DevBuf<double> H, S, skr;
     int nnzb = 0, max_nb = 0, max_cl = 0;
@@ -105,7 +105,11 @@ struct elses_system_s {
     int nu_max = 0, na_max = 0, k3_grid = 0, batch_atoms = 0, deg_cap = 0, k3_bps = 0;
     // Krylov launches: per batch of atoms, one launch per cluster size class (slots of 32 atoms),
     // each with its own shared-memory footprint and resident-CTA count
-    struct K3Launch { int batch_begin, batch_end, item_begin, item_count, na, grid; };
+    // scratch_off: where the launch's per-CTA scratch starts, so that the class launches of one
+    // batch can run at the same time
+    struct K3Launch { int batch_begin, batch_end, item_begin, item_count, na, grid; size_t scratch_off; };
+    cudaStream_t side = nullptr;           // second stream for concurrent class launches
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<K3Launch> k3_launches;
     std::vector<int> h_clsize;
     DevBuf<double> kscratch, Hp, Sp, urow, surow, hurow, etri, efac, erot_c, erot_s;
@@ -171,6 +175,10 @@ struct elses_system_s {
 };
 
 enum { T_KRYLOV = 0, T_EIG = 1, T_BISECT = 2, T_DENSITY = 3, T_FORCE = 4, T_ADJOINT = 5 };
+// device counters: [0] max neighbours, [1] max cluster, [2] status, [3] unused, [8..] the work
+// queues of the class launches of a batch (one each, so that they can run at the same time)
+constexpr int kQueue0 = 8;
+constexpr int kCounters = 24;
 
 namespace {
 
@@ -240,6 +248,7 @@ int prepare_columns(elses_system s) {
     int best_items = -1;
     for (int b = 0; b < s->n; b += s->batch_atoms) {
         const int e = std::min(s->n, b + s->batch_atoms);
+        size_t batch_off = 0;
         for (int ns = s->na_max / 32; ns >= 1; --ns) {
             const int begin = (int)ord.size();
             for (int a = b; a < e; ++a)
@@ -254,9 +263,10 @@ int prepare_columns(elses_system s) {
             if (bps < 1) return fail(ELSES_ERR_CAPACITY, "Krylov kernel cannot be resident (%d-atom class)", na);
             if (s->p.k3_ctas_per_sm > 0) bps = std::min(bps, s->p.k3_ctas_per_sm);
             const int grid = std::min(count, s->num_sms * bps);
-            s->k3_launches.push_back({b, e, begin, count, na, grid});
-            scratch = std::max(scratch, s->p.krylov_block ? (size_t)grid * block_krylov_scratch_doubles(nm, na)
-                                                          : (size_t)grid * kWarpsPerAtom * 2 * nm * na * 4);
+            s->k3_launches.push_back({b, e, begin, count, na, grid, batch_off});
+            batch_off += s->p.krylov_block ? (size_t)grid * block_krylov_scratch_doubles(nm, na)
+                                           : (size_t)grid * kWarpsPerAtom * 2 * nm * na * 4;
+            scratch = std::max(scratch, batch_off);
             if (count > best_items) { best_items = count; s->k3_bps = bps; }
         }
     }
@@ -327,6 +337,23 @@ int prepare_columns(elses_system s) {
 
 // Krylov build + projected eigenproblem for atoms [b, e). Writes V and UP either to the stored
 // arrays or to the batch buffers (two-pass), returning the pointers used.
+// The second stream: work launched on it after fork_side runs beside `st` until join_side.
+int fork_side(elses_system s, cudaStream_t st) {
+    if (!s->side) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
+    }
+    CUDA_TRY(cudaEventRecord(s->ev_fork, st));
+    CUDA_TRY(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
+    return 0;
+}
+int join_side(elses_system s, cudaStream_t st) {
+    CUDA_TRY(cudaEventRecord(s->ev_join, s->side));
+    CUDA_TRY(cudaStreamWaitEvent(st, s->ev_join, 0));
+    return 0;
+}
+
 // Krylov-kernel arguments for atoms [b, e) (the launch fields are set per size class).
 KrylovArgs krylov_args(elses_system s, int b, int e) {
     const int nm = s->nu_max;
@@ -379,22 +406,33 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
     }
     if (!need_rows) ka.UP = nullptr;
     s->tic(T_KRYLOV, st);
-    for (const auto& L : s->k3_launches) {
-        if (L.batch_begin != b) continue;
+    std::vector<const elses_system_s::K3Launch*> ls;
+    for (const auto& L : s->k3_launches)
+        if (L.batch_begin == b) ls.push_back(&L);
+    // batched form: the largest class (few atoms, long CTAs) runs beside the others on a second
+    // stream, so that its partial wave does not leave SMs idle
+    const bool conc = s->p.schedule == 1 && ls.size() >= 2;
+    if (conc) TRY(fork_side(s, st));
+    for (size_t i = 0; i < ls.size(); ++i) {
+        const auto& L = *ls[i];
+        cudaStream_t lst = (conc && i == 0) ? s->side : st;
         ka.na_max = L.na;
         ka.order = s->order.p + L.item_begin;
         ka.n_items = L.item_count;
+        ka.scratch = s->kscratch.p + L.scratch_off;
         ka.queue = nullptr;
         if (s->p.schedule == 1) {
             // batched form: persistent CTAs pull atoms from the size-sorted queue
-            CUDA_TRY(cudaMemsetAsync(s->counters.p + 3, 0, sizeof(int), st));
-            ka.queue = s->counters.p + 3;
+            int* q = s->counters.p + kQueue0 + (int)std::min<size_t>(i, kCounters - kQueue0 - 1);
+            CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(int), lst));
+            ka.queue = q;
         }
-        if (s->p.krylov_block) block_krylov_columns(ka, L.grid, st);
-        else krylov_columns(ka, L.grid, st);
+        if (s->p.krylov_block) block_krylov_columns(ka, L.grid, lst);
+        else krylov_columns(ka, L.grid, lst);
         s->stats.launches++;
         s->stats.krylov_launches++;
     }
+    if (conc) TRY(join_side(s, st));
     s->toc(st);
 
     EigArgs ea{};
@@ -445,13 +483,17 @@ int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* 
     if ((int)s->adj_bps.size() != s->na_max / 32 + 1) s->adj_bps.assign(s->na_max / 32 + 1, 0);
     size_t need = 0;
     std::vector<int> grid(s->k3_launches.size(), 0);
-    for (size_t i = 0; i < s->k3_launches.size(); ++i) {
+    std::vector<size_t> off(s->k3_launches.size(), 0);
+    for (size_t i = 0, used = 0; i < s->k3_launches.size(); ++i) {
         const auto& L = s->k3_launches[i];
         int& bps = s->adj_bps[L.na / 32];
         if (bps == 0) bps = adjoint_blocks_per_sm(L.na, kdeg);
         if (bps < 1) return fail(ELSES_ERR_CAPACITY, "adjoint kernel cannot be resident (%d-atom class)", L.na);
         grid[i] = std::min(L.item_count, s->num_sms * bps);
-        need = std::max(need, (size_t)grid[i] * kWarpsPerAtom * adjoint_warp_doubles(nm, L.na));
+        if (i == 0 || L.batch_begin != s->k3_launches[i - 1].batch_begin) used = 0;
+        off[i] = used;     // the class launches of a batch run at the same time: own scratch each
+        used += (size_t)grid[i] * kWarpsPerAtom * adjoint_warp_doubles(nm, L.na);
+        need = std::max(need, used);
     }
     TRY(s->ascratch.ensure(need));
     for (int b = 0; b < s->n; b += s->batch_atoms) {
@@ -485,17 +527,27 @@ int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* 
         ka.flops = nullptr;
         ka.UP = nullptr;
         s->tic(T_ADJOINT, st);
-        for (size_t i = 0; i < s->k3_launches.size(); ++i) {
+        std::vector<size_t> li;
+        for (size_t i = 0; i < s->k3_launches.size(); ++i)
+            if (s->k3_launches[i].batch_begin == b) li.push_back(i);
+        const bool conc = li.size() >= 2;   // the largest class beside the others, as for the Krylov pass
+        if (conc) TRY(fork_side(s, st));
+        for (size_t t = 0; t < li.size(); ++t) {
+            const size_t i = li[t];
             const auto& L = s->k3_launches[i];
-            if (L.batch_begin != b) continue;
+            cudaStream_t lst = (conc && t == 0) ? s->side : st;
             ka.na_max = L.na;
             ka.order = s->order.p + L.item_begin;
             ka.n_items = L.item_count;
-            CUDA_TRY(cudaMemsetAsync(s->counters.p + 3, 0, sizeof(int), st));
-            ka.queue = s->counters.p + 3;
-            adjoint_columns(ka, ga, grid[i], st);
+            int* q = s->counters.p + kQueue0 + (int)std::min<size_t>(t, kCounters - kQueue0 - 1);
+            CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(int), lst));
+            ka.queue = q;
+            AdjointArgs gl = ga;
+            gl.scratch = s->ascratch.p + off[i];
+            adjoint_columns(ka, gl, grid[i], lst);
             s->stats.launches++;
         }
+        if (conc) TRY(join_side(s, st));
         s->toc(st);
     }
     CUDA_TRY(cudaGetLastError());
@@ -568,6 +620,12 @@ void elses_system_destroy(elses_system s) {
     for (auto* b : ibs) b->release();
     s->bstate.release();
     s->ticket.release();
+    if (s->side) {
+        cudaStreamSynchronize(s->side);
+        cudaStreamDestroy(s->side);
+        cudaEventDestroy(s->ev_fork);
+        cudaEventDestroy(s->ev_join);
+    }
     delete s;
 }
 
@@ -636,8 +694,8 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
     const int n = n_atoms;
     TRY(s->pos.ensure(3 * (size_t)n));
     CUDA_TRY(cudaMemcpyAsync(s->pos.p, pos_dev, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st));
-    TRY(s->counters.ensure(8));
-    CUDA_TRY(cudaMemsetAsync(s->counters.p, 0, sizeof(int) * 8, st));
+    TRY(s->counters.ensure(kCounters));
+    CUDA_TRY(cudaMemsetAsync(s->counters.p, 0, sizeof(int) * kCounters, st));
     TRY(s->flops_ctr.ensure(1));
     CUDA_TRY(cudaMemsetAsync(s->flops_ctr.p, 0, sizeof(unsigned long long), st));
     check_finite(s->pos.p, 3 * n, s->counters.p + 2, st);
