@@ -123,8 +123,8 @@ struct EigArgs {
     const double* surow;
     const double* hurow;
     const int* nu_eff;      // [M] global
-    double* tri;            // [col][5 nu_max]: tridiagonal D, E and the three vectors
-    double* fac;            // [col][2 nu_max^2]: Householder reflectors + tau, Cholesky factor
+    double* tri;            // [col][5 nu_max]: tridiagonal D, E and the three vectors y = Q_H^T z
+    double* fac;            // [col][2 nu_max^2]: Householder reflectors (row k) + tau, Cholesky factor
     double* rot_c;          // [col][rot_cap]: recorded Givens rotations
     double* rot_s;
     unsigned char* rot_k;
@@ -140,7 +140,12 @@ struct EigArgs {
 __host__ __device__ size_t eig_tri_doubles(int nm);
 __host__ __device__ size_t eig_fac_doubles(int nm);
 __host__ __device__ size_t eig_rot_cap(int nm);
-void projected_eig(const EigArgs& a, cudaStream_t st);
+// reduce, chase, spectra (eps, c, d, g); V too when form_v
+void projected_eig(const EigArgs& a, cudaStream_t st, bool form_v);
+// V of the columns whose factors (fac, rotations, perm) are those of the last projected_eig
+void eig_vectors(const EigArgs& a, cudaStream_t st);
+// T[batch col][2 nu_max]: the density weights at mu with the recorded rotations applied
+void eig_density_weights(const EigArgs& a, double mu, double kT, double* T, cudaStream_t st);
 
 // ---------------------------------------------------------------- a7, a9 (reduce.cu)
 struct BisectState {
@@ -171,7 +176,9 @@ int reduce_grid();
 void bisect_init(const ReduceArgs& a, cudaStream_t st);      // bracket + N(lo), N(hi)
 void bisect_step(const ReduceArgs& a, cudaStream_t st);      // one bisection step (no-op when done)
 void scalars_at(const ReduceArgs& a, double mu, cudaStream_t st);  // N, E_band, Omega at mu
-void dos_at(const ReduceArgs& a, const double* z_dev, int n_z, double* out_dev, cudaStream_t st);
+// DOS at n_z energies; scratch holds dos_scratch_doubles(n_z), the result in its last n_z
+size_t dos_scratch_doubles(int n_z);
+void dos_at(const ReduceArgs& a, const double* z_dev, int n_z, double* scratch, cudaStream_t st);
 
 // ---------------------------------------------------------------- a8, G(z) (density.cu)
 struct DensityArgs {
@@ -183,7 +190,9 @@ struct DensityArgs {
     const double* c;
     const int* nu_eff;
     const double* V;        // batch-local columns
-    int v_col0;             // global column of V's first column
+    int v_col0;             // global column of V's (or T's and fac's) first column
+    const double* T;        // k_eig_weights output [batch col][2 nu_max]; used instead of V when set
+    const double* fac;      // the eigen-factors of the same columns (with T)
     const double* UP;
     int up_block0;
     double mu, kT;

@@ -8,20 +8,25 @@
 //
 // GB300 form. On this part the FP64 pipe charges a whole warp instruction whatever the number
 // of active lanes, so every FP64 instruction must carry work on all lanes:
-//   k_eig_reduce  one warp per column, matrices in shared memory: Cholesky, the reduction
-//                 A = L^-1 H' L^-T and the Householder reduction of A to tridiagonal form T
-//                 (lanes over rows / columns); the three vectors z = L^-1 (U, SU, HU)_j.
-//   k_eig_chase   one thread per column: implicit-shift QR sweeps on T (Wilkinson shift, Givens
-//                 bulge chase) -- the sequential part; the rotations are recorded.
-//   k_eig_vectors one warp per column: Q_H from the Householder reflectors, the recorded
-//                 rotations applied to its columns (lanes over rows), the spectra c, d, g = Q^T z
-//                 of the three vectors, V = L^-T Q.
+//   k_eig_reduce   one warp per column, matrices in shared memory: Cholesky, the reduction
+//                  A = L^-1 H' L^-T and the Householder reduction of A to tridiagonal form T
+//                  (lanes over rows / columns); the three vectors z = L^-1 (U, SU, HU)_j are
+//                  reflected along, y = Q_H^T z.
+//   k_eig_chase    one thread per column: implicit-shift QR sweeps on T (Wilkinson shift, Givens
+//                  bulge chase) -- the sequential part; the rotations are recorded.
+//   k_eig_spectra  one thread per column: the rotations replayed on y give c, d, g = Q^T z.
+//   k_eig_vectors  one warp per column, only where V itself is needed (G(z), the adjoint): Q_H
+//                  from the reflectors, the rotations applied to its columns, V = L^-T Q.
+//   k_eig_weights  one thread per column: for the density, t = V w = L^-T Q_H (R_1 .. R_n w)
+//                  needs V only applied to two vectors; the rotations (sequential) are applied
+//                  here, the reflectors and L^-T in the density kernel (lanes over rows).
 #include "internal.h"
 
 namespace elses {
 
-__host__ __device__ size_t eig_tri_doubles(int nm) { return 5 * (size_t)nm; }        // D, E, z (3 vectors)
-__host__ __device__ size_t eig_fac_doubles(int nm) { return 2 * (size_t)nm * nm; }   // reflectors + tau, L
+__host__ __device__ size_t eig_tri_doubles(int nm) { return 5 * (size_t)nm; }        // D, E, y (3 vectors)
+// reflector k in row k (entries i > k, tau_k at k), then L row-major
+__host__ __device__ size_t eig_fac_doubles(int nm) { return 2 * (size_t)nm * nm; }
 __host__ __device__ size_t eig_rot_cap(int nm) { return 2 * (size_t)nm * nm + 64; }  // Givens rotations per column
 constexpr int kRotStage = 128;   // rotations staged in shared memory at a time (k_eig_vectors)
 constexpr int kChaseThreads = 64;  // columns per CTA of k_eig_chase
@@ -54,10 +59,10 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
     const int c = blockIdx.x * (blockDim.x >> 5) + wib;
     if (c >= a.ncols) return;
     const int nm = a.nu_max, ld = nm + 1;
-    double* A = sm + (size_t)wib * (2 * nm * ld + 2 * nm);
-    double* L = A + nm * ld;
+    double* A = sm + (size_t)wib * ((2 * nm + 3) * ld + 2 * nm + 3);
+    double* L = A + (nm + 3) * ld;  // A: the matrix, then the three vectors as rows nu .. nu + 2
     double* inv = L + nm * ld;     // 1 / L_ii
-    double* P = inv + nm;          // Householder work vector
+    double* P = inv + nm;          // Householder work vector (nm + 3)
     double* yv = a.tri + (size_t)c * eig_tri_doubles(nm);   // D, E, yc, yd, yg (global)
     const int j = a.col0 + c;
     const int nu = a.nu_eff[j];
@@ -113,8 +118,8 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
             A[k * ld + i] = v;
         }
     __syncwarp();
-    // the three vectors z = L^-1 (U, SU, HU)_j for k_eig_vectors (which forms c, d, g = Q^T z):
-    // a column sweep with lanes over rows (rows lane and lane + 32), row m final at step m
+    // the three vectors z = L^-1 (U, SU, HU)_j into rows nu .. nu + 2 of A: a column sweep with
+    // lanes over rows (rows lane and lane + 32), row m final at step m
     {
         const double* src[3] = {a.urow + (size_t)c * nm, a.surow + (size_t)c * nm, a.hurow + (size_t)c * nm};
         double z0[3], z1[3];
@@ -149,13 +154,14 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
         }
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            if (lane < nu) yv[(2 + q) * nm + lane] = z0[q];
-            if (lane + 32 < nu) yv[(2 + q) * nm + lane + 32] = z1[q];
+            if (lane < nu) A[(nu + q) * ld + lane] = z0[q];
+            if (lane + 32 < nu) A[(nu + q) * ld + lane + 32] = z1[q];
         }
     }
     __syncwarp();
-    // Householder reduction: reflector k stored in column k below the diagonal, tau_k kept. The
-    // trailing block is kept in its lower triangle only (read symmetrically).
+    // Householder reduction: reflector k stored in column k below the diagonal, tau_k kept; the
+    // vector rows are reflected along (y = Q_H^T z). The trailing block is kept in its lower
+    // triangle only (read symmetrically).
     double* E = yv + nm;
     for (int k = 0; k + 2 < nu; ++k) {
         double part = 0.0;
@@ -171,14 +177,15 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
         const double tau = 1.0 / (alpha * (alpha - x0));
         if (lane == 0) A[(k + 1) * ld + k] = x0 - alpha;
         __syncwarp();
-        // p = tau A v (rows i > k)
+        // p = tau A v (rows i > k); the same sweep gives t_q = tau v^T y_q for the vector rows,
+        // in lanes the matrix rows leave idle
         double kp = 0.0;
-        for (int i = k + 1 + lane; i < nu; i += 32) {
+        for (int i = k + 1 + lane; i < nu + 3; i += 32) {
             double s = 0.0;
             for (int m = k + 1; m < nu; ++m) s = fma(m <= i ? A[i * ld + m] : A[m * ld + i], A[m * ld + k], s);
             s *= tau;
             P[i] = s;
-            kp = fma(A[i * ld + k], s, kp);
+            if (i < nu) kp = fma(A[i * ld + k], s, kp);
         }
         const double K = 0.5 * tau * warp_sum(kp);
         __syncwarp();
@@ -187,6 +194,11 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
         lower_pairs(k + 1, nu, lane, [&](int i, int m) {
             A[i * ld + m] = fma(-A[i * ld + k], P[m], fma(-P[i], A[m * ld + k], A[i * ld + m]));
         });
+        for (int m = k + 1 + lane; m < nu; m += 32) {   // y_q -= t_q v
+            const double vm = A[m * ld + k];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) A[(nu + q) * ld + m] = fma(-P[nu + q], vm, A[(nu + q) * ld + m]);
+        }
         __syncwarp();
         if (lane == 0) { E[k] = alpha; P[k] = tau; }   // P[k] keeps tau_k (P[i > k] reused later)
         __syncwarp();
@@ -201,12 +213,18 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
         P[nu - 1] = 0.0;
     }
     __syncwarp();
-    // factors for k_eig_vectors: reflectors (column k below the diagonal, tau_k on the diagonal), L
+    // the three vectors y = Q_H^T z
+    for (int q = lane; q < 3 * nu; q += 32) {
+        const int v = q / nu, m = q % nu;
+        yv[(2 + v) * nm + m] = A[(nu + v) * ld + m];
+    }
+    __syncwarp();
+    // factors: reflector k as row k of the first matrix (its entries i > k, tau_k at k), L
     double* F = a.fac + (size_t)c * eig_fac_doubles(nm);
     for (int q = lane; q < nu * nu; q += 32) {
-        const int i = q / nu, k = q % nu;
-        F[i * nm + k] = (i == k) ? P[k] : A[i * ld + k];
-        F[nm * nm + i * nm + k] = L[i * ld + k];
+        const int k = q / nu, i = q % nu;
+        F[k * nm + i] = (i == k) ? P[k] : A[i * ld + k];
+        F[nm * nm + k * nm + i] = L[k * ld + i];
     }
 }
 
@@ -304,6 +322,64 @@ __global__ void __launch_bounds__(kChaseThreads) k_eig_chase(const EigArgs a) {
     for (int k = 0; k < nm; ++k) a.eps[(size_t)j * nm + k] = (k < nu && ok) ? D[perm[k]] : 0.0;
 }
 
+// ----------------------------------------------------------------------------- k_eig_spectra
+// The recorded rotations of a column, read in order (forward) or backwards, from its own lists
+// (a thread's consecutive reads share cache sectors).
+struct RotList {
+    const double* c;
+    const double* s;
+    const unsigned char* k;
+    int n;
+    __device__ RotList(const EigArgs& a, int col) {
+        const size_t o = (size_t)col * eig_rot_cap(a.nu_max);
+        c = a.rot_c + o;
+        s = a.rot_s + o;
+        k = a.rot_k + o;
+        n = a.rot_n[col];
+    }
+};
+
+// Q = Q_H R_1^T .. R_n^T, so Q^T z = R_n .. R_1 y: each recorded rotation, in order, turns
+// (y_k, y_k+1) into (c y_k + s y_k+1, c y_k+1 - s y_k) in all three vectors. The spectra are
+// written in ascending order of the poles (zero past nu).
+__global__ void __launch_bounds__(kChaseThreads) k_eig_spectra(const EigArgs a) {
+    extern __shared__ double csm[];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.ncols) return;
+    const int nm = a.nu_max;
+    const int j = a.col0 + c;
+    const int nu = a.nu_eff[j];
+    double* base = csm + threadIdx.x;
+    const ThreadArray Y0{base}, Y1{base + (size_t)nm * kChaseThreads}, Y2{base + 2 * (size_t)nm * kChaseThreads};
+    const double* y = a.tri + (size_t)c * eig_tri_doubles(nm) + 2 * nm;
+    for (int k = 0; k < nu; ++k) {
+        Y0[k] = y[k];
+        Y1[k] = y[nm + k];
+        Y2[k] = y[2 * nm + k];
+    }
+    const RotList R(a, c);
+    for (int r = 0; r < R.n; ++r) {
+        const double cr = __ldg(R.c + r), sr = __ldg(R.s + r);
+        const int k = __ldg(R.k + r);
+        double p = Y0[k], q = Y0[k + 1];
+        Y0[k] = fma(cr, p, sr * q);
+        Y0[k + 1] = fma(cr, q, -sr * p);
+        p = Y1[k], q = Y1[k + 1];
+        Y1[k] = fma(cr, p, sr * q);
+        Y1[k + 1] = fma(cr, q, -sr * p);
+        p = Y2[k], q = Y2[k + 1];
+        Y2[k] = fma(cr, p, sr * q);
+        Y2[k + 1] = fma(cr, q, -sr * p);
+    }
+    const int* perm = a.perm + (size_t)c * nm;
+    for (int k = 0; k < nm; ++k) {
+        const int p = k < nu ? perm[k] : -1;
+        a.c[(size_t)j * nm + k] = p >= 0 ? Y0[p] : 0.0;
+        a.d[(size_t)j * nm + k] = p >= 0 ? Y1[p] : 0.0;
+        a.g[(size_t)j * nm + k] = p >= 0 ? Y2[p] : 0.0;
+    }
+}
+
 // ----------------------------------------------------------------------------- k_eig_vectors
 __global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a) {
     extern __shared__ __align__(16) double sm[];
@@ -320,7 +396,7 @@ __global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a) {
     const double* F = a.fac + (size_t)c * eig_fac_doubles(nm);
     for (int q = lane; q < nu * nu; q += 32) {
         const int i = q / nu, k = q % nu;
-        R[i * ld + k] = F[i * nm + k];
+        R[k * ld + i] = F[i * nm + k];
         L[i * ld + k] = F[nm * nm + i * nm + k];
         Q[i * ld + k] = (i == k) ? 1.0 : 0.0;
     }
@@ -365,30 +441,6 @@ __global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a) {
         }
         __syncwarp();
     }
-    // spectra c, d, g = Q^T z of the three vectors z = L^-1 (U, SU, HU)_j, in ascending order of
-    // the poles (lanes over poles)
-    {
-        const double* z = a.tri + (size_t)c * eig_tri_doubles(nm) + 2 * nm;
-        double* zs = inv + nm;
-        for (int q = lane; q < 3 * nu; q += 32) zs[(q / nu) * nm + q % nu] = z[(q / nu) * nm + q % nu];
-        __syncwarp();
-        const int* pm = a.perm + (size_t)c * nm;
-        for (int k = lane; k < nm; k += 32) {
-            double sc_ = 0.0, sd = 0.0, sg = 0.0;
-            if (k < nu) {
-                const int p = pm[k];
-                for (int n = 0; n < nu; ++n) {
-                    const double q = Q[n * ld + p];
-                    sc_ = fma(q, zs[n], sc_);
-                    sd = fma(q, zs[nm + n], sd);
-                    sg = fma(q, zs[2 * nm + n], sg);
-                }
-            }
-            a.c[(size_t)j * nm + k] = sc_;
-            a.d[(size_t)j * nm + k] = sd;
-            a.g[(size_t)j * nm + k] = sg;
-        }
-    }
     // V = L^-T Q in place (lanes over columns m, rows bottom-up)
     for (int m = lane; m < nu; m += 32)
         for (int i = nu - 1; i >= 0; --i) {
@@ -405,18 +457,83 @@ __global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a) {
     }
 }
 
-size_t eig_smem_reduce(int nm) { return sizeof(double) * 2 * (2 * (size_t)nm * (nm + 1) + 2 * (size_t)nm); }
-size_t eig_smem_vectors(int nm) { return sizeof(double) * (3 * (size_t)nm * (nm + 1) + 4 * (size_t)nm); }
+// ----------------------------------------------------------------------------- k_eig_weights
+// The density weights of Eq. 2, w = 2 f(e_k - mu) c_k and w e_k (pole order), put back in the
+// order of the eigenvalue iteration and multiplied by R_1^T .. R_n^T: the recorded rotations in
+// reverse, each turning (w_k, w_k+1) into (c w_k - s w_k+1, s w_k + c w_k+1). Out:
+// T[batch col][2 nu_max] = (u, u_E), zero past nu; t = L^-T Q_H u is finished in the density.
+__global__ void __launch_bounds__(kChaseThreads) k_eig_weights(const EigArgs a, double mu, double kT, double* T) {
+    extern __shared__ double csm[];
+    const int c0 = blockIdx.x * blockDim.x, c = c0 + threadIdx.x;
+    const int nm = a.nu_max;
+    double* base = csm + threadIdx.x;
+    const ThreadArray W{base}, WE{base + (size_t)nm * kChaseThreads};
+    if (c < a.ncols) {
+        const int j = a.col0 + c;
+        const int nu = a.nu_eff[j];
+        for (int k = 0; k < nm; ++k) {
+            W[k] = 0.0;
+            WE[k] = 0.0;
+        }
+        const int* perm = a.perm + (size_t)c * nm;
+        for (int k = 0; k < nu; ++k) {
+            const double e = a.eps[(size_t)j * nm + k];
+            const double f2 = 2.0 * fermi((e - mu) / kT) * a.c[(size_t)j * nm + k];
+            const int p = perm[k];
+            W[p] = f2;
+            WE[p] = f2 * e;
+        }
+        const RotList R(a, c);
+        for (int r = R.n - 1; r >= 0; --r) {
+            const double cr = __ldg(R.c + r), sr = __ldg(R.s + r);
+            const int k = __ldg(R.k + r);
+            double p = W[k], q = W[k + 1];
+            W[k] = fma(cr, p, -sr * q);
+            W[k + 1] = fma(cr, q, sr * p);
+            p = WE[k], q = WE[k + 1];
+            WE[k] = fma(cr, p, -sr * q);
+            WE[k + 1] = fma(cr, q, sr * p);
+        }
+    }
+    __syncthreads();
+    // coalesced write-out: element r of column c0 + t sits at csm[r * kChaseThreads + t]
+    const int ncl = min(kChaseThreads, a.ncols - c0);
+    for (int q = threadIdx.x; q < ncl * 2 * nm; q += kChaseThreads) {
+        const int t = q / (2 * nm), r = q % (2 * nm);
+        T[(size_t)(c0 + t) * 2 * nm + r] = csm[(size_t)r * kChaseThreads + t];
+    }
+}
 
-void projected_eig(const EigArgs& a, cudaStream_t st) {
-    const size_t s1 = eig_smem_reduce(a.nu_max), s3 = eig_smem_vectors(a.nu_max);
+size_t eig_smem_reduce(int nm) {
+    return sizeof(double) * 2 * ((2 * (size_t)nm + 3) * (nm + 1) + 2 * (size_t)nm + 3);
+}
+size_t eig_smem_vectors(int nm) { return sizeof(double) * (3 * (size_t)nm * (nm + 1) + (size_t)nm); }
+size_t eig_smem_threads(int nm, int arrays) { return sizeof(double) * arrays * (size_t)nm * kChaseThreads; }
+int eig_thread_grid(int ncols) { return (ncols + kChaseThreads - 1) / kChaseThreads; }
+
+void projected_eig(const EigArgs& a, cudaStream_t st, bool form_v) {
+    const size_t s1 = eig_smem_reduce(a.nu_max);
     smem_at_least(k_eig_reduce, s1);
-    smem_at_least(k_eig_vectors, s3);
     k_eig_reduce<<<(a.ncols + 1) / 2, 64, s1, st>>>(a);
-    const size_t s2 = sizeof(double) * 2 * (size_t)a.nu_max * kChaseThreads;
+    const size_t s2 = eig_smem_threads(a.nu_max, 2);
     smem_at_least(k_eig_chase, s2);
-    k_eig_chase<<<(a.ncols + kChaseThreads - 1) / kChaseThreads, kChaseThreads, s2, st>>>(a);
-    k_eig_vectors<<<a.ncols, 32, s3, st>>>(a);
+    k_eig_chase<<<eig_thread_grid(a.ncols), kChaseThreads, s2, st>>>(a);
+    const size_t s3 = eig_smem_threads(a.nu_max, 3);
+    smem_at_least(k_eig_spectra, s3);
+    k_eig_spectra<<<eig_thread_grid(a.ncols), kChaseThreads, s3, st>>>(a);
+    if (form_v) eig_vectors(a, st);
+}
+
+void eig_vectors(const EigArgs& a, cudaStream_t st) {
+    const size_t s = eig_smem_vectors(a.nu_max);
+    smem_at_least(k_eig_vectors, s);
+    k_eig_vectors<<<a.ncols, 32, s, st>>>(a);
+}
+
+void eig_density_weights(const EigArgs& a, double mu, double kT, double* T, cudaStream_t st) {
+    const size_t s = eig_smem_threads(a.nu_max, 2);
+    smem_at_least(k_eig_weights, s);
+    k_eig_weights<<<eig_thread_grid(a.ncols), kChaseThreads, s, st>>>(a, mu, kT, T);
 }
 
 }  // namespace elses

@@ -223,8 +223,10 @@ void scalars_at(const ReduceArgs& a, double mu, cudaStream_t st) {
 }
 
 // Density of states -(1/pi) Im sum_j sum_k d_k c_k / (z - e_k) at the energies z[iz] (grid
-// (blocks, n_z)): per block a fixed-order tree, then one atomic addition per block into out[iz].
-__global__ void __launch_bounds__(kRedThreads) k_dos(const ReduceArgs a, const double* __restrict__ z, double* out) {
+// (blocks, n_z)): per block a fixed-order tree into partials[iz][block]; k_dos_sum then adds the
+// blocks in index order, so the result does not depend on the order in which blocks finish.
+__global__ void __launch_bounds__(kRedThreads) k_dos(const ReduceArgs a, const double* __restrict__ z,
+                                                     double* partials) {
     const int iz = blockIdx.y;
     const double zr = z[2 * iz], zi = z[2 * iz + 1];
     const size_t total = (size_t)a.M * a.nu_max;
@@ -242,12 +244,30 @@ __global__ void __launch_bounds__(kRedThreads) k_dos(const ReduceArgs a, const d
         if (threadIdx.x < o) sv[threadIdx.x] += sv[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) atomicAdd(out + iz, sv[0] * 0.31830988618379067154);
+    if (threadIdx.x == 0) partials[(size_t)iz * gridDim.x + blockIdx.x] = sv[0];
 }
 
-void dos_at(const ReduceArgs& a, const double* z_dev, int n_z, double* out_dev, cudaStream_t st) {
-    const dim3 grid(reduce_grid(), n_z);
-    k_dos<<<grid, kRedThreads, 0, st>>>(a, z_dev, out_dev);
+__global__ void __launch_bounds__(kRedThreads) k_dos_sum(const double* __restrict__ partials, int nblocks,
+                                                         double* out) {
+    const int iz = blockIdx.x;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partials[(size_t)iz * nblocks + b];
+    __shared__ double sv[kRedThreads];
+    sv[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sv[threadIdx.x] += sv[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[iz] = sv[0] * 0.31830988618379067154;
+}
+
+size_t dos_scratch_doubles(int n_z) { return (size_t)n_z * (reduce_grid() + 1); }
+
+void dos_at(const ReduceArgs& a, const double* z_dev, int n_z, double* scratch, cudaStream_t st) {
+    const int G = reduce_grid();
+    k_dos<<<dim3(G, n_z), kRedThreads, 0, st>>>(a, z_dev, scratch);
+    k_dos_sum<<<n_z, kRedThreads, 0, st>>>(scratch, G, scratch + (size_t)n_z * G);
 }
 
 }  // namespace elses

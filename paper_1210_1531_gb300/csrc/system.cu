@@ -112,7 +112,7 @@ struct elses_system_s {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<K3Launch> k3_launches;
     std::vector<int> h_clsize;
-    DevBuf<double> kscratch, Hp, Sp, urow, surow, hurow, etri, efac, erot_c, erot_s;
+    DevBuf<double> kscratch, Hp, Sp, urow, surow, hurow, etri, efac, erot_c, erot_s, ewt;
     DevBuf<unsigned char> erot_k;
     DevBuf<int> erot_n, eperm;
     DevBuf<double> eps, cc, dd, gg, V, UP, Vb, UPb;
@@ -122,6 +122,8 @@ struct elses_system_s {
     DevBuf<double> bstore;                 // per-column bases kept for the exact gradient
     size_t bstride = 0, bvec = 0;
     bool use_store = false;
+    // the eigen-factors of every column are in the batch buffers and the stored V is not formed
+    bool v_lazy = false;
     std::vector<int> adj_bps;              // resident adjoint CTAs per SM, by cluster slots
     DevBuf<double> partials, zbuf, pre, gbuf, dosbuf;
     DevBuf<BisectState> bstate;
@@ -289,6 +291,7 @@ int prepare_columns(elses_system s) {
     TRY(s->erot_s.ensure(bc * eig_rot_cap(nm)));
     TRY(s->erot_k.ensure(bc * eig_rot_cap(nm)));
     TRY(s->erot_n.ensure(bc));
+    TRY(s->ewt.ensure(bc * 2 * nm));
     TRY(s->eperm.ensure(bc * nm));
     const size_t M = s->M;
     TRY(s->eps.ensure(M * nm));
@@ -332,11 +335,10 @@ int prepare_columns(elses_system s) {
     s->atoms_done = 0;
     s->have_mu = false;
     s->have_rho = false;
+    s->v_lazy = false;
     return 0;
 }
 
-// Krylov build + projected eigenproblem for atoms [b, e). Writes V and UP either to the stored
-// arrays or to the batch buffers (two-pass), returning the pointers used.
 // The second stream: work launched on it after fork_side runs beside `st` until join_side.
 int fork_side(elses_system s, cudaStream_t st) {
     if (!s->side) {
@@ -393,9 +395,58 @@ KrylovArgs krylov_args(elses_system s, int b, int e) {
     return ka;
 }
 
+// Eigenproblem arguments for atoms [b, e), V written at V.
+EigArgs eig_args(elses_system s, int b, int e, double* V) {
+    EigArgs ea{};
+    ea.ncols = 4 * (e - b);
+    ea.col0 = 4 * b;
+    ea.nu_max = s->nu_max;
+    ea.Hp = s->Hp.p;
+    ea.Sp = s->Sp.p;
+    ea.urow = s->urow.p;
+    ea.surow = s->surow.p;
+    ea.hurow = s->hurow.p;
+    ea.nu_eff = s->nu_eff.p;
+    ea.tri = s->etri.p;
+    ea.fac = s->efac.p;
+    ea.rot_c = s->erot_c.p;
+    ea.rot_s = s->erot_s.p;
+    ea.rot_k = s->erot_k.p;
+    ea.rot_n = s->erot_n.p;
+    ea.perm = s->eperm.p;
+    ea.eps = s->eps.p;
+    ea.c = s->cc.p;
+    ea.d = s->dd.p;
+    ea.g = s->gg.p;
+    ea.V = V;
+    ea.status = s->counters.p + 2;
+    return ea;
+}
+
+// The stored V of every column, from the kept factors, where the energy pass left it unformed
+// (G(z), the spectra on the pattern and the adjoint need V itself).
+int ensure_V(elses_system s, cudaStream_t st) {
+    if (!s->v_lazy) return 0;
+    s->tic(T_EIG, st);
+    eig_vectors(eig_args(s, 0, s->n, s->V.p), st);
+    s->toc(st);
+    s->stats.launches++;
+    s->v_lazy = false;
+    return 0;
+}
+
+// Krylov build + projected eigenproblem for atoms [b, e). Writes V and UP either to the stored
+// arrays or to the batch buffers (two-pass), returning the pointers used. form_v false leaves V
+// unformed; in the stored workflow that is kept only for a batch of every atom (its factors then
+// stay in the batch buffers until ensure_V or the next batch).
 int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_col0,
-              double** UP_out, int* up_block0, cudaStream_t st, bool need_rows = true) {
+              double** UP_out, int* up_block0, cudaStream_t st, bool need_rows = true, bool form_v = true) {
     const int nm = s->nu_max;
+    if (stored && !form_v && (b != 0 || e != s->n)) form_v = true;
+    // the batch buffers are about to be overwritten: V of the other columns first, unless every
+    // column is recomputed now
+    if (stored && (b != 0 || e != s->n)) TRY(ensure_V(s, st));
+    if (stored) s->v_lazy = false;
     KrylovArgs ka = krylov_args(s, b, e);
     if (stored) {
         ka.UP = s->UP.p;
@@ -409,13 +460,16 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
     std::vector<const elses_system_s::K3Launch*> ls;
     for (const auto& L : s->k3_launches)
         if (L.batch_begin == b) ls.push_back(&L);
-    // batched form: the largest class (few atoms, long CTAs) runs beside the others on a second
-    // stream, so that its partial wave does not leave SMs idle
+    // batched form: the class with the most atoms runs on the caller's stream and the others
+    // (few atoms each, partial waves) beside it, one after another, on a second stream
     const bool conc = s->p.schedule == 1 && ls.size() >= 2;
+    size_t main_cls = 0;
+    for (size_t i = 1; i < ls.size(); ++i)
+        if (ls[i]->item_count > ls[main_cls]->item_count) main_cls = i;
     if (conc) TRY(fork_side(s, st));
     for (size_t i = 0; i < ls.size(); ++i) {
         const auto& L = *ls[i];
-        cudaStream_t lst = (conc && i == 0) ? s->side : st;
+        cudaStream_t lst = (conc && i != main_cls) ? s->side : st;
         ka.na_max = L.na;
         ka.order = s->order.p + L.item_begin;
         ka.n_items = L.item_count;
@@ -435,33 +489,12 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
     if (conc) TRY(join_side(s, st));
     s->toc(st);
 
-    EigArgs ea{};
-    ea.ncols = 4 * (e - b);
-    ea.col0 = 4 * b;
-    ea.nu_max = nm;
-    ea.Hp = s->Hp.p;
-    ea.Sp = s->Sp.p;
-    ea.urow = s->urow.p;
-    ea.surow = s->surow.p;
-    ea.hurow = s->hurow.p;
-    ea.nu_eff = s->nu_eff.p;
-    ea.tri = s->etri.p;
-    ea.fac = s->efac.p;
-    ea.rot_c = s->erot_c.p;
-    ea.rot_s = s->erot_s.p;
-    ea.rot_k = s->erot_k.p;
-    ea.rot_n = s->erot_n.p;
-    ea.perm = s->eperm.p;
-    ea.eps = s->eps.p;
-    ea.c = s->cc.p;
-    ea.d = s->dd.p;
-    ea.g = s->gg.p;
-    ea.V = stored ? s->V.p + (size_t)4 * b * nm * nm : s->Vb.p;
-    ea.status = s->counters.p + 2;
+    EigArgs ea = eig_args(s, b, e, stored ? s->V.p + (size_t)4 * b * nm * nm : s->Vb.p);
     s->tic(T_EIG, st);
-    projected_eig(ea, st);
+    projected_eig(ea, st, form_v);
     s->toc(st);
-    s->stats.launches += 3;
+    s->stats.launches += form_v ? 4 : 3;
+    if (stored && !form_v) s->v_lazy = true;
     s->stats.columns += 4LL * (e - b);
     *V_out = ea.V;
     *v_col0 = 4 * b;
@@ -496,6 +529,7 @@ int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* 
         need = std::max(need, used);
     }
     TRY(s->ascratch.ensure(need));
+    if (!s->p.two_pass) TRY(ensure_V(s, st));
     for (int b = 0; b < s->n; b += s->batch_atoms) {
         const int e = std::min(s->n, b + s->batch_atoms);
         if (e <= lo || b >= hi) continue;
@@ -530,12 +564,15 @@ int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* 
         std::vector<size_t> li;
         for (size_t i = 0; i < s->k3_launches.size(); ++i)
             if (s->k3_launches[i].batch_begin == b) li.push_back(i);
-        const bool conc = li.size() >= 2;   // the largest class beside the others, as for the Krylov pass
+        const bool conc = li.size() >= 2;   // the main class beside the others, as for the Krylov pass
+        size_t main_cls = 0;
+        for (size_t t = 1; t < li.size(); ++t)
+            if (s->k3_launches[li[t]].item_count > s->k3_launches[li[main_cls]].item_count) main_cls = t;
         if (conc) TRY(fork_side(s, st));
         for (size_t t = 0; t < li.size(); ++t) {
             const size_t i = li[t];
             const auto& L = s->k3_launches[i];
-            cudaStream_t lst = (conc && t == 0) ? s->side : st;
+            cudaStream_t lst = (conc && t != main_cls) ? s->side : st;
             ka.na_max = L.na;
             ka.order = s->order.p + L.item_begin;
             ka.n_items = L.item_count;
@@ -803,6 +840,7 @@ int elses_set_hs(elses_system s, const double* H_dev, const double* S_dev, void*
     CUDA_TRY(cudaMemcpyAsync(s->S.p, S_dev, sizeof(double) * 16 * s->nnzb, cudaMemcpyDeviceToDevice, st));
     s->user_hs = true;
     s->have_rho = false;
+    s->v_lazy = false;   // every column is recomputed before V is used again
     s->atom_done.assign(s->n, 0);
     s->atoms_done = 0;
     s->have_mu = false;
@@ -828,8 +866,9 @@ int elses_green_columns(elses_system s, int col_begin, int col_end, int n_z, con
         double* V;
         double* UP;
         int v0, u0;
-        // first calculation of G in the two-pass workflow keeps only the spectra
-        TRY(run_batch(s, b, e, stored, &V, &v0, &UP, &u0, st, stored || n_z > 0));
+        // first calculation of G in the two-pass workflow keeps only the spectra; V is formed
+        // only for G(z) (or, stored, later where something needs it)
+        TRY(run_batch(s, b, e, stored, &V, &v0, &UP, &u0, st, stored || n_z > 0, n_z > 0));
         if (n_z > 0) {
             DensityArgs d = density_args(s, 0.0, nullptr, nullptr);
             d.atom_begin = b;
@@ -890,21 +929,34 @@ int elses_find_mu(elses_system s, double* mu_host, double* n_at_mu_host, void* s
     return ELSES_OK;
 }
 
+// rho columns of atoms [b, e) at mu: from V where it is formed, else from the eigen-factors of the
+// batch just computed (the weights with the rotations applied, then reflectors and L^-T).
+static void density_batch(elses_system s, double mu, double* rho, double* rhoE, int b, int e, const double* V,
+                          int v0, const double* UP, int u0, bool factors, cudaStream_t st) {
+    DensityArgs d = density_args(s, mu, rho, rhoE);
+    d.atom_begin = b;
+    d.atom_end = e;
+    d.V = V;
+    d.v_col0 = v0;
+    d.UP = UP;
+    d.up_block0 = u0;
+    s->tic(T_DENSITY, st);
+    if (factors) {
+        eig_density_weights(eig_args(s, b, e, nullptr), mu, s->p.kT, s->ewt.p, st);
+        s->stats.launches++;
+        d.T = s->ewt.p;
+        d.fac = s->efac.p;
+    }
+    density_columns(d, st);
+    s->toc(st);
+    s->stats.launches++;
+}
+
 static int density_impl(elses_system s, double mu, double* rho, double* rhoE, cudaStream_t st) {
     if (s->atoms_done != s->n) return fail(ELSES_ERR_STATE, "density_matrix needs every column");
     TRY(clear_status(s, st));
     if (!s->p.two_pass) {
-        DensityArgs d = density_args(s, mu, rho, rhoE);
-        d.atom_begin = 0;
-        d.atom_end = s->n;
-        d.V = s->V.p;
-        d.v_col0 = 0;
-        d.UP = s->UP.p;
-        d.up_block0 = 0;
-        s->tic(T_DENSITY, st);
-        density_columns(d, st);
-        s->toc(st);
-        s->stats.launches++;
+        density_batch(s, mu, rho, rhoE, 0, s->n, s->V.p, 0, s->UP.p, 0, s->v_lazy, st);
     } else {
         // second calculation of G (Eq. 3): recompute every batch, then its rho columns
         for (int b = 0; b < s->n; b += s->batch_atoms) {
@@ -912,18 +964,8 @@ static int density_impl(elses_system s, double mu, double* rho, double* rhoE, cu
             double* V;
             double* UP;
             int v0, u0;
-            TRY(run_batch(s, b, e, false, &V, &v0, &UP, &u0, st));
-            DensityArgs d = density_args(s, mu, rho, rhoE);
-            d.atom_begin = b;
-            d.atom_end = e;
-            d.V = V;
-            d.v_col0 = v0;
-            d.UP = UP;
-            d.up_block0 = u0;
-            s->tic(T_DENSITY, st);
-            density_columns(d, st);
-            s->toc(st);
-            s->stats.launches++;
+            TRY(run_batch(s, b, e, false, &V, &v0, &UP, &u0, st, true, false));
+            density_batch(s, mu, rho, rhoE, b, e, V, v0, UP, u0, true, st);
         }
     }
     return 0;
@@ -1013,16 +1055,16 @@ int elses_cohp_spectrum(elses_system s, int n_z, const double* z_host, double* C
     TRY(s->zbuf.ensure(2 * (size_t)n_z));
     CUDA_TRY(cudaMemcpyAsync(s->zbuf.p, z_host, sizeof(double) * 2 * n_z, cudaMemcpyHostToDevice, st));
     if (dos_host) {
-        TRY(s->dosbuf.ensure(n_z));
-        CUDA_TRY(cudaMemsetAsync(s->dosbuf.p, 0, sizeof(double) * n_z, st));
+        TRY(s->dosbuf.ensure(dos_scratch_doubles(n_z)));
         dos_at(reduce_args(s), s->zbuf.p, n_z, s->dosbuf.p, st);
-        s->stats.launches++;
+        s->stats.launches += 2;
     }
     if (C_dev || Csig_dev || Cpi_dev) {
         // G on the pattern for a chunk of energies at a time (at most 256 MB), then Eq. 4
         const size_t per_z = (size_t)s->nnzb * 16 * 2;
         const int chunk = (int)std::max<size_t>(1, std::min<size_t>(n_z, (size_t(1) << 25) / per_z));
         TRY(s->gbuf.ensure(per_z * chunk));
+        if (!s->p.two_pass) TRY(ensure_V(s, st));
         for (int iz0 = 0; iz0 < n_z; iz0 += chunk) {
             const int nzc = std::min(chunk, n_z - iz0);
             for (int b = 0; b < s->n; b += s->batch_atoms) {
@@ -1058,7 +1100,8 @@ int elses_cohp_spectrum(elses_system s, int n_z, const double* z_host, double* C
     int rc = check_status(s, st);
     if (rc < 0) return rc;
     if (dos_host) {
-        CUDA_TRY(cudaMemcpyAsync(dos_host, s->dosbuf.p, sizeof(double) * n_z, cudaMemcpyDeviceToHost, st));
+        const double* dos = s->dosbuf.p + dos_scratch_doubles(n_z) - n_z;
+        CUDA_TRY(cudaMemcpyAsync(dos_host, dos, sizeof(double) * n_z, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
     }
     return rc;

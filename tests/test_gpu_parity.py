@@ -127,6 +127,19 @@ def test_two_pass_equals_stored(eg, d64):
     assert np.array_equal(gu.to_np(rho), d64["rho"]) and np.array_equal(gu.to_np(F), d64["F"])
 
 
+def test_factor_density_equals_formed_V(eg, d64):
+    """One batch of every atom leaves V unformed and takes t = V w from the eigen-factors
+    (rotations, reflectors, L^-T); several batches form V. Same rho to rounding."""
+    s2 = eg.system_for(d64["w"], batch_atoms=16)
+    mu, e_band, _, F = s2.energy_force()
+    rho, rhoE = s2.density_matrix(mu)
+    assert mu == d64["mu"] and e_band == d64["e_band"]     # the spectra do not depend on V
+    scale = np.abs(d64["rho"]).max()
+    assert np.abs(gu.to_np(rho) - d64["rho"]).max() <= 1e-13 * scale
+    assert np.abs(gu.to_np(rhoE) - d64["rhoE"]).max() <= 1e-13 * np.abs(d64["rhoE"]).max()
+    assert np.abs(gu.to_np(F) - d64["F"]).max() <= 1e-12 * np.abs(d64["F"]).max()
+
+
 def test_batched_schedule_equals_plain(eg, d64):
     s2 = eg.system_for(d64["w"], schedule=1)
     mu, e_band, _, F = s2.energy_force()
