@@ -92,6 +92,14 @@ typedef struct elses_params {
                                Arnoldi method); elses_omega_gradient is not available with it */
     int    batch_atoms;     /* atoms per Krylov -> eigensolver batch (0: automatic, sized by a
                                memory budget); smaller batches need less device memory          */
+    int    autotune;        /* 1: elses_build_clusters runs elses_autotune on its first build
+                               (ignored when k3_ctas_per_sm is set)                              */
+    int    graph;           /* 1: elses_energy_force replays its step as a CUDA graph: the first
+                               call with a new launch plan runs as usual, the next captures the
+                               device work (columns, the bisection's fixed launch sequence,
+                               density, scalars, forces at the device-resident mu), later calls
+                               replay it with one host synchronisation; a rebuild that keeps the
+                               plan and buffers keeps the graph. Results equal the eager path.   */
 } elses_params;
 
 /* Counters and event timings of the calls since the last build (timing = 1 for the times). */
@@ -131,6 +139,19 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
 /* Replace H and S by user values on the system's own pattern (double[nnzb][4][4] device).
  * Forces need the Slater-Koster derivatives and are unavailable afterwards (ERR_STATE). */
 int elses_set_hs(elses_system sys, const double* H_dev, const double* S_dev, void* stream);
+
+/* Autotuner of the Krylov kernel's launch shape (a3, a4). For each cluster size class of the
+ * system (clusters of up to 32 s atoms in s slots; one CTA per atom, persistent), run = 1 times
+ * the kernel at every count of resident CTAs per SM that fits -- fewer CTAs keep more of their
+ * Krylov bases in L2, more hide more latency -- on a sample of the class's own atoms (up to two
+ * full waves, in launch order), and keeps the fastest per atom for the later calls of this
+ * system and its rebuilds. The timed launches use the column buffers, so columns computed before
+ * are invalidated; the results of later calls do not depend on the shape (bit for bit). run = 0
+ * only reports the shapes in use. classes_out: optional host int[2 * max_classes], pairs (slots
+ * s, CTAs per SM), largest class first; n_host: the number of classes. ERR_STATE for run = 1
+ * when params.k3_ctas_per_sm fixes the shape. Passage: none (a launch-shape choice). */
+int elses_autotune(elses_system sys, int run, int max_classes, int* classes_out, int* n_host,
+                   void* stream);
 
 /* a3-a6: per-column Krylov build, projection, projected generalized eigenproblem and spectra
  * for columns [col_begin, col_end) (whole atoms: both multiples of 4). Keeps the spectra (and,

@@ -49,7 +49,7 @@ class Params(ctypes.Structure):
                 ("max_neighbors", ctypes.c_int), ("max_cluster", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("timing", ctypes.c_int), ("k3_ctas_per_sm", ctypes.c_int),
                 ("force_mode", ctypes.c_int), ("krylov_block", ctypes.c_int),
-                ("batch_atoms", ctypes.c_int)]
+                ("batch_atoms", ctypes.c_int), ("autotune", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -64,7 +64,7 @@ class Stats(ctypes.Structure):
 EXPORTS = (
     "elses_build_clusters", "elses_set_hs", "elses_green_columns", "elses_find_mu",
     "elses_density_matrix", "elses_energies", "elses_energy_force", "elses_forces",
-    "elses_omega_gradient", "elses_icohp", "elses_cohp_spectrum",
+    "elses_omega_gradient", "elses_icohp", "elses_cohp_spectrum", "elses_autotune",
     "elses_get_pattern",
     "elses_get_hs", "elses_get_clusters", "elses_get_spectra", "elses_get_stats",
     "elses_reset_stats", "elses_probe_fp64", "elses_find_mu_static", "elses_system_destroy",
@@ -96,6 +96,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "elses_forces": [P, P, V],
         "elses_omega_gradient": [P, D, I, I, P, P, V],
         "elses_cohp_spectrum": [P, I, pD, P, P, P, pD, V],
+        "elses_autotune": [P, I, I, pI, pI, V],
         "elses_get_pattern": [P, pI, P, P, V],
         "elses_get_hs": [P, P, P, V],
         "elses_get_clusters": [P, pLL, pI, P, P, V],
@@ -148,7 +149,7 @@ def make_sk(p) -> SK:
 def make_params(r_cluster, nu, kT, n_electrons, two_pass=False, nu_classes=(), schedule=0,
                 max_neighbors=0, max_cluster=0, breakdown_tol=0.0, mu_tol=0.0,
                 max_bisect=0, timing=False, k3_ctas_per_sm=0, exact_forces=False,
-                krylov_block=False, batch_atoms=0) -> Params:
+                krylov_block=False, batch_atoms=0, autotune=False, graph=False) -> Params:
     p = Params()
     p.r_cluster, p.kT, p.n_electrons = float(r_cluster), float(kT), float(n_electrons)
     p.breakdown_tol, p.mu_tol = float(breakdown_tol), float(mu_tol)
@@ -163,6 +164,8 @@ def make_params(r_cluster, nu, kT, n_electrons, two_pass=False, nu_classes=(), s
     p.force_mode = 1 if exact_forces else 0
     p.krylov_block = 1 if krylov_block else 0
     p.batch_atoms = int(batch_atoms)
+    p.autotune = 1 if autotune else 0
+    p.graph = 1 if graph else 0
     return p
 
 
@@ -172,7 +175,7 @@ class System:
     def __init__(self, pos, box, sk, r_cluster, nu, kT, n_electrons, two_pass=False,
                  nu_classes=(), schedule=0, max_neighbors=0, max_cluster=0, timing=False,
                  k3_ctas_per_sm=0, exact_forces=False, krylov_block=False, batch_atoms=0,
-                 stream=None):
+                 autotune=False, graph=False, stream=None):
         self._L = load_library()
         self._h = ctypes.c_void_p(None)
         self.n = int(pos.shape[0])
@@ -181,7 +184,8 @@ class System:
         self.params = make_params(r_cluster, nu, kT, n_electrons, two_pass, nu_classes, schedule,
                                   max_neighbors, max_cluster, timing=timing,
                                   k3_ctas_per_sm=k3_ctas_per_sm, exact_forces=exact_forces,
-                                  krylov_block=krylov_block, batch_atoms=batch_atoms)
+                                  krylov_block=krylov_block, batch_atoms=batch_atoms,
+                                  autotune=autotune, graph=graph)
         self.box = (ctypes.c_double * 3)(*[float(b) for b in box])
         self.rebuild(pos, stream)
 
@@ -196,6 +200,21 @@ class System:
         nnzb = ctypes.c_int(0)
         _check(self._L.elses_get_pattern(self._h, ctypes.byref(nnzb), None, None, _stream(stream)))
         self.nnzb = nnzb.value
+
+    def autotune(self, stream=None):
+        """elses_autotune: the Krylov launch shape timed per cluster size class. Returns
+        {cluster slots of 32 atoms: resident CTAs per SM chosen}."""
+        return self._shapes(1, stream)
+
+    def autotune_shapes(self, stream=None):
+        """The Krylov launch shapes in use: {cluster slots of 32 atoms: CTAs per SM}."""
+        return self._shapes(0, stream)
+
+    def _shapes(self, run, stream):
+        out = (ctypes.c_int * 32)()
+        n = ctypes.c_int(0)
+        _check(self._L.elses_autotune(self._h, run, 16, out, ctypes.byref(n), _stream(stream)))
+        return {out[2 * i]: out[2 * i + 1] for i in range(min(n.value, 16))}
 
     # ------------------------------------------------------------------ a3-a10
     def green_columns(self, col_begin=0, col_end=None, z=None, stream=None):

@@ -97,11 +97,12 @@ __device__ __forceinline__ void rayleigh_ritz_gradient(const AdjointArgs& g, con
                                                        const double* cc, const double* dc, const double* Hpc,
                                                        const WarpScratch& w, int nv, int nm, size_t vs, int jp,
                                                        double sq, int lane) {
-    for (int k = lane; k < nv; k += 32) w.om[k] = omega_w(ec[k], g.mu, g.kT);
+    const double mu = g.mu_dev ? *g.mu_dev : g.mu;
+    for (int k = lane; k < nv; k += 32) w.om[k] = omega_w(ec[k], mu, g.kT);
     __syncwarp();
     for (int q = lane; q < nv * nv; q += 32) {
         const int k = q / nv, l = q % nv;
-        const double G = omega_divdiff(ec[k], ec[l], w.om[k], w.om[l], fermi((ec[l] - g.mu) / g.kT), g.kT);
+        const double G = omega_divdiff(ec[k], ec[l], w.om[k], w.om[l], fermi((ec[l] - mu) / g.kT), g.kT);
         w.X[k * nm + l] = G * 0.5 * (dc[k] * cc[l] + cc[k] * dc[l]);
     }
     __syncwarp();

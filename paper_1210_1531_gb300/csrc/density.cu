@@ -6,76 +6,13 @@
 //     rhoE_ij = 2 sum_k f(e_k - mu) e_k Z_ik c_k
 // for the pattern rows i of column j (atoms within r_cut of J), with Z = U V. Computed as
 // t = V (2 f c) (nu x nu) followed by rho_P = U_P t, which needs no Z. Where V is not formed, t
-// comes from the eigen-factors: V w = L^-T Q_H (R_1^T .. R_n^T w), the rotations applied by
-// k_eig_weights, the reflectors and L^-T here.
+// comes from the eigen-factors (k_eig_weights).
 //
 // One CTA per atom J, one warp per column; column j = 4J + b writes rho[(I, J)][a][b] through
 // the transpose map of the pattern (each element is written exactly once).
 #include "internal.h"
 
 namespace elses {
-
-// Two warp-wide sums at once (recursive halving, then a butterfly within each half): 5 additions
-// instead of 10. Both sums are returned in every lane.
-__device__ __forceinline__ void warp_sum_pair(double& x, double& y) {
-    const int lane = threadIdx.x & 31;
-    const bool upper = lane & 16;
-    double v = (upper ? y : x) + __shfl_xor_sync(0xffffffffu, upper ? x : y, 16);
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    x = __shfl_sync(0xffffffffu, v, 0);
-    y = __shfl_sync(0xffffffffu, v, 16);
-}
-
-// t = L^-T Q_H u for the pair (u, u_E) of column j from the kept eigen-factors: the reflectors
-// H_{nu-3} .. H_0 (H_k x = x - tau_k v_k v_k^T x, v_k in row k of the first factor matrix), then
-// the back substitution with L^T. Lanes over rows (row lane, and lane + 32 when nu > 32).
-template <bool kTwo>
-__device__ __forceinline__ void apply_factors(const DensityArgs& a, int j, int nu, double* t, double* tE) {
-    const int lane = threadIdx.x & 31, nm = a.nu_max;
-    const double* F = a.fac + (size_t)(j - a.v_col0) * 2 * nm * nm;
-    const double* Lf = F + (size_t)nm * nm;
-    const double* u = a.T + (size_t)(j - a.v_col0) * 2 * nm;
-    const int r1 = lane + 32;
-    double x0 = 0.0, e0 = 0.0, x1 = 0.0, e1 = 0.0;   // zero past nu
-    if (lane < nm) { x0 = u[lane]; e0 = u[nm + lane]; }
-    if (kTwo && r1 < nm) { x1 = u[r1]; e1 = u[nm + r1]; }
-    for (int k = nu - 3; k >= 0; --k) {
-        const double* v = F + (size_t)k * nm;
-        const double tau = v[k];
-        if (tau == 0.0) continue;
-        const double v0 = (lane > k && lane < nu) ? v[lane] : 0.0;
-        const double v1 = (kTwo && r1 > k && r1 < nu) ? v[r1] : 0.0;
-        double s = v0 * x0, sE = v0 * e0;
-        if (kTwo) { s = fma(v1, x1, s); sE = fma(v1, e1, sE); }
-        warp_sum_pair(s, sE);
-        s *= tau;
-        sE *= tau;
-        x0 = fma(-s, v0, x0);
-        e0 = fma(-sE, v0, e0);
-        if (kTwo) { x1 = fma(-s, v1, x1); e1 = fma(-sE, v1, e1); }
-    }
-    // L^T t = x, bottom-up: t_i = x_i / L_ii, then x_l -= L_il t_i for l < i
-    const double i0 = lane < nu ? 1.0 / Lf[(size_t)lane * nm + lane] : 0.0;
-    const double i1 = (kTwo && r1 < nu) ? 1.0 / Lf[(size_t)r1 * nm + r1] : 0.0;
-    for (int i = nu - 1; i >= 0; --i) {
-        const bool hi = kTwo && i >= 32;
-        const int owner = i & 31;
-        const double ti = __shfl_sync(0xffffffffu, hi ? x1 * i1 : x0 * i0, owner);
-        const double tEi = __shfl_sync(0xffffffffu, hi ? e1 * i1 : e0 * i0, owner);
-        const double* row = Lf + (size_t)i * nm;
-        const double l0 = lane < i ? row[lane] : 0.0;
-        x0 = lane == i ? ti : fma(-l0, ti, x0);
-        e0 = lane == i ? tEi : fma(-l0, tEi, e0);
-        if (kTwo) {
-            const double l1 = r1 < i ? row[r1] : 0.0;
-            x1 = r1 == i ? ti : fma(-l1, ti, x1);
-            e1 = r1 == i ? tEi : fma(-l1, tEi, e1);
-        }
-    }
-    if (lane < nu) { t[lane] = x0; tE[lane] = e0; }
-    if (kTwo && r1 < nu) { t[r1] = x1; tE[r1] = e1; }
-}
 
 __global__ void __launch_bounds__(128) k_density(const DensityArgs a) {
     __shared__ double wc[4][kMaxNu], wec[4][kMaxNu], t[4][kMaxNu], tE[4][kMaxNu];
@@ -85,13 +22,17 @@ __global__ void __launch_bounds__(128) k_density(const DensityArgs a) {
     const int j = 4 * J + warp;
     const int nm = a.nu_max;
     const int nu = a.nu_eff[j];
-    if (a.T) {
-        if (nu > 32) apply_factors<true>(a, j, nu, t[warp], tE[warp]);
-        else apply_factors<false>(a, j, nu, t[warp], tE[warp]);
+    if (a.T) {   // t and t_E from the eigen-factors (k_eig_weights)
+        const double* u = a.T + (size_t)(j - a.v_col0) * 2 * nm;
+        for (int n = lane; n < nu; n += 32) {
+            t[warp][n] = u[n];
+            tE[warp][n] = u[nm + n];
+        }
     } else {
+        const double mu = a.mu_dev ? *a.mu_dev : a.mu;
         for (int k = lane; k < nu; k += 32) {
             const double e = a.eps[(size_t)j * nm + k];
-            const double f2 = 2.0 * fermi((e - a.mu) / a.kT) * a.c[(size_t)j * nm + k];
+            const double f2 = 2.0 * fermi((e - mu) / a.kT) * a.c[(size_t)j * nm + k];
             wc[warp][k] = f2;
             wec[warp][k] = f2 * e;
         }

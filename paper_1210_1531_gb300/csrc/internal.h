@@ -94,6 +94,7 @@ struct AdjointArgs {
     const double* c;
     const double* d;
     double mu, kT;
+    const double* mu_dev;   // when set, mu is read here (device) instead
     double* gH;             // [nnzb][16] accumulated dOmega/dH
     double* gS;             // [nnzb][16] accumulated s_scale * dOmega/dS
     double s_scale;
@@ -144,8 +145,8 @@ __host__ __device__ size_t eig_rot_cap(int nm);
 void projected_eig(const EigArgs& a, cudaStream_t st, bool form_v);
 // V of the columns whose factors (fac, rotations, perm) are those of the last projected_eig
 void eig_vectors(const EigArgs& a, cudaStream_t st);
-// T[batch col][2 nu_max]: the density weights at mu with the recorded rotations applied
-void eig_density_weights(const EigArgs& a, double mu, double kT, double* T, cudaStream_t st);
+// T[batch col][2 nu_max]: t = V w and t_E = V w_E for the density weights at mu, from the factors
+void eig_density_weights(const EigArgs& a, double mu, const double* mu_dev, double kT, double* T, cudaStream_t st);
 
 // ---------------------------------------------------------------- a7, a9 (reduce.cu)
 struct BisectState {
@@ -170,12 +171,18 @@ struct ReduceArgs {
     BisectState* state;
     double* partials;       // [grid][4]
     unsigned* ticket;
-    double* pre;            // optional [M][nu_max]: exp((e - mu0)/kT) kept by the bisection
+    // optional, kept by the bisection once its bracket is narrow: per block of k_count, the poles
+    // within 60 kT of mu0 as (exp((e - mu0)/kT), d c) in its own range of act ([M][nu_max] in
+    // all), their number, and the sum of 2 d c of the poles below that window
+    double2* act;
+    int* act_n;             // [grid]
+    double* act_below;      // [grid]
 };
 int reduce_grid();
 void bisect_init(const ReduceArgs& a, cudaStream_t st);      // bracket + N(lo), N(hi)
 void bisect_step(const ReduceArgs& a, cudaStream_t st);      // one bisection step (no-op when done)
 void scalars_at(const ReduceArgs& a, double mu, cudaStream_t st);  // N, E_band, Omega at mu
+void scalars_at_state(const ReduceArgs& a, cudaStream_t st);      // the same at the state's mu
 // DOS at n_z energies; scratch holds dos_scratch_doubles(n_z), the result in its last n_z
 size_t dos_scratch_doubles(int n_z);
 void dos_at(const ReduceArgs& a, const double* z_dev, int n_z, double* scratch, cudaStream_t st);
@@ -191,11 +198,11 @@ struct DensityArgs {
     const int* nu_eff;
     const double* V;        // batch-local columns
     int v_col0;             // global column of V's (or T's and fac's) first column
-    const double* T;        // k_eig_weights output [batch col][2 nu_max]; used instead of V when set
-    const double* fac;      // the eigen-factors of the same columns (with T)
+    const double* T;        // t = V w, t_E [batch col][2 nu_max] (k_eig_weights); used instead of V when set
     const double* UP;
     int up_block0;
     double mu, kT;
+    const double* mu_dev;   // when set, mu is read here (device) instead
     double* rho;
     double* rhoE;
     int n_z;

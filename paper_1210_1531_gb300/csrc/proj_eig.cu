@@ -14,12 +14,12 @@
 //                  reflected along, y = Q_H^T z.
 //   k_eig_chase    one thread per column: implicit-shift QR sweeps on T (Wilkinson shift, Givens
 //                  bulge chase) -- the sequential part; the rotations are recorded.
-//   k_eig_spectra  one thread per column: the rotations replayed on y give c, d, g = Q^T z.
+//   k_eig_spectra  one thread per (column, vector): the rotations replayed on y give
+//                  c, d, g = Q^T z.
 //   k_eig_vectors  one warp per column, only where V itself is needed (G(z), the adjoint): Q_H
 //                  from the reflectors, the rotations applied to its columns, V = L^-T Q.
-//   k_eig_weights  one thread per column: for the density, t = V w = L^-T Q_H (R_1 .. R_n w)
-//                  needs V only applied to two vectors; the rotations (sequential) are applied
-//                  here, the reflectors and L^-T in the density kernel (lanes over rows).
+//   k_eig_weights  one thread per (column, vector): the density needs V only applied to two
+//                  vectors, t = V w = L^-T Q_H (R_1^T .. R_n^T w), taken from the factors.
 #include "internal.h"
 
 namespace elses {
@@ -231,10 +231,12 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
 // ----------------------------------------------------------------------------- k_eig_chase
 // A thread's array in shared memory, element i at p[i * kChaseThreads] (conflict-free: the
 // threads of a warp touch consecutive words for equal i).
-struct ThreadArray {
+template <int kStride>
+struct Strided {
     double* p;
-    __device__ __forceinline__ double& operator[](int i) const { return p[(size_t)i * kChaseThreads]; }
+    __device__ __forceinline__ double& operator[](int i) const { return p[(size_t)i * kStride]; }
 };
+using ThreadArray = Strided<kChaseThreads>;
 
 __global__ void __launch_bounds__(kChaseThreads) k_eig_chase(const EigArgs a) {
     extern __shared__ double csm[];
@@ -340,44 +342,33 @@ struct RotList {
 };
 
 // Q = Q_H R_1^T .. R_n^T, so Q^T z = R_n .. R_1 y: each recorded rotation, in order, turns
-// (y_k, y_k+1) into (c y_k + s y_k+1, c y_k+1 - s y_k) in all three vectors. The spectra are
-// written in ascending order of the poles (zero past nu).
-__global__ void __launch_bounds__(kChaseThreads) k_eig_spectra(const EigArgs a) {
+// (y_k, y_k+1) into (c y_k + s y_k+1, c y_k+1 - s y_k). A CTA takes 32 columns and one warp per
+// vector (c, d, g): three times the warps of a thread per column for the same instructions, and
+// the three threads of a column read its rotation list together. Written in ascending order of
+// the poles (zero past nu).
+constexpr int kSpecThreads = 96;
+__global__ void __launch_bounds__(kSpecThreads) k_eig_spectra(const EigArgs a) {
     extern __shared__ double csm[];
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
     if (c >= a.ncols) return;
     const int nm = a.nu_max;
     const int j = a.col0 + c;
     const int nu = a.nu_eff[j];
-    double* base = csm + threadIdx.x;
-    const ThreadArray Y0{base}, Y1{base + (size_t)nm * kChaseThreads}, Y2{base + 2 * (size_t)nm * kChaseThreads};
-    const double* y = a.tri + (size_t)c * eig_tri_doubles(nm) + 2 * nm;
-    for (int k = 0; k < nu; ++k) {
-        Y0[k] = y[k];
-        Y1[k] = y[nm + k];
-        Y2[k] = y[2 * nm + k];
-    }
+    const Strided<kSpecThreads> Y{csm + threadIdx.x};
+    const double* y = a.tri + (size_t)c * eig_tri_doubles(nm) + (2 + q) * (size_t)nm;
+    for (int k = 0; k < nu; ++k) Y[k] = y[k];
     const RotList R(a, c);
     for (int r = 0; r < R.n; ++r) {
         const double cr = __ldg(R.c + r), sr = __ldg(R.s + r);
         const int k = __ldg(R.k + r);
-        double p = Y0[k], q = Y0[k + 1];
-        Y0[k] = fma(cr, p, sr * q);
-        Y0[k + 1] = fma(cr, q, -sr * p);
-        p = Y1[k], q = Y1[k + 1];
-        Y1[k] = fma(cr, p, sr * q);
-        Y1[k + 1] = fma(cr, q, -sr * p);
-        p = Y2[k], q = Y2[k + 1];
-        Y2[k] = fma(cr, p, sr * q);
-        Y2[k + 1] = fma(cr, q, -sr * p);
+        const double p = Y[k], w = Y[k + 1];
+        Y[k] = fma(cr, p, sr * w);
+        Y[k + 1] = fma(cr, w, -sr * p);
     }
     const int* perm = a.perm + (size_t)c * nm;
-    for (int k = 0; k < nm; ++k) {
-        const int p = k < nu ? perm[k] : -1;
-        a.c[(size_t)j * nm + k] = p >= 0 ? Y0[p] : 0.0;
-        a.d[(size_t)j * nm + k] = p >= 0 ? Y1[p] : 0.0;
-        a.g[(size_t)j * nm + k] = p >= 0 ? Y2[p] : 0.0;
-    }
+    double* out = (q == 0 ? a.c : q == 1 ? a.d : a.g) + (size_t)j * nm;
+    for (int k = 0; k < nm; ++k) out[k] = k < nu ? Y[perm[k]] : 0.0;
 }
 
 // ----------------------------------------------------------------------------- k_eig_vectors
@@ -458,49 +449,72 @@ __global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a) {
 }
 
 // ----------------------------------------------------------------------------- k_eig_weights
-// The density weights of Eq. 2, w = 2 f(e_k - mu) c_k and w e_k (pole order), put back in the
-// order of the eigenvalue iteration and multiplied by R_1^T .. R_n^T: the recorded rotations in
-// reverse, each turning (w_k, w_k+1) into (c w_k - s w_k+1, s w_k + c w_k+1). Out:
-// T[batch col][2 nu_max] = (u, u_E), zero past nu; t = L^-T Q_H u is finished in the density.
-__global__ void __launch_bounds__(kChaseThreads) k_eig_weights(const EigArgs a, double mu, double kT, double* T) {
+// t = V w for the density weights of Eq. 2, w = 2 f(e_k - mu) c_k and w e_k, without V:
+// V w = L^-T Q_H R_1^T .. R_n^T w (w put back in the order of the eigenvalue iteration). In turn:
+//   the recorded rotations in reverse, each turning (w_k, w_k+1) into (c w_k - s w_k+1,
+//   s w_k + c w_k+1);
+//   the reflectors H_{nu-3} .. H_0, H_k x = x - tau_k v_k (v_k^T x);
+//   the back substitution L^T t = x (t_i = x_i / L_ii, then x_l -= L_il t_i for l < i).
+// One thread per (column, vector): a CTA takes 32 columns, warp 0 the vector w, warp 1 w e. No
+// reductions across lanes, so every FP64 instruction carries 32 columns.
+// Out: T[batch col][2 nu_max] = (t, t_E), zero past nu.
+constexpr int kWtThreads = 64;
+__global__ void __launch_bounds__(kWtThreads) k_eig_weights(const EigArgs a, double mu_in, const double* mu_dev,
+                                                             double kT, double* T) {
+    const double mu = mu_dev ? *mu_dev : mu_in;
     extern __shared__ double csm[];
-    const int c0 = blockIdx.x * blockDim.x, c = c0 + threadIdx.x;
+    const int lane = threadIdx.x & 31, v = threadIdx.x >> 5;
+    const int c0 = blockIdx.x * 32, c = c0 + lane;
     const int nm = a.nu_max;
-    double* base = csm + threadIdx.x;
-    const ThreadArray W{base}, WE{base + (size_t)nm * kChaseThreads};
+    const Strided<kWtThreads> X{csm + threadIdx.x};
     if (c < a.ncols) {
         const int j = a.col0 + c;
         const int nu = a.nu_eff[j];
-        for (int k = 0; k < nm; ++k) {
-            W[k] = 0.0;
-            WE[k] = 0.0;
-        }
+        for (int k = 0; k < nm; ++k) X[k] = 0.0;
         const int* perm = a.perm + (size_t)c * nm;
         for (int k = 0; k < nu; ++k) {
             const double e = a.eps[(size_t)j * nm + k];
             const double f2 = 2.0 * fermi((e - mu) / kT) * a.c[(size_t)j * nm + k];
-            const int p = perm[k];
-            W[p] = f2;
-            WE[p] = f2 * e;
+            X[perm[k]] = v ? f2 * e : f2;
         }
         const RotList R(a, c);
         for (int r = R.n - 1; r >= 0; --r) {
             const double cr = __ldg(R.c + r), sr = __ldg(R.s + r);
             const int k = __ldg(R.k + r);
-            double p = W[k], q = W[k + 1];
-            W[k] = fma(cr, p, -sr * q);
-            W[k + 1] = fma(cr, q, sr * p);
-            p = WE[k], q = WE[k + 1];
-            WE[k] = fma(cr, p, -sr * q);
-            WE[k + 1] = fma(cr, q, sr * p);
+            const double p = X[k], w = X[k + 1];
+            X[k] = fma(cr, p, -sr * w);
+            X[k + 1] = fma(cr, w, sr * p);
+        }
+        const double* F = a.fac + (size_t)c * eig_fac_doubles(nm);
+        for (int k = nu - 3; k >= 0; --k) {
+            const double* vk = F + (size_t)k * nm;
+            const double tau = vk[k];
+            if (tau == 0.0) continue;
+            double s0 = 0.0, s1 = 0.0;           // two partial sums: half the dependent chain
+            int i = k + 1;
+            for (; i + 1 < nu; i += 2) {
+                s0 = fma(vk[i], X[i], s0);
+                s1 = fma(vk[i + 1], X[i + 1], s1);
+            }
+            if (i < nu) s0 = fma(vk[i], X[i], s0);
+            const double sc = tau * (s0 + s1);
+            for (int m = k + 1; m < nu; ++m) X[m] = fma(-sc, vk[m], X[m]);
+        }
+        const double* L = F + (size_t)nm * nm;
+        for (int i = nu - 1; i >= 0; --i) {
+            const double* row = L + (size_t)i * nm;
+            const double ti = X[i] / row[i];
+            X[i] = ti;
+            for (int l = 0; l < i; ++l) X[l] = fma(-row[l], ti, X[l]);
         }
     }
     __syncthreads();
-    // coalesced write-out: element r of column c0 + t sits at csm[r * kChaseThreads + t]
-    const int ncl = min(kChaseThreads, a.ncols - c0);
-    for (int q = threadIdx.x; q < ncl * 2 * nm; q += kChaseThreads) {
+    // coalesced write-out: element k of vector v of column c0 + t sits at csm[k * 64 + v * 32 + t]
+    const int ncl = min(32, a.ncols - c0);
+    for (int q = threadIdx.x; q < ncl * 2 * nm; q += kWtThreads) {
         const int t = q / (2 * nm), r = q % (2 * nm);
-        T[(size_t)(c0 + t) * 2 * nm + r] = csm[(size_t)r * kChaseThreads + t];
+        const int vv = r / nm, k = r % nm;
+        T[(size_t)(c0 + t) * 2 * nm + r] = csm[(size_t)k * kWtThreads + vv * 32 + t];
     }
 }
 
@@ -518,9 +532,9 @@ void projected_eig(const EigArgs& a, cudaStream_t st, bool form_v) {
     const size_t s2 = eig_smem_threads(a.nu_max, 2);
     smem_at_least(k_eig_chase, s2);
     k_eig_chase<<<eig_thread_grid(a.ncols), kChaseThreads, s2, st>>>(a);
-    const size_t s3 = eig_smem_threads(a.nu_max, 3);
+    const size_t s3 = sizeof(double) * (size_t)a.nu_max * kSpecThreads;
     smem_at_least(k_eig_spectra, s3);
-    k_eig_spectra<<<eig_thread_grid(a.ncols), kChaseThreads, s3, st>>>(a);
+    k_eig_spectra<<<(a.ncols + 31) / 32, kSpecThreads, s3, st>>>(a);
     if (form_v) eig_vectors(a, st);
 }
 
@@ -530,10 +544,10 @@ void eig_vectors(const EigArgs& a, cudaStream_t st) {
     k_eig_vectors<<<a.ncols, 32, s, st>>>(a);
 }
 
-void eig_density_weights(const EigArgs& a, double mu, double kT, double* T, cudaStream_t st) {
-    const size_t s = eig_smem_threads(a.nu_max, 2);
+void eig_density_weights(const EigArgs& a, double mu, const double* mu_dev, double kT, double* T, cudaStream_t st) {
+    const size_t s = sizeof(double) * (size_t)a.nu_max * kWtThreads;
     smem_at_least(k_eig_weights, s);
-    k_eig_weights<<<eig_thread_grid(a.ncols), kChaseThreads, s, st>>>(a, mu, kT, T);
+    k_eig_weights<<<(a.ncols + 31) / 32, kWtThreads, s, st>>>(a, mu, mu_dev, kT, T);
 }
 
 }  // namespace elses

@@ -7,10 +7,13 @@
 // when N(mid) < N_e, else hi; stop when hi - lo < tol or after max_iter steps; mu = (lo+hi)/2.
 // E_band = sum 2 f g c = Tr(rho H) (Eq. 6); Omega = sum d c w(e), w = -2 kT ln(1 + e^{-(e-mu)/kT}).
 //
-// Once the bracket is narrower than 10 kT, one bisection step also keeps E_k = exp((e_k - mu0)/kT)
-// for the poles within 60 kT of its midpoint mu0 (when a buffer is given); every later midpoint x
-// lies within 5 kT of mu0, so f = 1 / (1 + E_k exp((mu0 - x)/kT)) needs one exponential per
-// launch instead of one per pole. The values agree with the direct form to rounding.
+// Once the bracket is narrower than 10 kT, the bisection step at its midpoint mu0 also keeps the
+// poles within 60 kT of mu0 as E_k = exp((e_k - mu0)/kT) with their weight d_k c_k, compacted
+// per block in pole order, and the sum of 2 d_k c_k of the poles below that window (when buffers
+// are given). Every later midpoint x lies within 5 kT of mu0, so a kept pole has
+// f = 1 / (1 + E_k exp((mu0 - x)/kT)), one exponential per launch instead of one per pole, a pole
+// under the window has f = 1 and one above it f = 0 (to e^-55 of its weight, far under the
+// rounding of the sums); the later steps read only the kept poles.
 //
 // Every evaluation is one grid-wide reduction in a fixed order (per-thread column strides, a
 // fixed block tree, then the block partials summed in index order by the last block to finish,
@@ -130,10 +133,11 @@ __global__ void k_bracket(const ReduceArgs a) {
     }
 }
 
-// mode 0: N(lo); 1: N(hi) and the bracket check; 2: one bisection step; 3: scalars at mu_in.
-// One thread per pole (flattened [column][k]); poles more than 50 kT from x contribute their
-// limit (f = 1 below, 0 above) without an exponential: the neglected part is below e^-50 of
-// their weight, far under the rounding of the sums.
+// mode 0: N(lo); 1: N(hi) and the bracket check; 2: one bisection step; 3: scalars at mu_in;
+// 4: scalars at the state's mu (written like mode 3).
+// Block b takes the poles of a contiguous range (flattened [column][k]); poles more than 50 kT
+// from x contribute their limit (f = 1 below, 0 above) without an exponential: the neglected part
+// is below e^-50 of their weight, far under the rounding of the sums.
 __global__ void __launch_bounds__(kRedThreads) k_count(const ReduceArgs a, int mode, double mu_in) {
     BisectState* s = a.state;
     double x;
@@ -142,37 +146,82 @@ __global__ void __launch_bounds__(kRedThreads) k_count(const ReduceArgs a, int m
         x = 0.5 * (s->lo + s->hi);
     } else if (mode == 0) x = s->lo;
     else if (mode == 1) x = s->hi;
+    else if (mode == 4) x = s->mu;
     else x = mu_in;
+    if (mode == 4) mode = 3;
     double v[3] = {0.0, 0.0, 0.0};
     const size_t total = (size_t)a.M * a.nu_max;
+    const size_t chunk = (total + gridDim.x - 1) / gridDim.x;
+    const size_t b0 = min(total, (size_t)blockIdx.x * chunk), b1 = min(total, b0 + chunk);
     const double inv_kT = 1.0 / a.kT;
-    const bool take_pre = mode == 2 && a.pre && !s->have_pre && s->hi - s->lo < 10.0 * a.kT;
-    const bool use_pre = mode == 2 && a.pre && s->have_pre;
-    const double scale = use_pre ? exp((s->mu0 - x) * inv_kT) : 1.0;
-    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
-         p += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(p / a.nu_max), k = (int)(p - (size_t)j * a.nu_max);
-        if (k >= __ldg(a.nu_eff + j)) continue;
-        const double e = a.eps[p], cc = a.c[p];
-        const double t = (e - x) * inv_kT;
-        if (take_pre && fabs(t) <= 60.0) a.pre[p] = exp(t);
-        double f2, om = 0.0;
-        if (t < -50.0) {
-            f2 = 2.0;
-            if (mode == 3) om = 2.0 * (e - x);
-        } else if (t > 50.0) {
-            continue;
-        } else if (use_pre) {
-            f2 = 2.0 / fma(a.pre[p], scale, 1.0);
-        } else {
-            f2 = 2.0 * fermi(t);
-            if (mode == 3) om = omega_w(e, x, a.kT);
+    const bool keep = mode == 2 && a.act && !s->have_pre && s->hi - s->lo < 10.0 * a.kT;
+    if (mode == 2 && a.act && s->have_pre) {
+        // the kept poles of this block; the block's constant part once, by thread 0
+        const double scale = exp((s->mu0 - x) * inv_kT);
+        const int n = a.act_n[blockIdx.x];
+        const double2* q = a.act + b0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const double2 w = q[i];
+            v[0] = fma(2.0 / fma(w.x, scale, 1.0), w.y, v[0]);
         }
-        const double dc = a.d[p] * cc;
-        v[0] = fma(f2, dc, v[0]);
-        if (mode == 3) {
-            v[1] = fma(f2 * a.g[p], cc, v[1]);
-            v[2] = fma(dc, om, v[2]);
+        if (threadIdx.x == 0) v[0] += a.act_below[blockIdx.x];
+    } else {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        __shared__ int wcount[kRedThreads / 32];
+        double below = 0.0;
+        int kept = 0;
+        for (size_t t0 = b0; t0 < b1; t0 += blockDim.x) {
+            const size_t p = t0 + threadIdx.x;
+            bool in_window = false;
+            double Ek = 0.0, dcw = 0.0;
+            if (p < b1) {
+                const int j = (int)(p / a.nu_max), k = (int)(p - (size_t)j * a.nu_max);
+                if (k < __ldg(a.nu_eff + j)) {
+                    const double e = a.eps[p], cc = a.c[p];
+                    const double t = (e - x) * inv_kT;
+                    const double dc = a.d[p] * cc;
+                    if (keep) {
+                        if (fabs(t) <= 60.0) {
+                            in_window = true;
+                            Ek = exp(t);
+                            dcw = dc;
+                        } else if (t < -60.0) {
+                            below = fma(2.0, dc, below);
+                        }
+                    }
+                    double f2 = 0.0, om = 0.0;
+                    if (t < -50.0) {
+                        f2 = 2.0;
+                        if (mode == 3) om = 2.0 * (e - x);
+                    } else if (t <= 50.0) {
+                        f2 = 2.0 * fermi(t);
+                        if (mode == 3) om = omega_w(e, x, a.kT);
+                    }
+                    v[0] = fma(f2, dc, v[0]);
+                    if (mode == 3) {
+                        v[1] = fma(f2 * a.g[p], cc, v[1]);
+                        v[2] = fma(dc, om, v[2]);
+                    }
+                }
+            }
+            if (keep) {   // this tile's kept poles, appended in pole order
+                const unsigned m = __ballot_sync(0xffffffffu, in_window);
+                if (lane == 0) wcount[wid] = __popc(m);
+                __syncthreads();
+                int off = kept, tot = kept;
+                for (int q = 0; q < kRedThreads / 32; ++q) {
+                    if (q < wid) off += wcount[q];
+                    tot += wcount[q];
+                }
+                if (in_window) a.act[b0 + off + __popc(m & ((1u << lane) - 1u))] = make_double2(Ek, dcw);
+                __syncthreads();
+                kept = tot;
+            }
+        }
+        if (keep) {
+            double bl[1] = {below};
+            block_reduce_store<1>(bl, a.act_below, 1);
+            if (threadIdx.x == 0) a.act_n[blockIdx.x] = kept;
         }
     }
     block_reduce_store<3>(v, a.partials, 4);
@@ -189,7 +238,7 @@ __global__ void __launch_bounds__(kRedThreads) k_count(const ReduceArgs a, int m
                 s->done = 1;
             }
         } else if (mode == 2) {
-            if (take_pre) {
+            if (keep) {
                 s->have_pre = 1;
                 s->mu0 = x;
             }
@@ -220,6 +269,10 @@ void bisect_step(const ReduceArgs& a, cudaStream_t st) {
 
 void scalars_at(const ReduceArgs& a, double mu, cudaStream_t st) {
     k_count<<<reduce_grid(), kRedThreads, 0, st>>>(a, 3, mu);
+}
+
+void scalars_at_state(const ReduceArgs& a, cudaStream_t st) {
+    k_count<<<reduce_grid(), kRedThreads, 0, st>>>(a, 4, 0.0);
 }
 
 // Density of states -(1/pi) Im sum_j sum_k d_k c_k / (z - e_k) at the energies z[iz] (grid

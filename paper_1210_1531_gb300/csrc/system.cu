@@ -57,6 +57,10 @@ int report_error(int code, const char* fmt, ...) {
         if (r_ < 0) return r_;     \
     } while (0)
 
+// Bumped by every device (re)allocation of a DevBuf: a captured graph whose buffers may have
+// moved is captured again.
+static unsigned long long g_alloc_epoch = 0;
+
 template <class T>
 struct DevBuf {
     T* p = nullptr;
@@ -72,6 +76,7 @@ struct DevBuf {
             return fail(ELSES_ERR_OOM, "device allocation of %zu bytes failed", want * sizeof(T));
         }
         cap = want;
+        ++g_alloc_epoch;
         return 0;
     }
     void release() {
@@ -79,6 +84,10 @@ struct DevBuf {
         p = nullptr;
         cap = 0;
     }
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
 };
 
 struct elses_system_s {
@@ -103,11 +112,12 @@ struct elses_system_s {
     std::vector<int> h_row_ptr;
 
     int nu_max = 0, na_max = 0, k3_grid = 0, batch_atoms = 0, deg_cap = 0, k3_bps = 0;
+    std::vector<int> tuned_bps;            // autotuner: resident Krylov CTAs per SM by cluster slots
     // Krylov launches: per batch of atoms, one launch per cluster size class (slots of 32 atoms),
     // each with its own shared-memory footprint and resident-CTA count
     // scratch_off: where the launch's per-CTA scratch starts, so that the class launches of one
     // batch can run at the same time
-    struct K3Launch { int batch_begin, batch_end, item_begin, item_count, na, grid; size_t scratch_off; };
+    struct K3Launch { int batch_begin, batch_end, item_begin, item_count, na, grid, bps; size_t scratch_off; };
     cudaStream_t side = nullptr;           // second stream for concurrent class launches
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<K3Launch> k3_launches;
@@ -125,7 +135,9 @@ struct elses_system_s {
     // the eigen-factors of every column are in the batch buffers and the stored V is not formed
     bool v_lazy = false;
     std::vector<int> adj_bps;              // resident adjoint CTAs per SM, by cluster slots
-    DevBuf<double> partials, zbuf, pre, gbuf, dosbuf;
+    DevBuf<double> partials, zbuf, gbuf, dosbuf, act_below;
+    DevBuf<double2> act;
+    DevBuf<int> act_n;
     DevBuf<BisectState> bstate;
     DevBuf<unsigned> ticket;
     std::vector<char> atom_done;
@@ -146,24 +158,57 @@ struct elses_system_s {
         else cudaEventCreate(&e);
         return e;
     }
+    // while a step is captured into the graph form, the timing events become event-record
+    // nodes of the graph (recorded at every replay, read by collect_graph)
+    bool capturing = false;
+    std::vector<EvPair> graph_ev;
     void tic(int cat, cudaStream_t st) {
         if (!p.timing) return;
         EvPair q{ev(), ev(), cat};
-        cudaEventRecord(q.a, st);
-        pending.push_back(q);
+        if (capturing) {
+            cudaEventRecordWithFlags(q.a, st, cudaEventRecordExternal);
+            graph_ev.push_back(q);
+        } else {
+            cudaEventRecord(q.a, st);
+            pending.push_back(q);
+        }
     }
     void toc(cudaStream_t st) {
-        if (!p.timing || pending.empty()) return;
+        if (!p.timing) return;
+        if (capturing) {
+            if (!graph_ev.empty()) cudaEventRecordWithFlags(graph_ev.back().b, st, cudaEventRecordExternal);
+            return;
+        }
+        if (pending.empty()) return;
         cudaEventRecord(pending.back().b, st);
+    }
+    void add_time(const EvPair& q) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+            double* slot[] = {&stats.t_krylov_ms, &stats.t_eig_ms, &stats.t_bisect_ms,
+                              &stats.t_density_ms, &stats.t_force_ms, &stats.t_adjoint_ms};
+            *slot[q.cat] += ms;
+        }
+    }
+    void collect_graph() {   // after a synchronisation of the stream that replayed the graph
+        for (auto& q : graph_ev) add_time(q);
+        cudaGetLastError();
+    }
+    // graph form of elses_energy_force (params.graph): the captured step, what it was captured
+    // for (launch plan, buffers, forces output, parameters), the kernels it launches
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t gstream = nullptr;       // capture stream (the legacy stream cannot capture)
+    std::vector<long long> graph_key;
+    long long graph_launches = 0, graph_krylov = 0, graph_columns = 0;
+    void drop_graph() {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        graph_exec = nullptr;
+        for (auto& q : graph_ev) { pool.push_back(q.a); pool.push_back(q.b); }
+        graph_ev.clear();
     }
     void collect() {   // after a synchronisation of the stream
         for (auto& q : pending) {
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
-                double* slot[] = {&stats.t_krylov_ms, &stats.t_eig_ms, &stats.t_bisect_ms,
-                                  &stats.t_density_ms, &stats.t_force_ms, &stats.t_adjoint_ms};
-                *slot[q.cat] += ms;
-            }
+            add_time(q);
             pool.push_back(q.a);
             pool.push_back(q.b);
         }
@@ -171,6 +216,8 @@ struct elses_system_s {
         cudaGetLastError();
     }
     ~elses_system_s() {
+        drop_graph();
+        if (gstream) cudaStreamDestroy(gstream);
         for (auto& q : pending) { pool.push_back(q.a); pool.push_back(q.b); }
         for (auto e : pool) cudaEventDestroy(e);
     }
@@ -264,8 +311,9 @@ int prepare_columns(elses_system s) {
             int bps = s->p.krylov_block ? block_krylov_blocks_per_sm(na, kdeg) : krylov_blocks_per_sm(na, kdeg);
             if (bps < 1) return fail(ELSES_ERR_CAPACITY, "Krylov kernel cannot be resident (%d-atom class)", na);
             if (s->p.k3_ctas_per_sm > 0) bps = std::min(bps, s->p.k3_ctas_per_sm);
+            else if (ns < (int)s->tuned_bps.size() && s->tuned_bps[ns] > 0) bps = std::min(bps, s->tuned_bps[ns]);
             const int grid = std::min(count, s->num_sms * bps);
-            s->k3_launches.push_back({b, e, begin, count, na, grid, batch_off});
+            s->k3_launches.push_back({b, e, begin, count, na, grid, bps, batch_off});
             batch_off += s->p.krylov_block ? (size_t)grid * block_krylov_scratch_doubles(nm, na)
                                            : (size_t)grid * kWarpsPerAtom * 2 * nm * na * 4;
             scratch = std::max(scratch, batch_off);
@@ -327,7 +375,9 @@ int prepare_columns(elses_system s) {
     }
     TRY(s->gblock.ensure((size_t)s->nnzb * 3));
     TRY(s->partials.ensure(4 * (size_t)reduce_grid()));
-    TRY(s->pre.ensure(M * nm));
+    TRY(s->act.ensure(M * nm));
+    TRY(s->act_n.ensure(reduce_grid()));
+    TRY(s->act_below.ensure(reduce_grid()));
     TRY(s->bstate.ensure(1));
     TRY(s->ticket.ensure(1));
     CUDA_TRY(cudaMemset(s->ticket.p, 0, sizeof(unsigned)));
@@ -507,7 +557,7 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
 // ([nnzb][16], overwritten): per batch, the adjoint kernel per size class, after the batch's
 // Krylov columns are recomputed when V is not kept (two-pass mode).
 int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* gS, double s_scale,
-                 cudaStream_t st) {
+                 cudaStream_t st, const double* mu_dev = nullptr) {
     const int nm = s->nu_max;
     const int kdeg = s->user_hs ? s->max_nb : s->deg_cap;
     CUDA_TRY(cudaMemsetAsync(gH, 0, sizeof(double) * 16 * (size_t)s->nnzb, st));
@@ -547,6 +597,7 @@ int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* 
         ga.c = s->cc.p;
         ga.d = s->dd.p;
         ga.mu = mu;
+        ga.mu_dev = mu_dev;
         ga.kT = s->p.kT;
         ga.gH = gH;
         ga.gS = gS;
@@ -591,6 +642,67 @@ int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* 
     return 0;
 }
 
+// The autotuner: per size class of the first batch, the Krylov kernel timed at every resident
+// CTA count that fits, on the class's first atoms in launch order (up to two full waves at the
+// largest count); the fastest per atom is kept in tuned_bps and the launches are planned again.
+int autotune_impl(elses_system s, cudaStream_t st) {
+    const int nm = s->nu_max;
+    const int kdeg = s->user_hs ? s->max_nb : s->deg_cap;
+    s->tuned_bps.assign(s->na_max / 32 + 1, 0);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    int rc = 0;
+    const auto launches = s->k3_launches;
+    for (const auto& L : launches) {
+        if (L.batch_begin != 0 || rc) continue;
+        const int ns = L.na / 32;
+        const int maxb = s->p.krylov_block ? block_krylov_blocks_per_sm(L.na, kdeg) : krylov_blocks_per_sm(L.na, kdeg);
+        const int sample = std::min(L.item_count, 2 * s->num_sms * maxb);
+        const size_t per_cta = s->p.krylov_block ? block_krylov_scratch_doubles(nm, L.na)
+                                                 : (size_t)kWarpsPerAtom * 2 * nm * L.na * 4;
+        if ((rc = s->kscratch.ensure((size_t)s->num_sms * maxb * per_cta)) < 0) break;
+        double best = 0.0;
+        int best_b = maxb;
+        for (int b = 1; b <= maxb && !rc; ++b) {
+            KrylovArgs ka = krylov_args(s, L.batch_begin, L.batch_end);
+            ka.UP = nullptr;
+            ka.flops = nullptr;
+            ka.na_max = L.na;
+            ka.order = s->order.p + L.item_begin;
+            ka.n_items = sample;
+            ka.scratch = s->kscratch.p;
+            const int grid = std::min(sample, s->num_sms * b);
+            float ms = 0.f;
+            for (int rep = 0; rep < 2; ++rep) {       // the first launch warms caches and clocks
+                if (s->p.schedule == 1) {
+                    ka.queue = s->counters.p + kQueue0;
+                    if (cudaMemsetAsync(ka.queue, 0, sizeof(int), st) != cudaSuccess) { rc = fail(ELSES_ERR_CUDA, "memset"); break; }
+                }
+                cudaEventRecord(e0, st);
+                if (s->p.krylov_block) block_krylov_columns(ka, grid, st);
+                else krylov_columns(ka, grid, st);
+                cudaEventRecord(e1, st);
+                s->stats.launches++;
+            }
+            if (rc) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                rc = fail(ELSES_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(cudaGetLastError()));
+                break;
+            }
+            const double per_atom = ms / sample;
+            if (b == 1 || per_atom < best) { best = per_atom; best_b = b; }
+        }
+        if (!rc) s->tuned_bps[ns] = best_b;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) { s->tuned_bps.clear(); return rc; }
+    TRY(clear_status(s, st));        // the sampled columns may have flagged a breakdown
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return prepare_columns(s);       // launch plan with the chosen shapes; columns invalidated
+}
+
 int check_built(elses_system s) {
     if (!s) return fail(ELSES_ERR_ARG, "null system");
     if (s->n <= 0 || !s->H.p) return fail(ELSES_ERR_STATE, "system not built");
@@ -613,7 +725,9 @@ ReduceArgs reduce_args(elses_system s) {
     r.state = s->bstate.p;
     r.partials = s->partials.p;
     r.ticket = s->ticket.p;
-    r.pre = s->pre.p;
+    r.act = s->act.p;
+    r.act_n = s->act_n.p;
+    r.act_below = s->act_below.p;
     return r;
 }
 
@@ -642,21 +756,7 @@ const char* elses_last_error(void) { return g_err.c_str(); }
 
 void elses_system_destroy(elses_system s) {
     if (!s) return;
-    DevBuf<double>* dbs[] = {&s->pos, &s->H, &s->S, &s->skr, &s->pre, &s->gbuf, &s->dosbuf, &s->bstore, &s->ascratch, &s->adjH, &s->adjS, &s->kscratch, &s->Hp, &s->Sp, &s->urow,
-                             &s->surow, &s->hurow, &s->etri, &s->efac, &s->erot_c, &s->erot_s,
-                             &s->eps, &s->cc, &s->dd, &s->gg,
-                             &s->V, &s->UP, &s->Vb, &s->UPb, &s->rho, &s->rhoE, &s->gblock,
-                             &s->partials, &s->zbuf};
-    for (auto* b : dbs) b->release();
-    s->flops_ctr.release();
-    DevBuf<int>* ibs[] = {&s->cell_of, &s->cell_count, &s->cell_start, &s->cursor, &s->cell_atoms,
-                          &s->row_cnt, &s->row_ptr, &s->col_idx, &s->row_of, &s->tmap, &s->cl_cnt,
-                          &s->cl_ptr, &s->cl_idx, &s->counters, &s->nu_eff, &s->order, &s->erot_n,
-                          &s->eperm};
-    s->erot_k.release();
-    for (auto* b : ibs) b->release();
-    s->bstate.release();
-    s->ticket.release();
+    // the device buffers are freed by their destructors
     if (s->side) {
         cudaStreamSynchronize(s->side);
         cudaStreamDestroy(s->side);
@@ -829,6 +929,7 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
     s->stats.launches += 2;
     TRY(check_status(s, st));
     TRY(prepare_columns(s));
+    if (s->p.autotune && s->tuned_bps.empty() && s->p.k3_ctas_per_sm <= 0) TRY(autotune_impl(s, st));
     return ELSES_OK;
 }
 
@@ -930,10 +1031,12 @@ int elses_find_mu(elses_system s, double* mu_host, double* n_at_mu_host, void* s
 }
 
 // rho columns of atoms [b, e) at mu: from V where it is formed, else from the eigen-factors of the
-// batch just computed (the weights with the rotations applied, then reflectors and L^-T).
+// batch just computed (t = V w formed by k_eig_weights).
 static void density_batch(elses_system s, double mu, double* rho, double* rhoE, int b, int e, const double* V,
-                          int v0, const double* UP, int u0, bool factors, cudaStream_t st) {
+                          int v0, const double* UP, int u0, bool factors, cudaStream_t st,
+                          const double* mu_dev = nullptr) {
     DensityArgs d = density_args(s, mu, rho, rhoE);
+    d.mu_dev = mu_dev;
     d.atom_begin = b;
     d.atom_end = e;
     d.V = V;
@@ -942,21 +1045,22 @@ static void density_batch(elses_system s, double mu, double* rho, double* rhoE, 
     d.up_block0 = u0;
     s->tic(T_DENSITY, st);
     if (factors) {
-        eig_density_weights(eig_args(s, b, e, nullptr), mu, s->p.kT, s->ewt.p, st);
+        eig_density_weights(eig_args(s, b, e, nullptr), mu, mu_dev, s->p.kT, s->ewt.p, st);
         s->stats.launches++;
         d.T = s->ewt.p;
-        d.fac = s->efac.p;
     }
     density_columns(d, st);
     s->toc(st);
     s->stats.launches++;
 }
 
-static int density_impl(elses_system s, double mu, double* rho, double* rhoE, cudaStream_t st) {
+// mu_dev: when set, mu is read from device memory (the captured step of the graph form).
+static int density_impl(elses_system s, double mu, double* rho, double* rhoE, cudaStream_t st,
+                        const double* mu_dev = nullptr) {
     if (s->atoms_done != s->n) return fail(ELSES_ERR_STATE, "density_matrix needs every column");
-    TRY(clear_status(s, st));
+    if (!mu_dev) TRY(clear_status(s, st));
     if (!s->p.two_pass) {
-        density_batch(s, mu, rho, rhoE, 0, s->n, s->V.p, 0, s->UP.p, 0, s->v_lazy, st);
+        density_batch(s, mu, rho, rhoE, 0, s->n, s->V.p, 0, s->UP.p, 0, s->v_lazy, st, mu_dev);
     } else {
         // second calculation of G (Eq. 3): recompute every batch, then its rho columns
         for (int b = 0; b < s->n; b += s->batch_atoms) {
@@ -965,7 +1069,7 @@ static int density_impl(elses_system s, double mu, double* rho, double* rhoE, cu
             double* UP;
             int v0, u0;
             TRY(run_batch(s, b, e, false, &V, &v0, &UP, &u0, st, true, false));
-            density_batch(s, mu, rho, rhoE, b, e, V, v0, UP, u0, true, st);
+            density_batch(s, mu, rho, rhoE, b, e, V, v0, UP, u0, true, st, mu_dev);
         }
     }
     return 0;
@@ -1000,11 +1104,11 @@ int elses_energies(elses_system s, double mu, double* n_host, double* e_band_hos
     return ELSES_OK;
 }
 
-int elses_energy_force(elses_system s, double* mu_host, double* e_band_host, double* f_free_host,
-                       double* forces_dev, void* stream) {
-    TRY(check_built(s));
-    cudaStream_t st = (cudaStream_t)stream;
-    if (forces_dev && s->user_hs) return fail(ELSES_ERR_STATE, "forces need the Slater-Koster H, S");
+namespace {
+
+int energy_force_eager(elses_system s, double* mu_host, double* e_band_host, double* f_free_host,
+                       double* forces_dev, cudaStream_t st) {
+    void* stream = (void*)st;
     int warn = elses_green_columns(s, 0, s->M, 0, nullptr, nullptr, nullptr, stream);
     if (warn < 0) return warn;
     double mu = 0.0;
@@ -1040,6 +1144,171 @@ int elses_energy_force(elses_system s, double* mu_host, double* e_band_host, dou
     if (e_band_host) *e_band_host = h.e_band;
     if (f_free_host) *f_free_host = h.omega + mu * s->p.n_electrons;
     return warn > 0 ? warn : rc;
+}
+
+// The device work of one energy + force evaluation, enqueued with no host synchronisation (the
+// captured step of the graph form): the columns, the bisection's fixed sequence of launches
+// (those after convergence return at once), the density, the scalars and the forces, all at the
+// mu the bisection leaves in device memory. The same kernels and arguments as the eager path.
+int enqueue_step(elses_system s, double* forces_dev, cudaStream_t st) {
+    TRY(clear_status(s, st));
+    const bool stored = !s->p.two_pass;
+    for (int b = 0; b < s->n; b += s->batch_atoms) {
+        const int e = std::min(s->n, b + s->batch_atoms);
+        double *V = nullptr, *UP = nullptr;
+        int v0 = 0, u0 = 0;
+        TRY(run_batch(s, b, e, stored, &V, &v0, &UP, &u0, st, stored, false));
+    }
+    s->atom_done.assign(s->n, 1);
+    s->atoms_done = s->n;
+    ReduceArgs r = reduce_args(s);
+    s->tic(T_BISECT, st);
+    bisect_init(r, st);
+    for (int it = 0; it < s->p.max_bisect; ++it) bisect_step(r, st);
+    s->toc(st);
+    s->stats.launches += 3 + s->p.max_bisect;
+    const double* mu_dev = (const double*)((const char*)s->bstate.p + offsetof(BisectState, mu));
+    TRY(density_impl(s, 0.0, s->rho.p, s->rhoE.p, st, mu_dev));
+    s->tic(T_BISECT, st);
+    scalars_at_state(r, st);
+    s->toc(st);
+    s->stats.launches++;
+    if (forces_dev) {
+        const double* gh = s->rho.p;
+        const double* gs = s->rhoE.p;
+        if (s->p.force_mode == 1) {
+            TRY(adjoint_impl(s, 0.0, 0, s->n, s->adjH.p, s->adjS.p, -1.0, st, mu_dev));
+            gh = s->adjH.p;
+            gs = s->adjS.p;
+        }
+        s->tic(T_FORCE, st);
+        forces(s->pos.p, s->n, s->box, s->skd, s->row_ptr.p, s->col_idx.p, s->row_of.p, s->tmap.p, s->nnzb,
+               gh, gs, s->gblock.p, forces_dev, st);
+        s->toc(st);
+        s->stats.launches += 2;
+    }
+    return 0;
+}
+
+// What a captured step depends on besides device data: the buffers (allocation epoch), the
+// forces output, the parameters and the Krylov launch plan.
+std::vector<long long> graph_key(elses_system s, const double* forces_dev) {
+    std::vector<long long> k = {(long long)g_alloc_epoch, (long long)(uintptr_t)forces_dev, s->n, s->nnzb,
+                                s->nu_max, s->na_max, s->batch_atoms, s->user_hs ? 1 : 0, s->max_nb,
+                                s->max_cl, s->deg_cap};
+    auto add_bytes = [&k](const void* src, size_t bytes) {
+        std::vector<long long> w((bytes + 7) / 8, 0);
+        std::memcpy(w.data(), src, bytes);
+        k.insert(k.end(), w.begin(), w.end());
+    };
+    add_bytes(&s->p, sizeof(elses_params));
+    add_bytes(s->box, sizeof(s->box));
+    add_bytes(&s->skd, sizeof(s->skd));
+    for (int b = 0; b < s->n; b += s->batch_atoms) k.push_back(s->h_row_ptr[b]);   // batch pattern offsets
+    for (const auto& L : s->k3_launches) {
+        k.insert(k.end(), {L.batch_begin, L.batch_end, L.item_begin, L.item_count, L.na, L.grid, L.bps,
+                           (long long)L.scratch_off});
+    }
+    return k;
+}
+
+int capture_step(elses_system s, double* forces_dev) {
+    s->drop_graph();
+    if (!s->gstream) CUDA_TRY(cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking));
+    if (!s->side) {   // the second stream and its events exist before the capture
+        TRY(fork_side(s, s->gstream));
+        TRY(join_side(s, s->gstream));
+        CUDA_TRY(cudaStreamSynchronize(s->gstream));
+    }
+    const long long l0 = s->stats.launches, c0 = s->stats.columns, k0 = s->stats.krylov_launches;
+    CUDA_TRY(cudaStreamBeginCapture(s->gstream, cudaStreamCaptureModeRelaxed));
+    s->capturing = true;
+    int rc = enqueue_step(s, forces_dev, s->gstream);
+    s->capturing = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s->gstream, &g);
+    s->graph_launches = s->stats.launches - l0;
+    s->graph_krylov = s->stats.krylov_launches - k0;
+    s->graph_columns = s->stats.columns - c0;
+    s->stats.launches = l0;            // counted at every replay
+    s->stats.columns = c0;
+    s->stats.krylov_launches = k0;
+    if (rc >= 0 && ce != cudaSuccess) rc = fail(ELSES_ERR_CUDA, "stream capture: %s", cudaGetErrorString(ce));
+    if (rc >= 0 && cudaGraphInstantiate(&s->graph_exec, g, 0) != cudaSuccess) {
+        s->graph_exec = nullptr;
+        rc = fail(ELSES_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    if (g) cudaGraphDestroy(g);
+    if (rc < 0) s->drop_graph();
+    return rc;
+}
+
+// The graph form: the first call with a new plan runs the eager path (and checks it), the next
+// captures the step, later calls replay it; one host synchronisation per call.
+int energy_force_graph(elses_system s, double* mu_host, double* e_band_host, double* f_free_host,
+                       double* forces_dev, cudaStream_t st) {
+    if (!s->graph_exec || graph_key(s, forces_dev) != s->graph_key) {
+        if (graph_key(s, forces_dev) != s->graph_key) {
+            s->drop_graph();
+            const int rc = energy_force_eager(s, mu_host, e_band_host, f_free_host, forces_dev, st);
+            if (rc >= 0) s->graph_key = graph_key(s, forces_dev);
+            return rc;
+        }
+        CUDA_TRY(cudaStreamSynchronize(st));   // the capture only records; nothing runs
+        TRY(capture_step(s, forces_dev));
+    }
+    CUDA_TRY(cudaGraphLaunch(s->graph_exec, st));
+    s->stats.launches += s->graph_launches;
+    s->stats.krylov_launches += s->graph_krylov;
+    s->stats.columns += s->graph_columns;
+    s->have_rho = true;
+    BisectState h{};
+    CUDA_TRY(cudaMemcpyAsync(&h, s->bstate.p, sizeof h, cudaMemcpyDeviceToHost, st));
+    const int rc = check_status(s, st);
+    s->collect_graph();
+    s->stats.bisect_steps = h.iter;
+    if (h.status & DEV_NONFINITE) return fail(ELSES_ERR_NONFINITE, "non-finite poles");
+    if (h.status & DEV_NO_BRACKET)
+        return fail(ELSES_ERR_NO_BRACKET, "N(lo)=%.17g N(hi)=%.17g do not bracket N_e=%.17g", h.n_lo, h.n_hi,
+                    s->p.n_electrons);
+    if (rc < 0) return rc;
+    s->mu = h.mu;
+    s->have_mu = true;
+    if (mu_host) *mu_host = h.mu;
+    if (e_band_host) *e_band_host = h.e_band;
+    if (f_free_host) *f_free_host = h.omega + h.mu * s->p.n_electrons;
+    return rc;
+}
+
+}  // namespace
+
+int elses_energy_force(elses_system s, double* mu_host, double* e_band_host, double* f_free_host,
+                       double* forces_dev, void* stream) {
+    TRY(check_built(s));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (forces_dev && s->user_hs) return fail(ELSES_ERR_STATE, "forces need the Slater-Koster H, S");
+    if (s->p.graph) return energy_force_graph(s, mu_host, e_band_host, f_free_host, forces_dev, st);
+    return energy_force_eager(s, mu_host, e_band_host, f_free_host, forces_dev, st);
+}
+
+int elses_autotune(elses_system s, int run, int max_classes, int* classes_out, int* n_host, void* stream) {
+    TRY(check_built(s));
+    if (max_classes < 0 || (max_classes > 0 && !classes_out)) return fail(ELSES_ERR_ARG, "bad class output");
+    if (run) {
+        if (s->p.k3_ctas_per_sm > 0) return fail(ELSES_ERR_STATE, "k3_ctas_per_sm fixes the launch shape");
+        TRY(autotune_impl(s, (cudaStream_t)stream));
+    }
+    int n = 0;
+    for (const auto& L : s->k3_launches) {   // the classes of the first batch, largest first
+        if (L.batch_begin != 0) continue;
+        if (n < max_classes) {
+            classes_out[2 * n] = L.na / 32;
+            classes_out[2 * n + 1] = L.bps;
+        }
+        ++n;
+    }
+    if (n_host) *n_host = n;
+    return ELSES_OK;
 }
 
 int elses_cohp_spectrum(elses_system s, int n_z, const double* z_host, double* C_dev, double* Csig_dev,

@@ -1,0 +1,43 @@
+"""The autotuner of the Krylov launch shape (elses_autotune): it picks, per cluster size class,
+the resident CTAs per SM by timing, and the results do not depend on the shape."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eg():
+    return gu.library()
+
+
+def test_autotuned_shape_keeps_results_bit_for_bit(eg):
+    w = wl.make("diamond_4096")
+    s = eg.system_for(w, schedule=1)
+    mu, e_band, _, F = s.energy_force()
+    F = gu.to_np(F)
+    shapes = s.autotune()
+    assert len(shapes) >= 1
+    for slots, bps in shapes.items():
+        assert 1 <= slots <= 16 and 1 <= bps <= 8
+    assert s.stats()["k3_ctas_per_sm"] in shapes.values()
+    mu2, e_band2, _, F2 = s.energy_force()               # columns recomputed with the new shape
+    assert mu2 == mu and e_band2 == e_band and np.array_equal(gu.to_np(F2), F)
+
+
+def test_autotune_at_build(eg):
+    w = wl.make("diamond_64")
+    a = eg.system_for(w)
+    b = eg.system_for(w, autotune=True)
+    ra, rb = a.energy_force(), b.energy_force()
+    assert ra[0] == rb[0] and ra[1] == rb[1] and np.array_equal(gu.to_np(ra[3]), gu.to_np(rb[3]))
+
+
+def test_autotune_refused_when_the_shape_is_fixed(eg):
+    s = eg.system_for(wl.make("diamond_64"), k3_ctas_per_sm=2)
+    with pytest.raises(eg.ElsesError) as err:
+        s.autotune()
+    assert err.value.code == -9

@@ -31,7 +31,10 @@ def test_find_mu_static_matches_find_mu_on_two_calls(name):
                                      w.n_electrons, g=sp["g"])
         if call == 1:       # after the first call's one-time address lookup nothing moves
             assert torch.cuda.mem_get_info()[0] == free_before
-        assert abs(mu - mu_ref) <= 1e-13
+        # two bisections with mu_tol = 1e-13 end within half a bracket of their own crossing
+        # of N_e; the crossings differ by the rounding of two summation orders (the static
+        # entry sums every pole, the system keeps the poles near mu once the bracket is narrow)
+        assert abs(mu - mu_ref) <= 3e-13
         assert abs(n - n_ref) <= 1e-8
         assert abs(e - e_ref) / w.n_atoms <= gu.E_TOL_PER_ATOM
     s.close()
