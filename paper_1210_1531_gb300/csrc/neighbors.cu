@@ -179,11 +179,24 @@ __global__ void k_lists(const double* __restrict__ pos, int n, CellGrid g,
         for (int b = 0; b < count[1]; ++b) {
             int cy = first[1] + b;
             if (!absol[1]) cy = (cy % g.nc[1] + g.nc[1]) % g.nc[1];
-            for (int e = 0; e < count[2]; ++e) {
-                int cz = first[2] + e;
-                if (!absol[2]) cz = (cz % g.nc[2] + g.nc[2]) % g.nc[2];
-                const int cc = (cx * g.nc[1] + cy) * g.nc[2] + cz;
-                const int s0 = cell_start[cc], s1 = cell_start[cc + 1];
+            // the stencil's cells along z are consecutive in the cell order, so their atoms form
+            // one range of cell_atoms (two where the stencil wraps around the box)
+            int zlo[2], zhi[2], nr = 0;
+            if (absol[2]) {
+                zlo[0] = 0;
+                zhi[0] = g.nc[2];
+                nr = 1;
+            } else {
+                int lo = first[2], hi = first[2] + count[2];     // [lo, hi), count < nc
+                if (lo < 0) { zlo[nr] = lo + g.nc[2]; zhi[nr] = g.nc[2]; ++nr; lo = 0; }
+                else if (hi > g.nc[2]) { zlo[nr] = 0; zhi[nr] = hi - g.nc[2]; ++nr; hi = g.nc[2]; }
+                zlo[nr] = lo;
+                zhi[nr] = hi;
+                ++nr;
+            }
+            for (int run = 0; run < nr; ++run) {
+                const int row = (cx * g.nc[1] + cy) * g.nc[2];
+                const int s0 = cell_start[row + zlo[run]], s1 = cell_start[row + zhi[run]];
                 for (int base = s0; base < s1; base += 32) {
                     const int q = base + lane;
                     bool hit = false;

@@ -531,9 +531,11 @@ void projected_eig(const EigArgs& a, cudaStream_t st, bool form_v) {
     k_eig_reduce<<<(a.ncols + 1) / 2, 64, s1, st>>>(a);
     const size_t s2 = eig_smem_threads(a.nu_max, 2);
     smem_at_least(k_eig_chase, s2);
+    carveout_for(k_eig_chase, s2, eig_thread_grid(a.ncols));
     k_eig_chase<<<eig_thread_grid(a.ncols), kChaseThreads, s2, st>>>(a);
     const size_t s3 = sizeof(double) * (size_t)a.nu_max * kSpecThreads;
     smem_at_least(k_eig_spectra, s3);
+    carveout_for(k_eig_spectra, s3, (a.ncols + 31) / 32);
     k_eig_spectra<<<(a.ncols + 31) / 32, kSpecThreads, s3, st>>>(a);
     if (form_v) eig_vectors(a, st);
 }
@@ -547,6 +549,7 @@ void eig_vectors(const EigArgs& a, cudaStream_t st) {
 void eig_density_weights(const EigArgs& a, double mu, const double* mu_dev, double kT, double* T, cudaStream_t st) {
     const size_t s = sizeof(double) * (size_t)a.nu_max * kWtThreads;
     smem_at_least(k_eig_weights, s);
+    carveout_for(k_eig_weights, s, (a.ncols + 31) / 32);
     k_eig_weights<<<(a.ncols + 31) / 32, kWtThreads, s, st>>>(a, mu, mu_dev, kT, T);
 }
 

@@ -91,13 +91,13 @@ __device__ __forceinline__ void sum_partials(const double* partials, int nblocks
 
 __global__ void k_bracket(const ReduceArgs a) {
     double mn = 1e300, mx = -1e300;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.M; j += gridDim.x * blockDim.x) {
-        const int nu = a.nu_eff[j];
-        for (int k = 0; k < nu; ++k) {
-            const double e = a.eps[(size_t)j * a.nu_max + k];
-            mn = fmin(mn, e);
-            mx = fmax(mx, e);
-        }
+    const size_t total = (size_t)a.M * a.nu_max;   // one thread per pole slot (coalesced)
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(p / a.nu_max), k = (int)(p - (size_t)j * a.nu_max);
+        if (k >= __ldg(a.nu_eff + j)) continue;
+        const double e = a.eps[p];
+        mn = fmin(mn, e);
+        mx = fmax(mx, e);
     }
     __shared__ double smn[kRedThreads], smx[kRedThreads];
     smn[threadIdx.x] = mn;
