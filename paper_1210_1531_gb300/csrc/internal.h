@@ -154,6 +154,7 @@ struct BisectState {
     double n_lo, n_hi, n_mid;
     double n_at, e_band, omega;
     double mu0;             // where the kept exponentials were taken
+    double scale;           // exp((mu0 - x)/kT) at the next midpoint x, once they are kept
     int iter, done, status, have_pre;
 };
 struct ReduceArgs {
@@ -165,6 +166,7 @@ struct ReduceArgs {
     const double* g;
     const int* nu_eff;
     double kT;
+    double inv_kT;          // 1 / kT (host-computed: not one division per thread)
     double n_electrons;
     double tol;
     int max_iter;

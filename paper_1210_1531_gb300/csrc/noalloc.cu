@@ -79,6 +79,7 @@ extern "C" int elses_find_mu_static(int n_columns, int nu_max, const double* eps
     r.g = g_dev ? g_dev : d_dev;
     r.nu_eff = nu_eff_dev;
     r.kT = kT;
+    r.inv_kT = 1.0 / kT;
     r.n_electrons = n_electrons;
     r.tol = mu_tol > 0 ? mu_tol : 1e-13;
     r.max_iter = max_bisect > 0 ? max_bisect : 100;

@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(64) k_eig_reduce(const EigArgs a) {
     for (int k = 0; k < nu; ++k) {
         const double dk = L[k * ld + k];
         if (!(dk > 0.0)) { spd = false; break; }
-        const double lkk = sqrt(dk), ik = 1.0 / lkk;
+        const double ik = rsqrt(dk), lkk = dk * ik;   // one reciprocal square root, no division
         __syncwarp();
         for (int i = k + 1 + lane; i < nu; i += 32) L[i * ld + k] *= ik;
         if (lane == 0) { L[k * ld + k] = lkk; inv[k] = ik; }

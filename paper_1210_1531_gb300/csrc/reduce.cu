@@ -51,6 +51,7 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* part
             partials[(size_t)blockIdx.x * nv_stride + q] = s;
         }
     }
+    __syncthreads();   // sh is read by thread 0 above: a later call must not overwrite it first
 }
 
 // True in every thread of the last block to finish (after all partials are visible).
@@ -114,12 +115,27 @@ __global__ void k_bracket(const ReduceArgs a) {
         a.partials[4 * (size_t)blockIdx.x] = smn[0];
         a.partials[4 * (size_t)blockIdx.x + 1] = smx[0];
     }
-    if (last_block(a.ticket) && threadIdx.x == 0) {
-        double lo = 1e300, hi = -1e300;
-        for (int b = 0; b < gridDim.x; ++b) {
-            lo = fmin(lo, __ldcg(a.partials + 4 * (size_t)b));
-            hi = fmax(hi, __ldcg(a.partials + 4 * (size_t)b + 1));
+    if (!last_block(a.ticket)) return;
+    // the last block: the block extrema by all its threads (strided), then a tree
+    double lo = 1e300, hi = -1e300;
+    for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+        lo = fmin(lo, __ldcg(a.partials + 4 * (size_t)b));
+        hi = fmax(hi, __ldcg(a.partials + 4 * (size_t)b + 1));
+    }
+    __syncthreads();   // smn / smx are reused
+    smn[threadIdx.x] = lo;
+    smx[threadIdx.x] = hi;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            smn[threadIdx.x] = fmin(smn[threadIdx.x], smn[threadIdx.x + o]);
+            smx[threadIdx.x] = fmax(smx[threadIdx.x], smx[threadIdx.x + o]);
         }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        lo = smn[0];
+        hi = smx[0];
         BisectState* s = a.state;
         s->lo = lo - 40.0 * a.kT;
         s->hi = hi + 40.0 * a.kT;
@@ -153,11 +169,11 @@ __global__ void __launch_bounds__(kRedThreads) k_count(const ReduceArgs a, int m
     const size_t total = (size_t)a.M * a.nu_max;
     const size_t chunk = (total + gridDim.x - 1) / gridDim.x;
     const size_t b0 = min(total, (size_t)blockIdx.x * chunk), b1 = min(total, b0 + chunk);
-    const double inv_kT = 1.0 / a.kT;
+    const double inv_kT = a.inv_kT;
     const bool keep = mode == 2 && a.act && !s->have_pre && s->hi - s->lo < 10.0 * a.kT;
     if (mode == 2 && a.act && s->have_pre) {
         // the kept poles of this block; the block's constant part once, by thread 0
-        const double scale = exp((s->mu0 - x) * inv_kT);
+        const double scale = s->scale;   // exp((mu0 - x)/kT), set by the previous step
         const int n = a.act_n[blockIdx.x];
         const double2* q = a.act + b0;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -224,10 +240,20 @@ __global__ void __launch_bounds__(kRedThreads) k_count(const ReduceArgs a, int m
             if (threadIdx.x == 0) a.act_n[blockIdx.x] = kept;
         }
     }
-    block_reduce_store<3>(v, a.partials, 4);
+    // the bisection needs N only; mode 3 also E_band and Omega
+    if (mode == 3) block_reduce_store<3>(v, a.partials, 4);
+    else {
+        double n1[1] = {v[0]};
+        block_reduce_store<1>(n1, a.partials, 4);
+    }
     if (!last_block(a.ticket)) return;
-    double tot[3];
-    sum_partials<3>(a.partials, gridDim.x, tot);
+    double tot[3] = {0.0, 0.0, 0.0};
+    if (mode == 3) sum_partials<3>(a.partials, gridDim.x, tot);
+    else {
+        double t1[1];
+        sum_partials<1>(a.partials, gridDim.x, t1);
+        tot[0] = t1[0];
+    }
     if (threadIdx.x == 0) {
         const double N = tot[0], E = tot[1], Om = tot[2];
         if (mode == 0) s->n_lo = N;
@@ -247,6 +273,7 @@ __global__ void __launch_bounds__(kRedThreads) k_count(const ReduceArgs a, int m
             s->iter += 1;
             if (s->iter >= a.max_iter || !(s->hi - s->lo >= a.tol)) s->done = 1;
             s->mu = 0.5 * (s->lo + s->hi);
+            if (s->have_pre) s->scale = exp((s->mu0 - 0.5 * (s->lo + s->hi)) * inv_kT);
         } else {
             s->n_at = N;
             s->e_band = E;

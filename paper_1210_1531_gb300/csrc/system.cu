@@ -719,6 +719,7 @@ ReduceArgs reduce_args(elses_system s) {
     r.g = s->gg.p;
     r.nu_eff = s->nu_eff.p;
     r.kT = s->p.kT;
+    r.inv_kT = 1.0 / s->p.kT;
     r.n_electrons = s->p.n_electrons;
     r.tol = s->p.mu_tol;
     r.max_iter = s->p.max_bisect;
