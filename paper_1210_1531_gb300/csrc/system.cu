@@ -863,18 +863,37 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
                 s->cell_atoms.p, st);
     s->stats.launches += 4;
 
-    // neighbour pattern
+    // neighbour pattern and clusters: both lists counted (the cluster one beside the neighbour
+    // one on the second stream), one readback, then both filled side by side
     TRY(s->row_cnt.ensure(n));
     TRY(s->row_ptr.ensure(n + 1));
+    const bool clusters = p.r_cluster > 0;
+    if (clusters) {
+        TRY(s->cl_cnt.ensure(n));
+        TRY(s->cl_ptr.ensure(n + 1));
+    }
     count_lists(s->pos.p, n, g, s->cell_of.p, s->cell_start.p, s->cell_atoms.p, sk->r_cut,
                 s->row_cnt.p, s->counters.p + 0, st);
     scan_exclusive(s->row_cnt.p, s->row_ptr.p, n, st);
     s->stats.launches += 2;
+    if (clusters) {
+        TRY(fork_side(s, st));
+        count_lists(s->pos.p, n, g, s->cell_of.p, s->cell_start.p, s->cell_atoms.p, p.r_cluster,
+                    s->cl_cnt.p, s->counters.p + 1, s->side);
+        scan_exclusive(s->cl_cnt.p, s->cl_ptr.p, n, s->side);
+        TRY(join_side(s, st));
+        s->stats.launches += 2;
+    }
     int hc[2] = {0, 0};
-    CUDA_TRY(cudaMemcpyAsync(&hc[0], s->counters.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    std::vector<int> hp;
+    CUDA_TRY(cudaMemcpyAsync(hc, s->counters.p, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
     s->h_row_ptr.resize(n + 1);
     CUDA_TRY(cudaMemcpyAsync(s->h_row_ptr.data(), s->row_ptr.p, sizeof(int) * (n + 1),
                              cudaMemcpyDeviceToHost, st));
+    if (clusters) {
+        hp.resize(n + 1);
+        CUDA_TRY(cudaMemcpyAsync(hp.data(), s->cl_ptr.p, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, st));
+    }
     CUDA_TRY(cudaStreamSynchronize(st));
     s->max_nb = hc[0];
     s->nnzb = s->h_row_ptr[n];
@@ -883,35 +902,17 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
     TRY(s->col_idx.ensure(s->nnzb));
     TRY(s->row_of.ensure(s->nnzb));
     TRY(s->tmap.ensure(s->nnzb));
-    fill_lists(s->pos.p, n, g, s->cell_of.p, s->cell_start.p, s->cell_atoms.p, sk->r_cut,
-               s->row_ptr.p, s->col_idx.p, p.max_neighbors, s->counters.p + 2, st);
-    s->stats.launches++;
-
-    // clusters
-    if (p.r_cluster > 0) {
-        TRY(s->cl_cnt.ensure(n));
-        TRY(s->cl_ptr.ensure(n + 1));
-        count_lists(s->pos.p, n, g, s->cell_of.p, s->cell_start.p, s->cell_atoms.p, p.r_cluster,
-                    s->cl_cnt.p, s->counters.p + 1, st);
-        scan_exclusive(s->cl_cnt.p, s->cl_ptr.p, n, st);
-        s->stats.launches += 2;
-        int tot = 0;
-        CUDA_TRY(cudaMemcpyAsync(&hc[1], s->counters.p + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CUDA_TRY(cudaMemcpyAsync(&tot, s->cl_ptr.p + n, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CUDA_TRY(cudaStreamSynchronize(st));
+    if (clusters) {
         s->max_cl = hc[1];
-        s->cl_total = tot;
+        s->cl_total = hp[n];
         if (s->max_cl > p.max_cluster)
             return fail(ELSES_ERR_CAPACITY, "a cluster has %d atoms (max_cluster %d)", s->max_cl, p.max_cluster);
-        TRY(s->cl_idx.ensure(std::max(1, tot)));
-        {
-            std::vector<int> hp(n + 1);
-            CUDA_TRY(cudaMemcpy(hp.data(), s->cl_ptr.p, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost));
-            s->h_clsize.resize(n);
-            for (int i = 0; i < n; ++i) s->h_clsize[i] = hp[i + 1] - hp[i];
-        }
+        TRY(s->cl_idx.ensure(std::max(1, hp[n])));
+        s->h_clsize.resize(n);
+        for (int i = 0; i < n; ++i) s->h_clsize[i] = hp[i + 1] - hp[i];
+        TRY(fork_side(s, st));
         fill_lists(s->pos.p, n, g, s->cell_of.p, s->cell_start.p, s->cell_atoms.p, p.r_cluster,
-                   s->cl_ptr.p, s->cl_idx.p, p.max_cluster, s->counters.p + 2, st);
+                   s->cl_ptr.p, s->cl_idx.p, p.max_cluster, s->counters.p + 2, s->side);
         s->stats.launches++;
     } else {
         if (n > p.max_cluster)
@@ -920,6 +921,9 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
         s->cl_total = (long long)n * n;
         s->h_clsize.assign(n, n);
     }
+    fill_lists(s->pos.p, n, g, s->cell_of.p, s->cell_start.p, s->cell_atoms.p, sk->r_cut,
+               s->row_ptr.p, s->col_idx.p, p.max_neighbors, s->counters.p + 2, st);
+    s->stats.launches++;
 
     // Slater-Koster H and S
     TRY(s->H.ensure((size_t)s->nnzb * 16));
@@ -928,6 +932,7 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
     sk_build(s->pos.p, n, s->box, s->skd, s->row_ptr.p, s->col_idx.p, s->nnzb, s->row_of.p, s->tmap.p,
              s->H.p, s->S.p, s->skr.p, st);
     s->stats.launches += 2;
+    if (clusters) TRY(join_side(s, st));   // the cluster lists
     TRY(check_status(s, st));
     TRY(prepare_columns(s));
     if (s->p.autotune && s->tuned_bps.empty() && s->p.k3_ctas_per_sm <= 0) TRY(autotune_impl(s, st));

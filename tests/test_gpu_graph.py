@@ -24,8 +24,9 @@ def _same(ra, rb, f_rel=0.0):
             and np.abs(Fa - Fb).max() <= f_rel * np.abs(Fa).max())
 
 
-@pytest.mark.parametrize("kw", [{}, {"two_pass": True}, {"exact_forces": True}, {"schedule": 1}],
-                         ids=["stored", "two_pass", "exact_forces", "batched"])
+@pytest.mark.parametrize("kw", [{}, {"two_pass": True}, {"exact_forces": True}, {"schedule": 1},
+                                {"krylov_block": True}, {"batch_atoms": 16}],
+                         ids=["stored", "two_pass", "exact_forces", "batched", "block", "batches"])
 def test_replay_equals_eager(eg, kw):
     w = wl.make("diamond_64")
     a = eg.system_for(w, **kw)
