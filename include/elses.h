@@ -144,12 +144,16 @@ int elses_set_hs(elses_system sys, const double* H_dev, const double* S_dev, voi
  * system (clusters of up to 32 s atoms in s slots; one CTA per atom, persistent), run = 1 times
  * the kernel at every count of resident CTAs per SM that fits -- fewer CTAs keep more of their
  * Krylov bases in L2, more hide more latency -- on a sample of the class's own atoms (up to two
- * full waves, in launch order), and keeps the fastest per atom for the later calls of this
- * system and its rebuilds. The timed launches use the column buffers, so columns computed before
- * are invalidated; the results of later calls do not depend on the shape (bit for bit). run = 0
- * only reports the shapes in use. classes_out: optional host int[2 * max_classes], pairs (slots
- * s, CTAs per SM), largest class first; n_host: the number of classes. ERR_STATE for run = 1
- * when params.k3_ctas_per_sm fixes the shape. Passage: none (a launch-shape choice). */
+ * full waves, in launch order), and keeps the fastest per atom. With the work queue
+ * (schedule = 1) and at least four atoms per CTA it then times the whole class in both orders
+ * of its atoms, decreasing cluster size (a short tail) and atom order (neighbouring clusters in
+ * flight together share H and S in L2), and keeps the faster. The choices hold for the later
+ * calls of this system and its rebuilds. The timed launches use the column buffers, so columns
+ * computed before are invalidated; the results of later calls do not depend on the shape or
+ * the order (bit for bit). run = 0 only reports the shapes in use. classes_out: optional host
+ * int[3 * max_classes], triples (slots s, CTAs per SM, queue order: 0 static, 1 by size, 2 by
+ * atom), largest class first; n_host: the number of classes. ERR_STATE for run = 1 when
+ * params.k3_ctas_per_sm fixes the shape. Passage: none (a launch-shape choice). */
 int elses_autotune(elses_system sys, int run, int max_classes, int* classes_out, int* n_host,
                    void* stream);
 

@@ -203,18 +203,20 @@ class System:
 
     def autotune(self, stream=None):
         """elses_autotune: the Krylov launch shape timed per cluster size class. Returns
-        {cluster slots of 32 atoms: resident CTAs per SM chosen}."""
+        {cluster slots of 32 atoms: (resident CTAs per SM, queue order)}, the order "static"
+        (plain schedule), "size" or "atom"."""
         return self._shapes(1, stream)
 
     def autotune_shapes(self, stream=None):
-        """The Krylov launch shapes in use: {cluster slots of 32 atoms: CTAs per SM}."""
+        """The Krylov launch shapes in use, as autotune() returns them."""
         return self._shapes(0, stream)
 
     def _shapes(self, run, stream):
-        out = (ctypes.c_int * 32)()
+        out = (ctypes.c_int * 48)()
         n = ctypes.c_int(0)
         _check(self._L.elses_autotune(self._h, run, 16, out, ctypes.byref(n), _stream(stream)))
-        return {out[2 * i]: out[2 * i + 1] for i in range(min(n.value, 16))}
+        names = {0: "static", 1: "size", 2: "atom"}
+        return {out[3 * i]: (out[3 * i + 1], names.get(out[3 * i + 2], "?")) for i in range(min(n.value, 16))}
 
     # ------------------------------------------------------------------ a3-a10
     def green_columns(self, col_begin=0, col_end=None, z=None, stream=None):

@@ -16,8 +16,10 @@
 //                  bulge chase) -- the sequential part; the rotations are recorded.
 //   k_eig_spectra  one thread per (column, vector): the rotations replayed on y give
 //                  c, d, g = Q^T z.
-//   k_eig_vectors  one warp per column, only where V itself is needed (G(z), the adjoint): Q_H
-//                  from the reflectors, the rotations applied to its columns, V = L^-T Q.
+//   k_eig_vectors  one warp per column, only where V itself is needed (G(z), the adjoint, or
+//                  batches that overwrite the factors): Q_H from the reflectors, the rotations
+//                  applied to its columns, V = L^-T Q; when V is formed with the columns, the
+//                  spectra c, d, g = Q^T z too (instead of k_eig_spectra).
 //   k_eig_weights  one thread per (column, vector): the density needs V only applied to two
 //                  vectors, t = V w = L^-T Q_H (R_1^T .. R_n^T w), taken from the factors.
 #include "internal.h"
@@ -372,7 +374,10 @@ __global__ void __launch_bounds__(kSpecThreads) k_eig_spectra(const EigArgs a) {
 }
 
 // ----------------------------------------------------------------------------- k_eig_vectors
-__global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a) {
+// spectra: also write c, d, g = Q^T z in pole order (the batches that form V get them here instead
+// of from k_eig_spectra): z = Q_H y is taken with Q_H once it is accumulated, and after the
+// rotations Q^T z = R_n .. R_1 y.
+__global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a, bool spectra) {
     extern __shared__ __align__(16) double sm[];
     const int lane = threadIdx.x;
     const int c = blockIdx.x;
@@ -384,6 +389,7 @@ __global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a) {
     double* L = R + nm * ld;
     double* Q = L + nm * ld;
     double* inv = Q + nm * ld;
+    double* zs = inv + nm;          // [3][nm]: z = Q_H y (spectra only)
     const double* F = a.fac + (size_t)c * eig_fac_doubles(nm);
     for (int q = lane; q < nu * nu; q += 32) {
         const int i = q / nu, k = q % nu;
@@ -402,6 +408,22 @@ __global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a) {
             for (int i = k + 1; i < nu; ++i) t = fma(R[i * ld + k], Q[i * ld + n], t);
             t *= tau;
             for (int i = k + 1; i < nu; ++i) Q[i * ld + n] = fma(-t, R[i * ld + k], Q[i * ld + n]);
+        }
+        __syncwarp();
+    }
+    if (spectra) {   // z = Q_H y (lanes over rows)
+        const double* y = a.tri + (size_t)c * eig_tri_doubles(nm) + 2 * nm;
+        for (int i = lane; i < nu; i += 32) {
+            double z0 = 0.0, z1 = 0.0, z2 = 0.0;
+            for (int k = 0; k < nu; ++k) {
+                const double q = Q[i * ld + k];
+                z0 = fma(q, y[k], z0);
+                z1 = fma(q, y[nm + k], z1);
+                z2 = fma(q, y[2 * nm + k], z2);
+            }
+            zs[i] = z0;
+            zs[nm + i] = z1;
+            zs[2 * nm + i] = z2;
         }
         __syncwarp();
     }
@@ -431,6 +453,24 @@ __global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a) {
             }
         }
         __syncwarp();
+    }
+    if (spectra) {   // c, d, g = Q^T z in ascending order of the poles (lanes over poles)
+        const int* pm = a.perm + (size_t)c * nm;
+        for (int k = lane; k < nm; k += 32) {
+            double sc = 0.0, sd = 0.0, sg = 0.0;
+            if (k < nu) {
+                const int p = pm[k];
+                for (int n = 0; n < nu; ++n) {
+                    const double q = Q[n * ld + p];
+                    sc = fma(q, zs[n], sc);
+                    sd = fma(q, zs[nm + n], sd);
+                    sg = fma(q, zs[2 * nm + n], sg);
+                }
+            }
+            a.c[(size_t)j * nm + k] = sc;
+            a.d[(size_t)j * nm + k] = sd;
+            a.g[(size_t)j * nm + k] = sg;
+        }
     }
     // V = L^-T Q in place (lanes over columns m, rows bottom-up)
     for (int m = lane; m < nu; m += 32)
@@ -521,7 +561,7 @@ __global__ void __launch_bounds__(kWtThreads) k_eig_weights(const EigArgs a, dou
 size_t eig_smem_reduce(int nm) {
     return sizeof(double) * 2 * ((2 * (size_t)nm + 3) * (nm + 1) + 2 * (size_t)nm + 3);
 }
-size_t eig_smem_vectors(int nm) { return sizeof(double) * (3 * (size_t)nm * (nm + 1) + (size_t)nm); }
+size_t eig_smem_vectors(int nm) { return sizeof(double) * (3 * (size_t)nm * (nm + 1) + 4 * (size_t)nm); }
 size_t eig_smem_threads(int nm, int arrays) { return sizeof(double) * arrays * (size_t)nm * kChaseThreads; }
 int eig_thread_grid(int ncols) { return (ncols + kChaseThreads - 1) / kChaseThreads; }
 
@@ -533,17 +573,22 @@ void projected_eig(const EigArgs& a, cudaStream_t st, bool form_v) {
     smem_at_least(k_eig_chase, s2);
     carveout_for(k_eig_chase, s2, eig_thread_grid(a.ncols));
     k_eig_chase<<<eig_thread_grid(a.ncols), kChaseThreads, s2, st>>>(a);
+    const size_t sv = eig_smem_vectors(a.nu_max);
+    smem_at_least(k_eig_vectors, sv);
+    if (form_v) {   // V and the spectra in one kernel
+        k_eig_vectors<<<a.ncols, 32, sv, st>>>(a, true);
+        return;
+    }
     const size_t s3 = sizeof(double) * (size_t)a.nu_max * kSpecThreads;
     smem_at_least(k_eig_spectra, s3);
     carveout_for(k_eig_spectra, s3, (a.ncols + 31) / 32);
     k_eig_spectra<<<(a.ncols + 31) / 32, kSpecThreads, s3, st>>>(a);
-    if (form_v) eig_vectors(a, st);
 }
 
-void eig_vectors(const EigArgs& a, cudaStream_t st) {
+void eig_vectors(const EigArgs& a, cudaStream_t st) {   // the spectra in use are kept
     const size_t s = eig_smem_vectors(a.nu_max);
     smem_at_least(k_eig_vectors, s);
-    k_eig_vectors<<<a.ncols, 32, s, st>>>(a);
+    k_eig_vectors<<<a.ncols, 32, s, st>>>(a, false);
 }
 
 void eig_density_weights(const EigArgs& a, double mu, const double* mu_dev, double kT, double* T, cudaStream_t st) {

@@ -113,6 +113,7 @@ struct elses_system_s {
 
     int nu_max = 0, na_max = 0, k3_grid = 0, batch_atoms = 0, deg_cap = 0, k3_bps = 0;
     std::vector<int> tuned_bps;            // autotuner: resident Krylov CTAs per SM by cluster slots
+    std::vector<int> tuned_order;          // autotuner: work-queue order by cluster slots (1 size, 2 atom)
     // Krylov launches: per batch of atoms, one launch per cluster size class (slots of 32 atoms),
     // each with its own shared-memory footprint and resident-CTA count
     // scratch_off: where the launch's per-CTA scratch starts, so that the class launches of one
@@ -304,7 +305,8 @@ int prepare_columns(elses_system s) {
                 if ((s->h_clsize[a] + 31) / 32 == ns) ord.push_back(a);
             const int count = (int)ord.size() - begin;
             if (count == 0) continue;
-            if (s->p.schedule == 1)
+            const bool by_atom = ns < (int)s->tuned_order.size() && s->tuned_order[ns] == 2;
+            if (s->p.schedule == 1 && !by_atom)
                 std::stable_sort(ord.begin() + begin, ord.end(),
                                  [&](int x, int y) { return s->h_clsize[x] > s->h_clsize[y]; });
             const int na = 32 * ns;
@@ -543,7 +545,7 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
     s->tic(T_EIG, st);
     projected_eig(ea, st, form_v);
     s->toc(st);
-    s->stats.launches += form_v ? 4 : 3;
+    s->stats.launches += 3;
     if (stored && !form_v) s->v_lazy = true;
     s->stats.columns += 4LL * (e - b);
     *V_out = ea.V;
@@ -644,11 +646,15 @@ int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* 
 
 // The autotuner: per size class of the first batch, the Krylov kernel timed at every resident
 // CTA count that fits, on the class's first atoms in launch order (up to two full waves at the
-// largest count); the fastest per atom is kept in tuned_bps and the launches are planned again.
+// largest count); the fastest per atom is kept in tuned_bps. With the work queue, the whole
+// class is then timed in both orders of its atoms -- decreasing cluster size (short tail) and
+// atom order (neighbouring clusters in flight together share H and S in L2) -- and the faster
+// is kept in tuned_order. The launches are planned again.
 int autotune_impl(elses_system s, cudaStream_t st) {
     const int nm = s->nu_max;
     const int kdeg = s->user_hs ? s->max_nb : s->deg_cap;
     s->tuned_bps.assign(s->na_max / 32 + 1, 0);
+    s->tuned_order.assign(s->na_max / 32 + 1, 0);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
@@ -694,10 +700,47 @@ int autotune_impl(elses_system s, cudaStream_t st) {
             if (b == 1 || per_atom < best) { best = per_atom; best_b = b; }
         }
         if (!rc) s->tuned_bps[ns] = best_b;
+        if (rc || s->p.schedule != 1 || L.item_count < 4 * s->num_sms * best_b) continue;
+        // queue order of the whole class: as planned (decreasing cluster size), then atom order
+        std::vector<int> seg(L.item_count);
+        if (cudaMemcpy(seg.data(), s->order.p + L.item_begin, sizeof(int) * L.item_count,
+                       cudaMemcpyDeviceToHost) != cudaSuccess) { rc = fail(ELSES_ERR_CUDA, "order readback"); break; }
+        std::vector<int> atom_order = seg;
+        std::sort(atom_order.begin(), atom_order.end());
+        float t_order[2] = {0.f, 0.f};
+        for (int o = 0; o < 2 && !rc; ++o) {
+            const std::vector<int>& ord = o == 0 ? seg : atom_order;
+            if (cudaMemcpyAsync(s->order.p + L.item_begin, ord.data(), sizeof(int) * L.item_count,
+                                cudaMemcpyHostToDevice, st) != cudaSuccess) { rc = fail(ELSES_ERR_CUDA, "order upload"); break; }
+            KrylovArgs ka = krylov_args(s, L.batch_begin, L.batch_end);
+            ka.UP = nullptr;
+            ka.flops = nullptr;
+            ka.na_max = L.na;
+            ka.order = s->order.p + L.item_begin;
+            ka.n_items = L.item_count;
+            ka.scratch = s->kscratch.p;
+            ka.queue = s->counters.p + kQueue0;
+            const int grid = std::min(L.item_count, s->num_sms * best_b);
+            for (int rep = 0; rep < 2; ++rep) {
+                cudaMemsetAsync(ka.queue, 0, sizeof(int), st);
+                cudaEventRecord(e0, st);
+                if (s->p.krylov_block) block_krylov_columns(ka, grid, st);
+                else krylov_columns(ka, grid, st);
+                cudaEventRecord(e1, st);
+                s->stats.launches++;
+            }
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t_order[o], e0, e1) != cudaSuccess)
+                rc = fail(ELSES_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(cudaGetLastError()));
+        }
+        if (!rc) s->tuned_order[ns] = t_order[1] < t_order[0] ? 2 : 1;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc) { s->tuned_bps.clear(); return rc; }
+    if (rc) {
+        s->tuned_bps.clear();
+        s->tuned_order.clear();
+        return rc;
+    }
     TRY(clear_status(s, st));        // the sampled columns may have flagged a breakdown
     CUDA_TRY(cudaStreamSynchronize(st));
     return prepare_columns(s);       // launch plan with the chosen shapes; columns invalidated
@@ -1308,8 +1351,11 @@ int elses_autotune(elses_system s, int run, int max_classes, int* classes_out, i
     for (const auto& L : s->k3_launches) {   // the classes of the first batch, largest first
         if (L.batch_begin != 0) continue;
         if (n < max_classes) {
-            classes_out[2 * n] = L.na / 32;
-            classes_out[2 * n + 1] = L.bps;
+            const int ns = L.na / 32;
+            const bool by_atom = ns < (int)s->tuned_order.size() && s->tuned_order[ns] == 2;
+            classes_out[3 * n] = ns;
+            classes_out[3 * n + 1] = L.bps;
+            classes_out[3 * n + 2] = s->p.schedule != 1 ? 0 : by_atom ? 2 : 1;
         }
         ++n;
     }

@@ -21,9 +21,10 @@ def test_autotuned_shape_keeps_results_bit_for_bit(eg):
     F = gu.to_np(F)
     shapes = s.autotune()
     assert len(shapes) >= 1
-    for slots, bps in shapes.items():
-        assert 1 <= slots <= 16 and 1 <= bps <= 8
-    assert s.stats()["k3_ctas_per_sm"] in shapes.values()
+    for slots, (bps, order) in shapes.items():
+        assert 1 <= slots <= 16 and 1 <= bps <= 8 and order in ("size", "atom")
+    assert s.stats()["k3_ctas_per_sm"] in [b for b, _ in shapes.values()]
+    assert s.autotune_shapes() == shapes
     mu2, e_band2, _, F2 = s.energy_force()               # columns recomputed with the new shape
     assert mu2 == mu and e_band2 == e_band and np.array_equal(gu.to_np(F2), F)
 

@@ -60,9 +60,18 @@ def test_cohp_two_pass_equals_stored(eg, d64):
 
 def test_lazy_V_survives_a_partial_recompute(eg, d64):
     """After the energy pass V is left unformed; recomputing a few columns first forms V of the
-    others from the kept factors, so the spectra on the pattern are unchanged."""
+    others from the kept factors, so the spectra on the pattern are unchanged (the recomputed
+    columns take their spectra as Q^T z with V: equal to rounding)."""
     s = eg.system_for(d64["w"])
     s.energy_force()
     assert s.green_columns(0, 8) == 0
     C, _, _, dos = s.cohp_spectrum(ZS, sigma_pi=False)
+    assert np.abs(gu.to_np(C) - d64["C"]).max() <= 1e-13 * np.abs(d64["C"]).max()
+    assert np.abs(dos - d64["dos"]).max() <= 1e-13 * np.abs(d64["dos"]).max()
+
+
+def test_spectra_are_reproducible(eg, d64):
+    """The DOS and the COHP spectrum are fixed-order reductions: a repeat is bit for bit."""
+    C, Cs, Cp, dos = d64["sys"].cohp_spectrum(ZS)
     assert np.array_equal(gu.to_np(C), d64["C"]) and np.array_equal(dos, d64["dos"])
+    assert np.array_equal(gu.to_np(Cs), d64["Cs"]) and np.array_equal(gu.to_np(Cp), d64["Cp"])
