@@ -313,7 +313,7 @@ def run_ours(args):
             "config": bench_config(args, w, world),
             "plain": {"ms_per_step": plain_ms, "value": M / (plain_ms * 1e-3), "unit": "columns/s"},
             "exact_forces": exact,
-            "autotuned_shapes": {f"{32 * k}-atom clusters": f"{b} CTAs/SM, queue by {o}"
+            "autotuned_shapes": {f"{k}-atom clusters": f"{b} CTAs/SM, queue by {o}"
                                  for k, (b, o) in tuned.items()},
             "phases_ms_per_step": {k: stats[k] / args.steps for k in
                                    ("t_krylov_ms", "t_eig_ms", "t_bisect_ms", "t_density_ms", "t_force_ms")},

@@ -100,6 +100,11 @@ typedef struct elses_params {
                                density, scalars, forces at the device-resident mu), later calls
                                replay it with one host synchronisation; a rebuild that keeps the
                                plan and buffers keeps the graph. Results equal the eager path.   */
+    int    k3_lanes;        /* lanes per column of the Krylov kernel: 0 = automatic (a half-warp
+                               per column, two columns per warp, for the size classes whose
+                               clusters would leave the last slot of 32 atoms at most half full;
+                               forces from the density matrix and per-column spaces only),
+                               32 = one warp per column always                                   */
 } elses_params;
 
 /* Counters and event timings of the calls since the last build (timing = 1 for the times). */
@@ -141,7 +146,7 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
 int elses_set_hs(elses_system sys, const double* H_dev, const double* S_dev, void* stream);
 
 /* Autotuner of the Krylov kernel's launch shape (a3, a4). For each cluster size class of the
- * system (clusters of up to 32 s atoms in s slots; one CTA per atom, persistent), run = 1 times
+ * system (clusters up to its capacity in atoms; one CTA per atom, persistent), run = 1 times
  * the kernel at every count of resident CTAs per SM that fits -- fewer CTAs keep more of their
  * Krylov bases in L2, more hide more latency -- on a sample of the class's own atoms (up to two
  * full waves, in launch order), and keeps the fastest per atom. With the work queue
@@ -151,8 +156,8 @@ int elses_set_hs(elses_system sys, const double* H_dev, const double* S_dev, voi
  * calls of this system and its rebuilds. The timed launches use the column buffers, so columns
  * computed before are invalidated; the results of later calls do not depend on the shape or
  * the order (bit for bit). run = 0 only reports the shapes in use. classes_out: optional host
- * int[3 * max_classes], triples (slots s, CTAs per SM, queue order: 0 static, 1 by size, 2 by
- * atom), largest class first; n_host: the number of classes. ERR_STATE for run = 1 when
+ * int[3 * max_classes], triples (cluster capacity of the class in atoms, CTAs per SM,
+ * queue order: 0 static, 1 by size, 2 by atom), largest class first; n_host: the number of classes. ERR_STATE for run = 1 when
  * params.k3_ctas_per_sm fixes the shape. Passage: none (a launch-shape choice). */
 int elses_autotune(elses_system sys, int run, int max_classes, int* classes_out, int* n_host,
                    void* stream);

@@ -49,7 +49,8 @@ class Params(ctypes.Structure):
                 ("max_neighbors", ctypes.c_int), ("max_cluster", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("timing", ctypes.c_int), ("k3_ctas_per_sm", ctypes.c_int),
                 ("force_mode", ctypes.c_int), ("krylov_block", ctypes.c_int),
-                ("batch_atoms", ctypes.c_int), ("autotune", ctypes.c_int), ("graph", ctypes.c_int)]
+                ("batch_atoms", ctypes.c_int), ("autotune", ctypes.c_int), ("graph", ctypes.c_int),
+                ("k3_lanes", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -149,7 +150,7 @@ def make_sk(p) -> SK:
 def make_params(r_cluster, nu, kT, n_electrons, two_pass=False, nu_classes=(), schedule=0,
                 max_neighbors=0, max_cluster=0, breakdown_tol=0.0, mu_tol=0.0,
                 max_bisect=0, timing=False, k3_ctas_per_sm=0, exact_forces=False,
-                krylov_block=False, batch_atoms=0, autotune=False, graph=False) -> Params:
+                krylov_block=False, batch_atoms=0, autotune=False, graph=False, k3_lanes=0) -> Params:
     p = Params()
     p.r_cluster, p.kT, p.n_electrons = float(r_cluster), float(kT), float(n_electrons)
     p.breakdown_tol, p.mu_tol = float(breakdown_tol), float(mu_tol)
@@ -166,6 +167,7 @@ def make_params(r_cluster, nu, kT, n_electrons, two_pass=False, nu_classes=(), s
     p.batch_atoms = int(batch_atoms)
     p.autotune = 1 if autotune else 0
     p.graph = 1 if graph else 0
+    p.k3_lanes = int(k3_lanes)
     return p
 
 
@@ -175,7 +177,7 @@ class System:
     def __init__(self, pos, box, sk, r_cluster, nu, kT, n_electrons, two_pass=False,
                  nu_classes=(), schedule=0, max_neighbors=0, max_cluster=0, timing=False,
                  k3_ctas_per_sm=0, exact_forces=False, krylov_block=False, batch_atoms=0,
-                 autotune=False, graph=False, stream=None):
+                 autotune=False, graph=False, k3_lanes=0, stream=None):
         self._L = load_library()
         self._h = ctypes.c_void_p(None)
         self.n = int(pos.shape[0])
@@ -185,7 +187,7 @@ class System:
                                   max_neighbors, max_cluster, timing=timing,
                                   k3_ctas_per_sm=k3_ctas_per_sm, exact_forces=exact_forces,
                                   krylov_block=krylov_block, batch_atoms=batch_atoms,
-                                  autotune=autotune, graph=graph)
+                                  autotune=autotune, graph=graph, k3_lanes=k3_lanes)
         self.box = (ctypes.c_double * 3)(*[float(b) for b in box])
         self.rebuild(pos, stream)
 
@@ -203,7 +205,7 @@ class System:
 
     def autotune(self, stream=None):
         """elses_autotune: the Krylov launch shape timed per cluster size class. Returns
-        {cluster slots of 32 atoms: (resident CTAs per SM, queue order)}, the order "static"
+        {class capacity in atoms: (resident CTAs per SM, queue order)}, the order "static"
         (plain schedule), "size" or "atom"."""
         return self._shapes(1, stream)
 

@@ -65,7 +65,8 @@ struct KrylovArgs {
     int class_nu[4];
     double breakdown_tol;
     int onsite_diag;        // 1: on-site S blocks are I and on-site H blocks diagonal
-    int na_max;             // cluster capacity rounded up to a multiple of 32
+    int na_max;             // cluster capacity: a multiple of 32 (of 16 with half)
+    int half;               // 1: two columns per warp, one per half-warp (k_krylov_half)
     int deg_max;            // maximum pattern row length
     double* scratch;        // per resident CTA: 4 warps x (U, SU) x nu_max x na_max x 4
     double* Hp;             // [col][nu_max*(nu_max+1)/2] packed upper, batch-local col
@@ -105,6 +106,7 @@ struct AdjointArgs {
 };
 size_t krylov_smem_bytes(int na_max, int deg_max);
 int krylov_blocks_per_sm(int na_max, int deg_max);
+int krylov_half_blocks_per_sm(int na_max, int deg_max);
 size_t block_krylov_scratch_doubles(int nu_max, int na_max);
 int block_krylov_blocks_per_sm(int na_max, int deg_max);
 void block_krylov_columns(const KrylovArgs& a, int grid, cudaStream_t st);

@@ -126,6 +126,89 @@ __global__ void __launch_bounds__(kThreads, 3) k_krylov(const KrylovArgs a) {
     }
 }
 
+// The same recursion with two columns per warp, one per half-warp (W = 16; the module header of
+// krylov.cuh): a CTA of 2 warps per atom J, column alpha = threadIdx.x / 16, for clusters whose
+// last slot of 32 atoms would be at most half full (na_max a multiple of 16). Without kept bases.
+constexpr int kHalfThreads = 16 * kWarpsPerAtom;
+__global__ void __launch_bounds__(kHalfThreads, 6) k_krylov_half(const KrylovArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int NA = a.na_max;
+    double* vec = reinterpret_cast<double*>(smem_raw);
+    double* hbuf = vec + (size_t)kWarpsPerAtom * 2 * NA * 4;
+    ClusterView v;
+    carve_view(reinterpret_cast<unsigned char*>(hbuf + kWarpsPerAtom * kMaxNu), NA, a.deg_max, v);
+    __shared__ int sh_atom;
+
+    const int tid = threadIdx.x, lane = tid & 15, alpha = tid >> 4;
+    const unsigned gm = group_mask<16>();
+    const size_t col_scratch = (size_t)2 * a.nu_max * NA * 4;
+    double* Uw = a.scratch + (size_t)blockIdx.x * kWarpsPerAtom * col_scratch + (size_t)alpha * col_scratch;
+    double* SUw = Uw + (size_t)a.nu_max * NA * 4;
+    const int n_batch = a.n_items;
+
+    for (int iter = 0;; ++iter) {
+        if (tid == 0) {
+            const int idx = a.queue ? atomicAdd(a.queue, 1) : blockIdx.x + iter * gridDim.x;
+            int atom = -1;
+            if (idx < n_batch) atom = a.order[idx];
+            sh_atom = atom;
+        }
+        __syncthreads();
+        const int J = sh_atom;
+        if (J < 0) break;
+        if (!cluster_view_w<16, kHalfThreads>(a, J, NA, v)) {
+            if (tid == 0) flag(a.status, DEV_CAPACITY);
+            __syncthreads();
+            continue;
+        }
+        do {
+            const int j = 4 * J + alpha;
+            const int n_at = v.n_at, NP = v.NS * 16;
+            double* A = vec + (size_t)(alpha * 2) * NA * 4;
+            double* B = A + (size_t)NA * 4;
+            int nu = 0, jp = 0;
+            const int nu_eff = column_forward_w<false, 16>(a, v, J, alpha, A, B, hbuf + alpha * kMaxNu, Uw, SUw,
+                                                         nullptr, nullptr, nu, jp);
+            if (nu_eff <= 0) break;
+            if (lane == 0) {
+                a.nu_eff[j] = nu_eff;
+                if (nu_eff < nu) flag(a.status, DEV_BREAKDOWN);
+                if (a.flops) {   // the same algorithmic count as k_krylov
+                    const bool onsite = a.onsite_diag != 0;
+                    const unsigned long long nent = (unsigned long long)v.nent;
+                    const unsigned long long nc = 4ull * n_at, vv = (unsigned long long)nu_eff;
+                    const unsigned long long per = a.skr ? 24ull : 32ull;
+                    const unsigned long long spm = onsite ? vv * (2ull * per * nent + 4ull * n_at) : vv * 2ull * per * nent;
+                    const unsigned long long tri = vv * (vv + 1) / 2;
+                    const unsigned long long trim = vv > 0 ? (vv - 1) * vv / 2 : 0;
+                    const unsigned long long dense = nc * (6 * tri + 2 * vv) + (vv > 0 ? nc * (6 * trim + 4 * (vv - 1)) : 0);
+                    atomicAdd(a.flops, spm + dense);
+                }
+            }
+            __syncwarp(gm);
+            if (a.UP) {
+                const int e0 = a.row_ptr[J], ne = a.row_ptr[J + 1] - e0;
+                for (int q = lane; q < ne * 4; q += 16) {
+                    const int e = e0 + (q >> 2), r = q & 3;
+                    const int b = bsearch_sorted(v.cl, n_at, a.col_idx[e]);
+                    const int p = v.pos_of[b];
+                    double* out = a.UP + ((size_t)((e - a.up_block0) * 4 + alpha) * 4 + r) * a.nu_max;
+                    for (int k = 0; k < nu_eff; ++k) out[k] = Uw[4 * ((size_t)k * NP + p) + r];
+                }
+            }
+        } while (0);
+        __syncthreads();
+    }
+}
+
+int krylov_half_blocks_per_sm(int na_max, int deg_max) {
+    const size_t smem = krylov_smem_bytes(na_max, deg_max);
+    smem_at_least(k_krylov_half, smem);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_krylov_half, kHalfThreads, smem);
+    return nb;
+}
+
 int krylov_blocks_per_sm(int na_max, int deg_max) {
     const size_t smem = krylov_smem_bytes(na_max, deg_max);
     smem_at_least(k_krylov<false>, smem);
@@ -136,7 +219,10 @@ int krylov_blocks_per_sm(int na_max, int deg_max) {
 
 void krylov_columns(const KrylovArgs& a, int grid, cudaStream_t st) {
     const size_t smem = krylov_smem_bytes(a.na_max, a.deg_max);
-    if (a.bstore) {
+    if (a.half && !a.bstore) {
+        smem_at_least(k_krylov_half, smem);
+        k_krylov_half<<<grid, kHalfThreads, smem, st>>>(a);
+    } else if (a.bstore) {
         smem_at_least(k_krylov<true>, smem);
         k_krylov<true><<<grid, kThreads, smem, st>>>(a);
     } else {

@@ -6,7 +6,8 @@
 // are sorted by in-cluster degree and assigned to lanes in snake order over slots of 32, so that
 // lane work is balanced; each lane owns whole atoms (4 rows). A vector of the cluster is held
 // in "position" order: position p = slot * 32 + lane, orbital r at 4 p + r. The bases live in
-// global scratch as [k][position][orbital] (coalesced 32-byte rows per lane).
+// global scratch as [k][position][orbital] (coalesced 32-byte rows per lane). The forms ending in
+// _w at the end of the file do the same for groups of W lanes per column.
 #pragma once
 
 #include "internal.h"
@@ -483,6 +484,420 @@ __device__ __forceinline__ int column_forward(const KrylovArgs& a, const Cluster
             st4(SUn1 + 4 * p, v0, v1);
         }
         __syncwarp();
+    }
+    return nu_eff;
+}
+
+
+// ------------------------------------------------------------------------------------------------
+// The same building blocks for a group of W lanes per column (W = 16: two columns per warp, one
+// per half-warp; used by k_krylov_half). Shuffles and barriers take the group's own mask, so the
+// two halves of a warp are independent. Kept apart from the one-warp forms above so that those
+// compile exactly as before.
+// The lanes of the calling thread's group of W lanes (the warp, or its half).
+template <int W>
+__device__ __forceinline__ unsigned group_mask() {
+    return W == 32 ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
+}
+
+// Sum of 16 values held by every lane over the group (recursive halving on lane bits 3..0; for
+// W = 32 then one exchange across bit 4): lane l of the group ends with the sum of value l & 15.
+template <int W>
+__device__ __forceinline__ double warp_sum16_w(double (&v)[16]) {
+    const int lane = threadIdx.x & 31;
+    const unsigned m = group_mask<W>();
+#pragma unroll
+    for (int w = 8; w >= 1; w >>= 1) {
+        const bool upper = (lane & w) != 0;
+#pragma unroll
+        for (int i = 0; i < w; ++i) {
+            double send = upper ? v[i] : v[i + w];
+            double keep = upper ? v[i + w] : v[i];
+            v[i] = keep + __shfl_xor_sync(m, send, w);
+        }
+    }
+    if (W == 32) return v[0] + __shfl_xor_sync(m, v[0], 16);
+    return v[0];
+}
+
+// Sum of one value over the group.
+template <int W>
+__device__ __forceinline__ double group_sum(double v) {
+    const unsigned m = group_mask<W>();
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(m, v, o);
+    return v;
+}
+
+// y = A x on the cluster (lane-owned rows; x gathered from shared memory, y in shared or global
+// memory). Each lane walks one list holding the entries of all its rows in slot order
+// (entry.p4 low 16 bits: neighbour offset in x; high bits: the row's slot; `lane` is the lane
+// within the group of W, `ent` the [kmax][W] lists), so lanes stop after
+// their own entry count instead of after the widest row of every slot. Rows start from the
+// on-site term: the diagonal of the on-site block of `dvals` (block index eself[p]), the
+// identity when dvals is null, or zero when the on-site block is a list entry. With `skr` the
+// off-site blocks are applied in their two-centre form (13 FP64 instructions instead of 16;
+// which = 0 selects the H integrals, 1 the S integrals).
+template <int W>
+__device__ __forceinline__ void spmv_w(const double* __restrict__ vals, const double* __restrict__ skr,
+                                     int which, const Ent* __restrict__ ent, int kmax, int NS,
+                                     const double* x, double* y, int lane, bool onsite,
+                                     const double* __restrict__ dvals, const int* eself) {
+    for (int s = 0; s < NS; ++s) {
+        const int p = s * W + lane, po = 4 * p;
+        double2 o01 = make_double2(0.0, 0.0), o23 = make_double2(0.0, 0.0);
+        if (onsite) {
+            o01 = *reinterpret_cast<const double2*>(x + po);
+            o23 = *reinterpret_cast<const double2*>(x + po + 2);
+            const int es = eself[p];
+            if (dvals && es >= 0) {
+                const double* d = dvals + 16 * (size_t)es;
+                o01.x *= __ldg(d); o01.y *= __ldg(d + 5); o23.x *= __ldg(d + 10); o23.y *= __ldg(d + 15);
+            }
+        }
+        *reinterpret_cast<double2*>(y + po) = o01;
+        *reinterpret_cast<double2*>(y + po + 2) = o23;
+    }
+    int cur = -1;
+    double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
+    for (int k = 0; k < kmax; ++k) {
+        const Ent en = ent[W * k + lane];
+        if (en.blk >= 0) {
+            const int s = en.p4 >> 16, p4 = en.p4 & 0xffff;
+            if (s != cur) {
+                if (cur >= 0) {
+                    double2* yo = reinterpret_cast<double2*>(y + 4 * (cur * W + lane));
+                    yo[0] = make_double2(y0, y1);
+                    yo[1] = make_double2(y2, y3);
+                }
+                cur = s;
+                const double2* yi = reinterpret_cast<const double2*>(y + 4 * (s * W + lane));
+                const double2 i01 = yi[0], i23 = yi[1];
+                y0 = i01.x; y1 = i01.y; y2 = i23.x; y3 = i23.y;
+            }
+            const double2 x01 = *reinterpret_cast<const double2*>(x + p4);
+            const double2 x23 = *reinterpret_cast<const double2*>(x + p4 + 2);
+            if (skr) {
+                // two-centre block: t = u.x_p; y_s += V_ss x_s + V_sp t;
+                // y_p += V_pi x_p + (dV t - V_sp x_s) u,  dV = V_pp_sigma - V_pp_pi
+                const double2* q = reinterpret_cast<const double2*>(skr + 12 * (size_t)en.blk);
+                const double2 u01 = __ldg(q), u2_ = __ldg(q + 1);
+                const double2 v01 = __ldg(q + 2 + 2 * which), v23 = __ldg(q + 3 + 2 * which);
+                const double t = fma(u2_.x, x23.y, fma(u01.y, x23.x, u01.x * x01.y));
+                y0 = fma(v01.y, t, fma(v01.x, x01.x, y0));
+                const double aa = fma(v23.y, t, -v01.y * x01.x);
+                y1 = fma(aa, u01.x, fma(v23.x, x01.y, y1));
+                y2 = fma(aa, u01.y, fma(v23.x, x23.x, y2));
+                y3 = fma(aa, u2_.x, fma(v23.x, x23.y, y3));
+            } else {
+                const double2* b2 = reinterpret_cast<const double2*>(vals + 16 * (size_t)en.blk);
+                const double2 a0 = __ldg(b2 + 0), a1 = __ldg(b2 + 1), a2 = __ldg(b2 + 2), a3 = __ldg(b2 + 3);
+                const double2 a4 = __ldg(b2 + 4), a5 = __ldg(b2 + 5), a6 = __ldg(b2 + 6), a7 = __ldg(b2 + 7);
+                y0 = fma(a0.x, x01.x, fma(a0.y, x01.y, fma(a1.x, x23.x, fma(a1.y, x23.y, y0))));
+                y1 = fma(a2.x, x01.x, fma(a2.y, x01.y, fma(a3.x, x23.x, fma(a3.y, x23.y, y1))));
+                y2 = fma(a4.x, x01.x, fma(a4.y, x01.y, fma(a5.x, x23.x, fma(a5.y, x23.y, y2))));
+                y3 = fma(a6.x, x01.x, fma(a6.y, x01.y, fma(a7.x, x23.x, fma(a7.y, x23.y, y3))));
+            }
+        }
+    }
+    if (cur >= 0) {
+        double2* yo = reinterpret_cast<double2*>(y + 4 * (cur * W + lane));
+        yo[0] = make_double2(y0, y1);
+        yo[1] = make_double2(y2, y3);
+    }
+}
+
+// Builds the view of atom J's cluster (every thread of the CTA, T threads, calls it) for slots of
+// W lanes. Returns false, the same on every thread, when the cluster exceeds NA atoms or the
+// lists exceed their capacity.
+template <int W, int T>
+__device__ __forceinline__ bool cluster_view_w(const KrylovArgs& a, int J, int NA, ClusterView& v) {
+    __shared__ int sh_bad, sh_kmax, sh_nent;
+    const int tid = threadIdx.x;
+    const bool onsite = a.onsite_diag != 0;
+    Ent* ell = v.ell;
+    int* cl = v.cl;
+    int* deg = v.deg;
+    int* pos_of = v.pos_of;
+    int* atom_of_rank = v.atom_of_rank;
+    int* eoff = v.eoff;
+    int* eself = v.eself;
+    int n_at, cbase = 0;
+    if (a.cl_ptr) { cbase = a.cl_ptr[J]; n_at = a.cl_ptr[J + 1] - cbase; }
+    else n_at = a.n_atoms;
+    if (n_at > NA) return false;   // uniform across the CTA
+    for (int q = tid; q < n_at; q += T) cl[q] = a.cl_ptr ? a.cl_idx[cbase + q] : q;
+    __syncthreads();
+    for (int q = tid; q < n_at; q += T) {
+        const int A = cl[q];
+        int cnt = 0;
+        for (int e = a.row_ptr[A]; e < a.row_ptr[A + 1]; ++e) {
+            const int ce = a.col_idx[e];
+            cnt += (!onsite || ce != A) && bsearch_sorted(cl, n_at, ce) >= 0;
+        }
+        deg[q] = cnt;
+    }
+    __syncthreads();
+    const int NS = (n_at + W - 1) / W;
+    for (int q = tid; q < NS * W; q += T) {
+        int rank = q;   // ranks >= n_at are empty positions
+        if (q < n_at) {
+            const int dq = deg[q];
+            rank = 0;
+            for (int b = 0; b < n_at; ++b) {
+                const int db = deg[b];
+                rank += (db > dq) || (db == dq && b < q);
+            }
+        }
+        const int s = rank / W;
+        int l = rank % W;
+        if (s & 1) l = W - 1 - l;
+        if (q < n_at) pos_of[q] = s * W + l;
+        atom_of_rank[rank] = q < n_at ? q : -1 - (s * W + l);   // empty: encode its position
+    }
+    __syncthreads();
+    // per-lane lists: the entries of the lane's rows in slot order
+    if (tid < W) {
+        const unsigned m = W == 32 ? 0xffffffffu : 0xffffu;
+        int off = 0;
+        for (int sl = 0; sl < NS; ++sl) {
+            const int pp = sl * W + tid;
+            // rank of position pp (inverse of the snake map)
+            const int l = (sl & 1) ? W - 1 - tid : tid;
+            const int q = atom_of_rank[sl * W + l];
+            eoff[pp] = off;
+            off += q >= 0 ? deg[q] : 0;
+        }
+        int kmax = off, ntot = off;
+        for (int o = W / 2; o > 0; o >>= 1) {
+            kmax = max(kmax, __shfl_xor_sync(m, kmax, o));
+            ntot += __shfl_xor_sync(m, ntot, o);
+        }
+        if (tid == 0) {
+            sh_nent = ntot;
+            sh_kmax = kmax;
+            sh_bad = kmax * W > NA * a.deg_max;
+        }
+    }
+    __syncthreads();
+    if (sh_bad) return false;
+    const int kmax = sh_kmax;
+    for (int q = tid; q < kmax * W; q += T) ell[q] = Ent{0, -1};
+    __syncthreads();
+    for (int rank = tid; rank < NS * W; rank += T) {
+        const int q = atom_of_rank[rank];
+        const int p = q >= 0 ? pos_of[q] : -1 - q;
+        const int sl = p / W, l = p % W;
+        int k = eoff[p];
+        int es = -1;
+        if (q >= 0) {
+            const int A = cl[q];
+            for (int e = a.row_ptr[A]; e < a.row_ptr[A + 1]; ++e) {
+                const int ce = a.col_idx[e];
+                if (onsite && ce == A) {
+                    es = e;
+                    continue;
+                }
+                const int b = bsearch_sorted(cl, n_at, ce);
+                if (b >= 0) ell[W * (k++) + l] = Ent{(4 * pos_of[b]) | (sl << 16), e};
+            }
+        }
+        eself[p] = es;
+    }
+    __syncthreads();
+    v.n_at = n_at;
+    v.NS = NS;
+    v.kmax = kmax;
+    v.nent = sh_nent;
+    return true;
+}
+
+// Forward Krylov recursion of column j = 4 J + alpha by one warp (the reading of the module
+// header of krylov.cu): leaves U and SU in Uw, SUw ([k][position][orbital]) and writes H', S'
+// (packed upper) and row j of U, SU, HU of the column. With kAdj it also keeps HU in HUw and the
+// Gram-Schmidt coefficients in hess[n][k] (row stride nu_max): SU_k . HU_n for k <= n (the
+// first pass) and beta_n at k = n + 1, which the adjoint needs. A and B are the warp's two
+// shared vectors, h its coefficient buffer. Returns nu_eff (nu_out: the column's nu), or 0 for
+// bad input (flagged).
+template <bool kAdj, int W>
+__device__ __forceinline__ int column_forward_w(const KrylovArgs& a, const ClusterView& v, int J, int alpha,
+                                              double* A, double* B, double* h, double* Uw, double* SUw,
+                                              double* HUw, double* hess, int& nu_out, int& jp_out) {
+    const int lane = threadIdx.x & (W - 1);      // lane within the column's group
+    const unsigned gm = group_mask<W>();
+    const bool onsite = a.onsite_diag != 0;
+    const int n_at = v.n_at, NS = v.NS, kmax = v.kmax;
+    const int* cl = v.cl;
+    const int* pos_of = v.pos_of;
+    const Ent* ell = v.ell;
+    const int* eself = v.eself;
+    const int PK = a.nu_max * (a.nu_max + 1) / 2;
+    const int j = 4 * J + alpha;
+    const int col = j - 4 * a.atom_begin;
+    const int NP = NS * W;
+    const int nu = min(nu_for(a, n_at), a.nu_max);
+    nu_out = nu;
+    const int aJ = bsearch_sorted(cl, n_at, J);
+    int eJJ = -1;
+    for (int e = a.row_ptr[J]; e < a.row_ptr[J + 1]; ++e)
+        if (a.col_idx[e] == J) eJJ = e;
+    const double sjj = eJJ >= 0 ? a.S[16 * (size_t)eJJ + 5 * alpha] : -1.0;
+    if (aJ < 0 || !(sjj > 0.0)) {   // no diagonal block or S_jj <= 0: bad input
+        if (lane == 0) { flag(a.status, DEV_ARG); a.nu_eff[j] = 0; }
+        return 0;
+    }
+    const int jp = 4 * pos_of[aJ] + alpha;
+    jp_out = jp;
+    const size_t vs = (size_t)NP * 4;                    // one basis vector
+
+    for (int q = lane; q < NP * 4; q += W) A[q] = 0.0;
+    __syncwarp(gm);
+    if (lane == 0) A[jp] = 1.0 / sqrt(sjj);
+    __syncwarp(gm);
+    spmv_w<W>(a.S, a.skr, 1, ell, kmax, NS, A, SUw, lane, onsite, nullptr, eself);   // S u_1 -> SU[0]
+    for (int sl = 0; sl < NS; ++sl) {
+        const int p = sl * W + lane;
+        double2 x0, x1;
+        ld4(A + 4 * p, x0, x1);
+        st4(Uw + 4 * (size_t)p, x0, x1);
+    }
+    __syncwarp(gm);
+
+    int nu_eff = nu;
+    for (int n = 0; n < nu; ++n) {
+        double* SUn = SUw + (size_t)n * vs;
+        spmv_w<W>(a.H, a.skr, 0, ell, kmax, NS, A, B, lane, onsite, a.H, eself);
+        __syncwarp(gm);
+        if constexpr (kAdj) {
+            for (int sl = 0; sl < NS; ++sl) {
+                const int p = sl * W + lane;
+                double2 x0, x1;
+                ld4(B + 4 * p, x0, x1);
+                st4(HUw + (size_t)n * vs + 4 * p, x0, x1);
+            }
+        }
+        if (lane == 0) {
+            a.urow[(size_t)col * a.nu_max + n] = A[jp];
+            a.surow[(size_t)col * a.nu_max + n] = SUn[jp];
+            a.hurow[(size_t)col * a.nu_max + n] = B[jp];
+        }
+        // pass A: H'[k][n], S'[k][n] and the first CGS coefficients, k <= n, five k at a time
+        double hh = 0.0;
+        for (int k0 = 0; k0 <= n; k0 += 5) {
+            double acc[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+            for (int sl = 0; sl < NS; ++sl) {
+                const int p = sl * W + lane;
+                double2 hu0, hu1, su0, su1;
+                ld4(B + 4 * p, hu0, hu1);
+                ld4(SUn + 4 * p, su0, su1);
+                if (k0 == 0) acc[15] = fma4(hu0, hu1, hu0, hu1, acc[15]);
+#pragma unroll
+                for (int kk = 0; kk < 5; ++kk) {
+                    const int k = k0 + kk;
+                    if (k <= n) {
+                        double2 u0, u1, v0, v1;
+                        ld4(Uw + (size_t)k * vs + 4 * p, u0, u1);
+                        ld4(SUw + (size_t)k * vs + 4 * p, v0, v1);
+                        acc[kk] = fma4(u0, u1, hu0, hu1, acc[kk]);
+                        acc[5 + kk] = fma4(u0, u1, su0, su1, acc[5 + kk]);
+                        acc[10 + kk] = fma4(v0, v1, hu0, hu1, acc[10 + kk]);
+                    }
+                }
+            }
+            const double r = warp_sum16_w<W>(acc);
+            const int kk = lane % 5, kind = lane / 5, k = k0 + kk;
+            if (lane < 15 && k <= n) {
+                const size_t pk = (size_t)col * PK + k + (size_t)n * (n + 1) / 2;
+                if (kind == 0) a.Hp[pk] = r;
+                else if (kind == 1) a.Sp[pk] = r;
+                else {
+                    h[k] = r;
+                    if constexpr (kAdj) hess[(size_t)n * a.nu_max + k] = r;
+                }
+            }
+            if (k0 == 0) hh = __shfl_sync(gm, r, ((threadIdx.x & 31) & ~(W - 1)) + 15);
+        }
+        if (n == nu - 1) break;
+        __syncwarp(gm);
+        // sweep B: w = hu - U h (first pass) and the second-pass coefficients SU^T w,
+        // sixteen k at a time (the first sixteen in the same sweep as the update)
+        for (int k0 = 0; k0 <= n; k0 += 16) {
+            double acc2[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc2[q] = 0.0;
+            for (int sl = 0; sl < NS; ++sl) {
+                const int p = sl * W + lane;
+                double2 w0, w1;
+                ld4(B + 4 * p, w0, w1);
+                if (k0 == 0) {
+                    sub_basis(Uw, NP, p, h, n, w0, w1);
+                    st4(B + 4 * p, w0, w1);
+                }
+#pragma unroll
+                for (int kk = 0; kk < 16; ++kk) {
+                    if (k0 + kk <= n) {
+                        double2 v0, v1;
+                        ld4(SUw + (size_t)(k0 + kk) * vs + 4 * p, v0, v1);
+                        acc2[kk] = fma4(v0, v1, w0, w1, acc2[kk]);
+                    }
+                }
+            }
+            const double r2 = warp_sum16_w<W>(acc2);
+            // the first-pass coefficients were last read by the update of the first
+            // chunk, so the second-pass ones replace them in place
+            __syncwarp(gm);
+            if (lane < 16 && k0 + lane <= n) h[k0 + lane] = r2;
+            __syncwarp(gm);
+        }
+        // sweep C: w -= U h (second pass)
+        for (int sl = 0; sl < NS; ++sl) {
+            const int p = sl * W + lane;
+            double2 w0, w1;
+            ld4(B + 4 * p, w0, w1);
+            sub_basis(Uw, NP, p, h, n, w0, w1);
+            st4(B + 4 * p, w0, w1);
+        }
+        __syncwarp(gm);
+        // Sw (into the next SU slot) and beta
+        double* SUn1 = SUw + (size_t)(n + 1) * vs;
+        spmv_w<W>(a.S, a.skr, 1, ell, kmax, NS, B, SUn1, lane, onsite, nullptr, eself);
+        double part = 0.0;
+        for (int sl = 0; sl < NS; ++sl) {
+            const int p = sl * W + lane;
+            double2 w0, w1, v0, v1;
+            ld4(B + 4 * p, w0, w1);
+            ld4(SUn1 + 4 * p, v0, v1);
+            part = fma4(w0, w1, v0, v1, part);
+        }
+        const double beta2 = group_sum<W>(part);
+        if (!(beta2 == beta2)) {   // NaN
+            if (lane == 0) flag(a.status, DEV_NONFINITE);
+            nu_eff = n + 1;
+            break;
+        }
+        const double beta = sqrt(fmax(beta2, 0.0));
+        if (beta <= a.breakdown_tol * sqrt(hh)) {
+            nu_eff = n + 1;
+            break;
+        }
+        if constexpr (kAdj) {
+            if (lane == 0) hess[(size_t)n * a.nu_max + n + 1] = beta;
+        }
+        const double inv = 1.0 / beta;
+        for (int sl = 0; sl < NS; ++sl) {
+            const int p = sl * W + lane;
+            double2 w0, w1, v0, v1;
+            ld4(B + 4 * p, w0, w1);
+            ld4(SUn1 + 4 * p, v0, v1);
+            w0.x *= inv; w0.y *= inv; w1.x *= inv; w1.y *= inv;
+            v0.x *= inv; v0.y *= inv; v1.x *= inv; v1.y *= inv;
+            st4(A + 4 * p, w0, w1);
+            st4(Uw + (size_t)(n + 1) * vs + 4 * p, w0, w1);
+            st4(SUn1 + 4 * p, v0, v1);
+        }
+        __syncwarp(gm);
     }
     return nu_eff;
 }

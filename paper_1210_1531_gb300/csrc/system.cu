@@ -112,13 +112,15 @@ struct elses_system_s {
     std::vector<int> h_row_ptr;
 
     int nu_max = 0, na_max = 0, k3_grid = 0, batch_atoms = 0, deg_cap = 0, k3_bps = 0;
-    std::vector<int> tuned_bps;            // autotuner: resident Krylov CTAs per SM by cluster slots
-    std::vector<int> tuned_order;          // autotuner: work-queue order by cluster slots (1 size, 2 atom)
+    std::vector<int> tuned_bps;            // autotuner: resident Krylov CTAs per SM by class capacity / 16
+    std::vector<int> tuned_order;          // autotuner: work-queue order by class capacity / 16 (1 size, 2 atom)
+    std::vector<int> tuned_half;           // autotuner: odd 16-slot classes, 1 half-warps, 2 whole warps
     // Krylov launches: per batch of atoms, one launch per cluster size class (slots of 32 atoms),
     // each with its own shared-memory footprint and resident-CTA count
     // scratch_off: where the launch's per-CTA scratch starts, so that the class launches of one
     // batch can run at the same time
-    struct K3Launch { int batch_begin, batch_end, item_begin, item_count, na, grid, bps; size_t scratch_off; };
+    // key: the class's bound on cluster size in slots of 16 atoms (its capacity na may be larger)
+    struct K3Launch { int batch_begin, batch_end, item_begin, item_count, na, grid, bps, half, key; size_t scratch_off; };
     cudaStream_t side = nullptr;           // second stream for concurrent class launches
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<K3Launch> k3_launches;
@@ -289,33 +291,54 @@ int prepare_columns(elses_system s) {
         s->batch_atoms = (int)std::min<size_t>((size_t)s->n, std::max<size_t>(32, cols0 / 4));
         if (s->p.batch_atoms > 0) s->batch_atoms = std::min(s->n, s->p.batch_atoms);
     }
-    // size classes: atoms grouped by slots of 32 cluster atoms, largest class first; inside a
-    // class the batched form orders atoms by decreasing cluster size, the plain form by index
+    // size classes: atoms grouped by cluster slots, largest class first; inside a class the
+    // batched form orders atoms by decreasing cluster size (or atom order, as tuned), the plain
+    // form by index. Where two columns per warp apply (forces from the density matrix, one space
+    // per column, k3_lanes != 32) the slots hold 16 atoms: a class of an odd number c of them
+    // runs k_krylov_half (one column per half-warp, capacity 16 c) when it keeps at least as many
+    // warps per SM as k_krylov at capacity 16 (c + 1), or as the autotuner chose; the others run
+    // k_krylov. Otherwise slots of 32.
+    const bool half_ok = s->p.k3_lanes != 32 && s->p.force_mode == 0 && !s->p.krylov_block;
+    const int gslot = half_ok ? 16 : 32;
     std::vector<int> ord;
     ord.reserve(s->n);
     s->k3_launches.clear();
     size_t scratch = 0;
     int best_items = -1;
+    // an odd 16-slot class runs with half-warps, or with whole warps inside the next (even) class
+    auto odd_half = [&](int k) {
+        const int th = k < (int)s->tuned_half.size() ? s->tuned_half[k] : 0;
+        if (th) return th == 1;
+        return krylov_half_blocks_per_sm(16 * k, kdeg) >= 2 * krylov_blocks_per_sm(16 * (k + 1), kdeg);
+    };
     for (int b = 0; b < s->n; b += s->batch_atoms) {
         const int e = std::min(s->n, b + s->batch_atoms);
         size_t batch_off = 0;
-        for (int ns = s->na_max / 32; ns >= 1; --ns) {
+        for (int ns = s->na_max / gslot; ns >= 1; --ns) {
+            const int key = gslot * ns / 16;
+            const bool half = half_ok && (ns & 1) && odd_half(key);
+            if (half_ok && (ns & 1) && !half) continue;          // merged into class ns + 1
+            const bool merge_below = half_ok && !(ns & 1) && ns > 1 && !odd_half(key - 1);
             const int begin = (int)ord.size();
-            for (int a = b; a < e; ++a)
-                if ((s->h_clsize[a] + 31) / 32 == ns) ord.push_back(a);
+            for (int a = b; a < e; ++a) {
+                const int c = (s->h_clsize[a] + gslot - 1) / gslot;
+                if (c == ns || (merge_below && c == ns - 1)) ord.push_back(a);
+            }
             const int count = (int)ord.size() - begin;
             if (count == 0) continue;
-            const bool by_atom = ns < (int)s->tuned_order.size() && s->tuned_order[ns] == 2;
+            const int na = gslot * ns;
+            const bool by_atom = key < (int)s->tuned_order.size() && s->tuned_order[key] == 2;
             if (s->p.schedule == 1 && !by_atom)
                 std::stable_sort(ord.begin() + begin, ord.end(),
                                  [&](int x, int y) { return s->h_clsize[x] > s->h_clsize[y]; });
-            const int na = 32 * ns;
-            int bps = s->p.krylov_block ? block_krylov_blocks_per_sm(na, kdeg) : krylov_blocks_per_sm(na, kdeg);
+            int bps = s->p.krylov_block ? block_krylov_blocks_per_sm(na, kdeg)
+                      : half             ? krylov_half_blocks_per_sm(na, kdeg)
+                                         : krylov_blocks_per_sm(na, kdeg);
             if (bps < 1) return fail(ELSES_ERR_CAPACITY, "Krylov kernel cannot be resident (%d-atom class)", na);
             if (s->p.k3_ctas_per_sm > 0) bps = std::min(bps, s->p.k3_ctas_per_sm);
-            else if (ns < (int)s->tuned_bps.size() && s->tuned_bps[ns] > 0) bps = std::min(bps, s->tuned_bps[ns]);
+            else if (key < (int)s->tuned_bps.size() && s->tuned_bps[key] > 0) bps = std::min(bps, s->tuned_bps[key]);
             const int grid = std::min(count, s->num_sms * bps);
-            s->k3_launches.push_back({b, e, begin, count, na, grid, bps, batch_off});
+            s->k3_launches.push_back({b, e, begin, count, na, grid, bps, half ? 1 : 0, key, batch_off});
             batch_off += s->p.krylov_block ? (size_t)grid * block_krylov_scratch_doubles(nm, na)
                                            : (size_t)grid * kWarpsPerAtom * 2 * nm * na * 4;
             scratch = std::max(scratch, batch_off);
@@ -523,6 +546,7 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
         const auto& L = *ls[i];
         cudaStream_t lst = (conc && i != main_cls) ? s->side : st;
         ka.na_max = L.na;
+        ka.half = L.half;
         ka.order = s->order.p + L.item_begin;
         ka.n_items = L.item_count;
         ka.scratch = s->kscratch.p + L.scratch_off;
@@ -571,13 +595,14 @@ int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* 
     std::vector<size_t> off(s->k3_launches.size(), 0);
     for (size_t i = 0, used = 0; i < s->k3_launches.size(); ++i) {
         const auto& L = s->k3_launches[i];
-        int& bps = s->adj_bps[L.na / 32];
-        if (bps == 0) bps = adjoint_blocks_per_sm(L.na, kdeg);
-        if (bps < 1) return fail(ELSES_ERR_CAPACITY, "adjoint kernel cannot be resident (%d-atom class)", L.na);
+        const int na = (L.na + 31) / 32 * 32;   // the adjoint keeps one warp per column
+        int& bps = s->adj_bps[na / 32];
+        if (bps == 0) bps = adjoint_blocks_per_sm(na, kdeg);
+        if (bps < 1) return fail(ELSES_ERR_CAPACITY, "adjoint kernel cannot be resident (%d-atom class)", na);
         grid[i] = std::min(L.item_count, s->num_sms * bps);
         if (i == 0 || L.batch_begin != s->k3_launches[i - 1].batch_begin) used = 0;
         off[i] = used;     // the class launches of a batch run at the same time: own scratch each
-        used += (size_t)grid[i] * kWarpsPerAtom * adjoint_warp_doubles(nm, L.na);
+        used += (size_t)grid[i] * kWarpsPerAtom * adjoint_warp_doubles(nm, na);
         need = std::max(need, used);
     }
     TRY(s->ascratch.ensure(need));
@@ -626,7 +651,8 @@ int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* 
             const size_t i = li[t];
             const auto& L = s->k3_launches[i];
             cudaStream_t lst = (conc && t != main_cls) ? s->side : st;
-            ka.na_max = L.na;
+            ka.na_max = (L.na + 31) / 32 * 32;
+            ka.half = 0;
             ka.order = s->order.p + L.item_begin;
             ka.n_items = L.item_count;
             int* q = s->counters.p + kQueue0 + (int)std::min<size_t>(t, kCounters - kQueue0 - 1);
@@ -653,28 +679,47 @@ int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* 
 int autotune_impl(elses_system s, cudaStream_t st) {
     const int nm = s->nu_max;
     const int kdeg = s->user_hs ? s->max_nb : s->deg_cap;
-    s->tuned_bps.assign(s->na_max / 32 + 1, 0);
-    s->tuned_order.assign(s->na_max / 32 + 1, 0);
+    s->tuned_bps.assign(s->na_max / 16 + 1, 0);
+    s->tuned_order.assign(s->na_max / 16 + 1, 0);
+    s->tuned_half.assign(s->na_max / 16 + 1, 0);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
     int rc = 0;
     const auto launches = s->k3_launches;
+    const bool half_ok = s->p.k3_lanes != 32 && s->p.force_mode == 0 && !s->p.krylov_block;
     for (const auto& L : launches) {
         if (L.batch_begin != 0 || rc) continue;
-        const int ns = L.na / 32;
-        const int maxb = s->p.krylov_block ? block_krylov_blocks_per_sm(L.na, kdeg) : krylov_blocks_per_sm(L.na, kdeg);
-        const int sample = std::min(L.item_count, 2 * s->num_sms * maxb);
-        const size_t per_cta = s->p.krylov_block ? block_krylov_scratch_doubles(nm, L.na)
-                                                 : (size_t)kWarpsPerAtom * 2 * nm * L.na * 4;
-        if ((rc = s->kscratch.ensure((size_t)s->num_sms * maxb * per_cta)) < 0) break;
+        const int ns = L.key;
+        // the kernel forms to compare: a class of an odd number of 16-atom slots runs either
+        // with half-warps (capacity 16 ns) or with whole warps (capacity 16 (ns + 1))
+        struct Form { int half, na, maxb; };
+        std::vector<Form> forms;
+        if (half_ok && (ns & 1)) forms = {{1, 16 * ns, 0}, {0, 16 * (ns + 1), 0}};
+        else forms = {{L.half, L.na, 0}};
+        int maxb_all = 0;
+        for (auto& f : forms) {
+            f.maxb = s->p.krylov_block ? block_krylov_blocks_per_sm(f.na, kdeg)
+                     : f.half          ? krylov_half_blocks_per_sm(f.na, kdeg)
+                                       : krylov_blocks_per_sm(f.na, kdeg);
+            maxb_all = std::max(maxb_all, f.maxb);
+            const size_t per_cta = s->p.krylov_block ? block_krylov_scratch_doubles(nm, f.na)
+                                                     : (size_t)kWarpsPerAtom * 2 * nm * f.na * 4;
+            if ((rc = s->kscratch.ensure((size_t)s->num_sms * f.maxb * per_cta)) < 0) break;
+        }
+        if (rc) break;
+        const int sample = std::min(L.item_count, 2 * s->num_sms * maxb_all);   // the same atoms for every form
         double best = 0.0;
-        int best_b = maxb;
-        for (int b = 1; b <= maxb && !rc; ++b) {
+        int best_b = 1, best_f = 0;
+        bool first = true;
+        for (size_t fi = 0; fi < forms.size() && !rc; ++fi) {
+          const Form F = forms[fi];
+          for (int b = 1; b <= F.maxb && !rc; ++b) {
             KrylovArgs ka = krylov_args(s, L.batch_begin, L.batch_end);
             ka.UP = nullptr;
             ka.flops = nullptr;
-            ka.na_max = L.na;
+            ka.na_max = F.na;
+            ka.half = F.half;
             ka.order = s->order.p + L.item_begin;
             ka.n_items = sample;
             ka.scratch = s->kscratch.p;
@@ -697,8 +742,11 @@ int autotune_impl(elses_system s, cudaStream_t st) {
                 break;
             }
             const double per_atom = ms / sample;
-            if (b == 1 || per_atom < best) { best = per_atom; best_b = b; }
+            if (first || per_atom < best) { best = per_atom; best_b = b; best_f = (int)fi; first = false; }
+          }
         }
+        if (!rc && forms.size() == 2) s->tuned_half[ns] = forms[best_f].half ? 1 : 2;
+        const int chosen_na = forms[best_f].na, chosen_half = forms[best_f].half;
         if (!rc) s->tuned_bps[ns] = best_b;
         if (rc || s->p.schedule != 1 || L.item_count < 4 * s->num_sms * best_b) continue;
         // queue order of the whole class: as planned (decreasing cluster size), then atom order
@@ -715,7 +763,8 @@ int autotune_impl(elses_system s, cudaStream_t st) {
             KrylovArgs ka = krylov_args(s, L.batch_begin, L.batch_end);
             ka.UP = nullptr;
             ka.flops = nullptr;
-            ka.na_max = L.na;
+            ka.na_max = chosen_na;
+            ka.half = chosen_half;
             ka.order = s->order.p + L.item_begin;
             ka.n_items = L.item_count;
             ka.scratch = s->kscratch.p;
@@ -739,6 +788,7 @@ int autotune_impl(elses_system s, cudaStream_t st) {
     if (rc) {
         s->tuned_bps.clear();
         s->tuned_order.clear();
+        s->tuned_half.clear();
         return rc;
     }
     TRY(clear_status(s, st));        // the sampled columns may have flagged a breakdown
@@ -830,6 +880,7 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
     if (p.force_mode < 0 || p.force_mode > 1) return fail(ELSES_ERR_ARG, "force_mode must be 0 or 1");
     if (p.krylov_block < 0 || p.krylov_block > 1) return fail(ELSES_ERR_ARG, "krylov_block must be 0 or 1");
     if (p.batch_atoms < 0) return fail(ELSES_ERR_ARG, "batch_atoms must be >= 0");
+    if (p.k3_lanes != 0 && p.k3_lanes != 32) return fail(ELSES_ERR_ARG, "k3_lanes must be 0 or 32");
     if (p.krylov_block) {
         if (p.nu < 4) return fail(ELSES_ERR_ARG, "a block space needs nu >= 4");
         for (int c = 0; c < p.n_classes; ++c)
@@ -1351,9 +1402,9 @@ int elses_autotune(elses_system s, int run, int max_classes, int* classes_out, i
     for (const auto& L : s->k3_launches) {   // the classes of the first batch, largest first
         if (L.batch_begin != 0) continue;
         if (n < max_classes) {
-            const int ns = L.na / 32;
-            const bool by_atom = ns < (int)s->tuned_order.size() && s->tuned_order[ns] == 2;
-            classes_out[3 * n] = ns;
+            const int key = L.key;
+            const bool by_atom = key < (int)s->tuned_order.size() && s->tuned_order[key] == 2;
+            classes_out[3 * n] = L.na;
             classes_out[3 * n + 1] = L.bps;
             classes_out[3 * n + 2] = s->p.schedule != 1 ? 0 : by_atom ? 2 : 1;
         }

@@ -21,8 +21,8 @@ def test_autotuned_shape_keeps_results_bit_for_bit(eg):
     F = gu.to_np(F)
     shapes = s.autotune()
     assert len(shapes) >= 1
-    for slots, (bps, order) in shapes.items():
-        assert 1 <= slots <= 16 and 1 <= bps <= 8 and order in ("size", "atom")
+    for atoms, (bps, order) in shapes.items():
+        assert atoms % 16 == 0 and 16 <= atoms <= 512 and 1 <= bps <= 16 and order in ("size", "atom")
     assert s.stats()["k3_ctas_per_sm"] in [b for b, _ in shapes.values()]
     assert s.autotune_shapes() == shapes
     mu2, e_band2, _, F2 = s.energy_force()               # columns recomputed with the new shape

@@ -6,6 +6,8 @@ bit-exact neighbour, cluster and pattern lists. mu is not unique when it falls i
 is flat there), so the GPU's mu is checked for validity (the oracle's N at that mu is N_e) and
 rho is compared with the oracle evaluated at the GPU's mu.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -267,6 +269,25 @@ def test_diamond4096_sampled_columns(eg):
     for J in wl.sample_columns(w.n_atoms, 64):
         assert np.array_equal(cidx[cp[J]:cp[J + 1]], structure.cluster(w.pos, w.box, J, w.r_cluster))
     assert abs(r["F"].sum(axis=0)).max() < 1e-8
+
+
+def test_half_warp_columns(eg):
+    """Clusters of 3.6 A (about 30 to 45 atoms): the size classes with an odd number of 16-atom
+    slots run two columns per warp, one per half-warp (k_krylov_half). They match the oracle on
+    sampled columns, and the one-warp-per-column kernel (k3_lanes = 32) to rounding."""
+    w = dataclasses.replace(wl.make("diamond_4096"), r_cluster=3.6)
+    r = _sampled_parity(eg, w, 48)
+    caps = r["sys"].autotune_shapes()
+    assert any(cap % 32 == 16 for cap in caps), caps          # a half-warp class is in use
+    b = eg.system_for(w, k3_lanes=32)
+    assert all(cap % 32 == 0 for cap in b.autotune_shapes())
+    mu, e_band, _, F = b.energy_force()
+    assert abs(mu - r["mu"]) <= 3e-13
+    rho_a, _ = r["sys"].density_matrix(r["mu"])
+    rho_b, _ = b.density_matrix(r["mu"])
+    ra, rb = gu.to_np(rho_a), gu.to_np(rho_b)
+    assert np.abs(ra - rb).max() <= 1e-12 * np.abs(rb).max()
+    assert np.abs(r["F"] - gu.to_np(F)).max() <= 1e-10 * np.abs(gu.to_np(F)).max()
 
 
 def test_diamond4096_batched_equals_plain(eg):
