@@ -40,7 +40,7 @@ FP64_NOMINAL_GFLOPS = 152 * 2 * 2 * 2.07     # SMs x FP64 FMA/clk/SM x 2 flops x
 # DRAM bytes (read + write) of the k_krylov launches of one 4096-atom step, from one ncu capture
 # of the source whose sha256 prefix (krylov.cu + krylov.cuh) is given; reported per launch, null
 # once that source changes
-KRYLOV_TRAFFIC = {"krylov_sha256_prefix": "dd66aba4cfd5f9da", "bytes_per_step": 179.14e9,
+KRYLOV_TRAFFIC = {"krylov_sha256_prefix": "1dea01a43985331b", "bytes_per_step": 176.29e9,
                   "launches_per_step": 2}
 
 
