@@ -157,7 +157,8 @@ int elses_set_hs(elses_system sys, const double* H_dev, const double* S_dev, voi
  * computed before are invalidated; the results of later calls do not depend on the shape or
  * the order (bit for bit). run = 0 only reports the shapes in use. classes_out: optional host
  * int[3 * max_classes], triples (cluster capacity of the class in atoms, CTAs per SM,
- * queue order: 0 static, 1 by size, 2 by atom), largest class first; n_host: the number of classes. ERR_STATE for run = 1 when
+ * queue order: 0 static, 1 by size, 2 by atom), each class once (tuned at the first batch that
+ * has it); n_host: the number of classes. ERR_STATE for run = 1 when
  * params.k3_ctas_per_sm fixes the shape. Passage: none (a launch-shape choice). */
 int elses_autotune(elses_system sys, int run, int max_classes, int* classes_out, int* n_host,
                    void* stream);

@@ -281,12 +281,13 @@ int prepare_columns(elses_system s) {
         const size_t PK0 = (size_t)nm * (nm + 1) / 2;
         const size_t per_col0 = sizeof(double) * (2 * PK0 + 3 * (size_t)nm + eig_tri_doubles(nm) + eig_fac_doubles(nm) +
                                                   2 * eig_rot_cap(nm)) + eig_rot_cap(nm) + sizeof(int) * (nm + 1);
-        // batch buffers: up to 8 GB or a fifth of the free memory, so that large systems run in a
+        // batch buffers: up to 16 GB or a fifth of the free memory, so that large systems run in a
         // few long launches (shorter Krylov launch tails; measured on 10^6 atoms: 4800-atom
-        // batches 17.7 s per step, 37000-atom batches 17.3 s)
+        // batches 17.7 s per step, 37000-atom batches 17.3 s) and systems of a few 10^4 atoms in
+        // one batch, which needs no V for the energy (the 32768-atom composite: 2 batches at 8 GB)
         size_t free_b = 0, total_b = 0;
         cudaMemGetInfo(&free_b, &total_b);
-        const size_t budget = std::max<size_t>(size_t(1) << 30, std::min<size_t>(size_t(8) << 30, free_b / 5));
+        const size_t budget = std::max<size_t>(size_t(1) << 30, std::min<size_t>(size_t(16) << 30, free_b / 5));
         const size_t cols0 = std::max<size_t>(128, budget / per_col0);
         s->batch_atoms = (int)std::min<size_t>((size_t)s->n, std::max<size_t>(32, cols0 / 4));
         if (s->p.batch_atoms > 0) s->batch_atoms = std::min(s->n, s->p.batch_atoms);
@@ -670,7 +671,7 @@ int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* 
     return 0;
 }
 
-// The autotuner: per size class of the first batch, the Krylov kernel timed at every resident
+// The autotuner: per size class (at the first batch that has it), the Krylov kernel timed at every resident
 // CTA count that fits, on the class's first atoms in launch order (up to two full waves at the
 // largest count); the fastest per atom is kept in tuned_bps. With the work queue, the whole
 // class is then timed in both orders of its atoms -- decreasing cluster size (short tail) and
@@ -688,8 +689,10 @@ int autotune_impl(elses_system s, cudaStream_t st) {
     int rc = 0;
     const auto launches = s->k3_launches;
     const bool half_ok = s->p.k3_lanes != 32 && s->p.force_mode == 0 && !s->p.krylov_block;
+    std::vector<char> seen(s->na_max / 16 + 1, 0);
     for (const auto& L : launches) {
-        if (L.batch_begin != 0 || rc) continue;
+        if (rc || seen[L.key]) continue;   // each class once, at its first batch
+        seen[L.key] = 1;
         const int ns = L.key;
         // the kernel forms to compare: a class of an odd number of 16-atom slots runs either
         // with half-warps (capacity 16 ns) or with whole warps (capacity 16 (ns + 1))
@@ -1399,8 +1402,10 @@ int elses_autotune(elses_system s, int run, int max_classes, int* classes_out, i
         TRY(autotune_impl(s, (cudaStream_t)stream));
     }
     int n = 0;
-    for (const auto& L : s->k3_launches) {   // the classes of the first batch, largest first
-        if (L.batch_begin != 0) continue;
+    std::vector<char> seen(s->na_max / 16 + 1, 0);
+    for (const auto& L : s->k3_launches) {   // every class once, largest first within a batch
+        if (seen[L.key]) continue;
+        seen[L.key] = 1;
         if (n < max_classes) {
             const int key = L.key;
             const bool by_atom = key < (int)s->tuned_order.size() && s->tuned_order[key] == 2;
