@@ -323,6 +323,29 @@ def test_dimer_breakdown_warning(eg):
     assert nu[1] == 2 and nu[2] == 2                       # px, py: invariant pi pairs
 
 
+def test_dimer_columns_stop_at_different_steps(eg):
+    """A z-dimer with nu = 8: the s and pz columns span 4 dimensions, the px and py columns 2
+    (invariant pi pairs). The two columns that share a warp in the half-warp form (s with px, py
+    with pz) stop at different Krylov steps; each Krylov space is then exact on its invariant
+    subspace, so rho matches the oracle and the exact diagonalisation."""
+    pos, box = wl.dimer(wl.sk_params().r0)
+    w = wl.Workload("dimer", pos, box, wl.sk_params(), r_cluster=0.0, nu=8)
+    s = eg.system_for(w)
+    assert any(cap % 32 == 16 for cap in s.autotune_shapes())      # the half-warp form
+    mu, e_band, _, _ = s.energy_force()
+    nu = gu.to_np(s.spectra()["nu_eff"])
+    assert list(nu[:4]) == [4, 2, 2, 4] and list(nu[4:]) == [4, 2, 2, 4]
+    res = pipeline.run(w, mu=mu)
+    rho, rhoE = s.density_matrix(mu)
+    assert np.abs(gu.to_np(rho) - res["rho"]).max() < gu.RHO_TOL
+    assert np.abs(gu.to_np(rhoE) - res["rhoE"]).max() < gu.RHO_TOL
+    assert abs(e_band - res["E_band"]) / w.n_atoms < gu.E_TOL_PER_ATOM
+    ref = pipeline.dense_reference(w)
+    rp, ci = (gu.to_np(t) for t in s.pattern())
+    dense = hamiltonian.bsr_to_dense(rp, ci, gu.to_np(rho))
+    assert np.abs(dense - ref["rho"]).max() < 1e-8 and abs(mu - ref["mu"]) < 1e-8
+
+
 def test_errors_are_reported(eg):
     w = wl.make("diamond_64")
     pos = torch.tensor(w.pos, device="cuda")
