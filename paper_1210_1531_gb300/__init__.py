@@ -172,7 +172,15 @@ def make_params(r_cluster, nu, kT, n_electrons, two_pass=False, nu_classes=(), s
 
 
 class System:
-    """One atomic system on the current CUDA device (wraps an elses_system handle)."""
+    """One atomic system on the current CUDA device (wraps an elses_system handle).
+
+    The keyword arguments map to the fields of elses_params (include/elses.h): the workflow
+    (two_pass), the size classes of nu (nu_classes), the Krylov launch form (schedule: 0 plain,
+    1 work queue; k3_ctas_per_sm; k3_lanes: 0 automatic half-warp columns, 32 one warp per
+    column; autotune: time the launch shapes at build), the step's CUDA-graph replay (graph),
+    the forces (exact_forces: the gradient of the truncated method), block-start Krylov spaces
+    (krylov_block), the batch size (batch_atoms) and per-call event timings (timing).
+    """
 
     def __init__(self, pos, box, sk, r_cluster, nu, kT, n_electrons, two_pass=False,
                  nu_classes=(), schedule=0, max_neighbors=0, max_cluster=0, timing=False,
