@@ -9,21 +9,21 @@
 //   density_matrix : rho, rhoE on the pattern                                        (a8)
 //   energies       : N, E_band, Omega, F_free                                        (a9)
 //   forces         : per-block gradient contraction, per-atom sums                   (a10)
+// The autotuner (autotune.cu) and the CUDA-graph form of the step (graph.cu) share the state and
+// helpers declared in system_impl.h.
 #include <algorithm>
-#include <cmath>
 #include <cstdarg>
 #include <cstdio>
-#include <cstring>
 #include <string>
-#include <vector>
 
-#include "internal.h"
+#include "system_impl.h"
 
 using namespace elses;
 
 static thread_local std::string g_err;
 
-static int fail(int code, const char* fmt, ...) {
+namespace elses {
+int fail(int code, const char* fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -33,7 +33,6 @@ static int fail(int code, const char* fmt, ...) {
     return code;
 }
 
-namespace elses {
 int report_error(int code, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -45,194 +44,9 @@ int report_error(int code, const char* fmt, ...) {
 }
 }  // namespace elses
 
-#define CUDA_TRY(x)                                                                        \
-    do {                                                                                   \
-        cudaError_t e_ = (x);                                                              \
-        if (e_ != cudaSuccess) return fail(ELSES_ERR_CUDA, "%s: %s", #x, cudaGetErrorString(e_)); \
-    } while (0)
+unsigned long long g_alloc_epoch = 0;
 
-#define TRY(x)                     \
-    do {                           \
-        int r_ = (x);              \
-        if (r_ < 0) return r_;     \
-    } while (0)
-
-// Bumped by every device (re)allocation of a DevBuf: a captured graph whose buffers may have
-// moved is captured again.
-static unsigned long long g_alloc_epoch = 0;
-
-template <class T>
-struct DevBuf {
-    T* p = nullptr;
-    size_t cap = 0;
-    int ensure(size_t n) {
-        if (n <= cap && p) return 0;
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-        size_t want = std::max<size_t>(n, 1);
-        if (cudaMalloc(&p, want * sizeof(T)) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(ELSES_ERR_OOM, "device allocation of %zu bytes failed", want * sizeof(T));
-        }
-        cap = want;
-        ++g_alloc_epoch;
-        return 0;
-    }
-    void release() {
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-    }
-    DevBuf() = default;
-    DevBuf(const DevBuf&) = delete;
-    DevBuf& operator=(const DevBuf&) = delete;
-    ~DevBuf() { release(); }
-};
-
-struct elses_system_s {
-    int n = 0, M = 0;
-    double box[3] = {0, 0, 0};
-    elses_sk sk{};
-    elses_params p{};
-    SKDev skd{};
-    int num_sms = 0;
-    CellGrid grid{};
-    bool user_hs = false;
-
-    DevBuf<double> pos;
-    DevBuf<int> cell_of, cell_count, cell_start, cursor, cell_atoms;
-    DevBuf<int> row_cnt, row_ptr, col_idx, row_of, tmap;
-    DevBuf<int> cl_cnt, cl_ptr, cl_idx;
-    DevBuf<int> counters;   // see kCounters
-    DevBuf<unsigned long long> flops_ctr;
-    DevBuf<double> H, S, skr;
-    int nnzb = 0, max_nb = 0, max_cl = 0;
-    long long cl_total = 0;
-    std::vector<int> h_row_ptr;
-
-    int nu_max = 0, na_max = 0, k3_grid = 0, batch_atoms = 0, deg_cap = 0, k3_bps = 0;
-    std::vector<int> tuned_bps;            // autotuner: resident Krylov CTAs per SM by class capacity / 16
-    std::vector<int> tuned_order;          // autotuner: work-queue order by class capacity / 16 (1 size, 2 atom)
-    std::vector<int> tuned_half;           // autotuner: odd 16-slot classes, 1 half-warps, 2 whole warps
-    // Krylov launches: per batch of atoms, one launch per cluster size class (slots of 32 atoms),
-    // each with its own shared-memory footprint and resident-CTA count
-    // scratch_off: where the launch's per-CTA scratch starts, so that the class launches of one
-    // batch can run at the same time
-    // key: the class's bound on cluster size in slots of 16 atoms (its capacity na may be larger)
-    struct K3Launch { int batch_begin, batch_end, item_begin, item_count, na, grid, bps, half, key; size_t scratch_off; };
-    cudaStream_t side = nullptr;           // second stream for concurrent class launches
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    std::vector<K3Launch> k3_launches;
-    std::vector<int> h_clsize;
-    DevBuf<double> kscratch, Hp, Sp, urow, surow, hurow, etri, efac, erot_c, erot_s, ewt;
-    DevBuf<unsigned char> erot_k;
-    DevBuf<int> erot_n, eperm;
-    DevBuf<double> eps, cc, dd, gg, V, UP, Vb, UPb;
-    DevBuf<int> nu_eff, order;
-    DevBuf<double> rho, rhoE, gblock;
-    DevBuf<double> ascratch, adjH, adjS;   // exact-gradient scratch and its pattern gradients
-    DevBuf<double> bstore;                 // per-column bases kept for the exact gradient
-    size_t bstride = 0, bvec = 0;
-    bool use_store = false;
-    // the eigen-factors of every column are in the batch buffers and the stored V is not formed
-    bool v_lazy = false;
-    std::vector<int> adj_bps;              // resident adjoint CTAs per SM, by cluster slots
-    DevBuf<double> partials, zbuf, gbuf, dosbuf, act_below;
-    DevBuf<double2> act;
-    DevBuf<int> act_n;
-    DevBuf<BisectState> bstate;
-    DevBuf<unsigned> ticket;
-    std::vector<char> atom_done;
-    long long atoms_done = 0;
-
-    elses_stats stats{};
-    double mu = 0.0;
-    bool have_mu = false;
-    bool have_rho = false;   // rho, rhoE of the current positions are in rho / rhoE
-
-    // CUDA-event timing of kernel groups (params.timing = 1)
-    struct EvPair { cudaEvent_t a, b; int cat; };
-    std::vector<EvPair> pending;
-    std::vector<cudaEvent_t> pool;
-    cudaEvent_t ev() {
-        cudaEvent_t e;
-        if (!pool.empty()) { e = pool.back(); pool.pop_back(); }
-        else cudaEventCreate(&e);
-        return e;
-    }
-    // while a step is captured into the graph form, the timing events become event-record
-    // nodes of the graph (recorded at every replay, read by collect_graph)
-    bool capturing = false;
-    std::vector<EvPair> graph_ev;
-    void tic(int cat, cudaStream_t st) {
-        if (!p.timing) return;
-        EvPair q{ev(), ev(), cat};
-        if (capturing) {
-            cudaEventRecordWithFlags(q.a, st, cudaEventRecordExternal);
-            graph_ev.push_back(q);
-        } else {
-            cudaEventRecord(q.a, st);
-            pending.push_back(q);
-        }
-    }
-    void toc(cudaStream_t st) {
-        if (!p.timing) return;
-        if (capturing) {
-            if (!graph_ev.empty()) cudaEventRecordWithFlags(graph_ev.back().b, st, cudaEventRecordExternal);
-            return;
-        }
-        if (pending.empty()) return;
-        cudaEventRecord(pending.back().b, st);
-    }
-    void add_time(const EvPair& q) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
-            double* slot[] = {&stats.t_krylov_ms, &stats.t_eig_ms, &stats.t_bisect_ms,
-                              &stats.t_density_ms, &stats.t_force_ms, &stats.t_adjoint_ms};
-            *slot[q.cat] += ms;
-        }
-    }
-    void collect_graph() {   // after a synchronisation of the stream that replayed the graph
-        for (auto& q : graph_ev) add_time(q);
-        cudaGetLastError();
-    }
-    // graph form of elses_energy_force (params.graph): the captured step, what it was captured
-    // for (launch plan, buffers, forces output, parameters), the kernels it launches
-    cudaGraphExec_t graph_exec = nullptr;
-    cudaStream_t gstream = nullptr;       // capture stream (the legacy stream cannot capture)
-    std::vector<long long> graph_key;
-    long long graph_launches = 0, graph_krylov = 0, graph_columns = 0;
-    void drop_graph() {
-        if (graph_exec) cudaGraphExecDestroy(graph_exec);
-        graph_exec = nullptr;
-        for (auto& q : graph_ev) { pool.push_back(q.a); pool.push_back(q.b); }
-        graph_ev.clear();
-    }
-    void collect() {   // after a synchronisation of the stream
-        for (auto& q : pending) {
-            add_time(q);
-            pool.push_back(q.a);
-            pool.push_back(q.b);
-        }
-        pending.clear();
-        cudaGetLastError();
-    }
-    ~elses_system_s() {
-        drop_graph();
-        if (gstream) cudaStreamDestroy(gstream);
-        for (auto& q : pending) { pool.push_back(q.a); pool.push_back(q.b); }
-        for (auto e : pool) cudaEventDestroy(e);
-    }
-};
-
-enum { T_KRYLOV = 0, T_EIG = 1, T_BISECT = 2, T_DENSITY = 3, T_FORCE = 4, T_ADJOINT = 5 };
-// device counters: [0] max neighbours, [1] max cluster, [2] status, [3] unused, [8..] the work
-// queues of the class launches of a batch (one each, so that they can run at the same time)
-constexpr int kQueue0 = 8;
-constexpr int kCounters = 24;
-
-namespace {
+namespace elses {
 
 int nu_of_params(const elses_params& p) {
     int m = p.nu;
@@ -240,7 +54,7 @@ int nu_of_params(const elses_params& p) {
     return m;
 }
 
-int check_status(elses_system s, cudaStream_t st, bool allow_breakdown_warning = true) {
+int check_status(elses_system s, cudaStream_t st, bool allow_breakdown_warning) {
     int h = 0;
     CUDA_TRY(cudaMemcpyAsync(&h, s->counters.p + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
@@ -516,7 +330,7 @@ int ensure_V(elses_system s, cudaStream_t st) {
 // unformed; in the stored workflow that is kept only for a batch of every atom (its factors then
 // stay in the batch buffers until ensure_V or the next batch).
 int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_col0,
-              double** UP_out, int* up_block0, cudaStream_t st, bool need_rows = true, bool form_v = true) {
+              double** UP_out, int* up_block0, cudaStream_t st, bool need_rows, bool form_v) {
     const int nm = s->nu_max;
     if (stored && !form_v && (b != 0 || e != s->n)) form_v = true;
     // the batch buffers are about to be overwritten: V of the other columns first, unless every
@@ -584,7 +398,7 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
 // ([nnzb][16], overwritten): per batch, the adjoint kernel per size class, after the batch's
 // Krylov columns are recomputed when V is not kept (two-pass mode).
 int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* gS, double s_scale,
-                 cudaStream_t st, const double* mu_dev = nullptr) {
+                 cudaStream_t st, const double* mu_dev) {
     const int nm = s->nu_max;
     const int kdeg = s->user_hs ? s->max_nb : s->deg_cap;
     CUDA_TRY(cudaMemsetAsync(gH, 0, sizeof(double) * 16 * (size_t)s->nnzb, st));
@@ -671,134 +485,6 @@ int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* 
     return 0;
 }
 
-// The autotuner: per size class (at the first batch that has it), the Krylov kernel timed at every resident
-// CTA count that fits, on the class's first atoms in launch order (up to two full waves at the
-// largest count); the fastest per atom is kept in tuned_bps. With the work queue, the whole
-// class is then timed in both orders of its atoms -- decreasing cluster size (short tail) and
-// atom order (neighbouring clusters in flight together share H and S in L2) -- and the faster
-// is kept in tuned_order. The launches are planned again.
-int autotune_impl(elses_system s, cudaStream_t st) {
-    const int nm = s->nu_max;
-    const int kdeg = s->user_hs ? s->max_nb : s->deg_cap;
-    s->tuned_bps.assign(s->na_max / 16 + 1, 0);
-    s->tuned_order.assign(s->na_max / 16 + 1, 0);
-    s->tuned_half.assign(s->na_max / 16 + 1, 0);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    CUDA_TRY(cudaEventCreate(&e0));
-    CUDA_TRY(cudaEventCreate(&e1));
-    int rc = 0;
-    const auto launches = s->k3_launches;
-    const bool half_ok = s->p.k3_lanes != 32 && s->p.force_mode == 0 && !s->p.krylov_block;
-    std::vector<char> seen(s->na_max / 16 + 1, 0);
-    for (const auto& L : launches) {
-        if (rc || seen[L.key]) continue;   // each class once, at its first batch
-        seen[L.key] = 1;
-        const int ns = L.key;
-        // the kernel forms to compare: a class of an odd number of 16-atom slots runs either
-        // with half-warps (capacity 16 ns) or with whole warps (capacity 16 (ns + 1))
-        struct Form { int half, na, maxb; };
-        std::vector<Form> forms;
-        if (half_ok && (ns & 1)) forms = {{1, 16 * ns, 0}, {0, 16 * (ns + 1), 0}};
-        else forms = {{L.half, L.na, 0}};
-        int maxb_all = 0;
-        for (auto& f : forms) {
-            f.maxb = s->p.krylov_block ? block_krylov_blocks_per_sm(f.na, kdeg)
-                     : f.half          ? krylov_half_blocks_per_sm(f.na, kdeg)
-                                       : krylov_blocks_per_sm(f.na, kdeg);
-            maxb_all = std::max(maxb_all, f.maxb);
-            const size_t per_cta = s->p.krylov_block ? block_krylov_scratch_doubles(nm, f.na)
-                                                     : (size_t)kWarpsPerAtom * 2 * nm * f.na * 4;
-            if ((rc = s->kscratch.ensure((size_t)s->num_sms * f.maxb * per_cta)) < 0) break;
-        }
-        if (rc) break;
-        const int sample = std::min(L.item_count, 2 * s->num_sms * maxb_all);   // the same atoms for every form
-        double best = 0.0;
-        int best_b = 1, best_f = 0;
-        bool first = true;
-        for (size_t fi = 0; fi < forms.size() && !rc; ++fi) {
-          const Form F = forms[fi];
-          for (int b = 1; b <= F.maxb && !rc; ++b) {
-            KrylovArgs ka = krylov_args(s, L.batch_begin, L.batch_end);
-            ka.UP = nullptr;
-            ka.flops = nullptr;
-            ka.na_max = F.na;
-            ka.half = F.half;
-            ka.order = s->order.p + L.item_begin;
-            ka.n_items = sample;
-            ka.scratch = s->kscratch.p;
-            const int grid = std::min(sample, s->num_sms * b);
-            float ms = 0.f;
-            for (int rep = 0; rep < 2; ++rep) {       // the first launch warms caches and clocks
-                if (s->p.schedule == 1) {
-                    ka.queue = s->counters.p + kQueue0;
-                    if (cudaMemsetAsync(ka.queue, 0, sizeof(int), st) != cudaSuccess) { rc = fail(ELSES_ERR_CUDA, "memset"); break; }
-                }
-                cudaEventRecord(e0, st);
-                if (s->p.krylov_block) block_krylov_columns(ka, grid, st);
-                else krylov_columns(ka, grid, st);
-                cudaEventRecord(e1, st);
-                s->stats.launches++;
-            }
-            if (rc) break;
-            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                rc = fail(ELSES_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(cudaGetLastError()));
-                break;
-            }
-            const double per_atom = ms / sample;
-            if (first || per_atom < best) { best = per_atom; best_b = b; best_f = (int)fi; first = false; }
-          }
-        }
-        if (!rc && forms.size() == 2) s->tuned_half[ns] = forms[best_f].half ? 1 : 2;
-        const int chosen_na = forms[best_f].na, chosen_half = forms[best_f].half;
-        if (!rc) s->tuned_bps[ns] = best_b;
-        if (rc || s->p.schedule != 1 || L.item_count < 4 * s->num_sms * best_b) continue;
-        // queue order of the whole class: as planned (decreasing cluster size), then atom order
-        std::vector<int> seg(L.item_count);
-        if (cudaMemcpy(seg.data(), s->order.p + L.item_begin, sizeof(int) * L.item_count,
-                       cudaMemcpyDeviceToHost) != cudaSuccess) { rc = fail(ELSES_ERR_CUDA, "order readback"); break; }
-        std::vector<int> atom_order = seg;
-        std::sort(atom_order.begin(), atom_order.end());
-        float t_order[2] = {0.f, 0.f};
-        for (int o = 0; o < 2 && !rc; ++o) {
-            const std::vector<int>& ord = o == 0 ? seg : atom_order;
-            if (cudaMemcpyAsync(s->order.p + L.item_begin, ord.data(), sizeof(int) * L.item_count,
-                                cudaMemcpyHostToDevice, st) != cudaSuccess) { rc = fail(ELSES_ERR_CUDA, "order upload"); break; }
-            KrylovArgs ka = krylov_args(s, L.batch_begin, L.batch_end);
-            ka.UP = nullptr;
-            ka.flops = nullptr;
-            ka.na_max = chosen_na;
-            ka.half = chosen_half;
-            ka.order = s->order.p + L.item_begin;
-            ka.n_items = L.item_count;
-            ka.scratch = s->kscratch.p;
-            ka.queue = s->counters.p + kQueue0;
-            const int grid = std::min(L.item_count, s->num_sms * best_b);
-            for (int rep = 0; rep < 2; ++rep) {
-                cudaMemsetAsync(ka.queue, 0, sizeof(int), st);
-                cudaEventRecord(e0, st);
-                if (s->p.krylov_block) block_krylov_columns(ka, grid, st);
-                else krylov_columns(ka, grid, st);
-                cudaEventRecord(e1, st);
-                s->stats.launches++;
-            }
-            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t_order[o], e0, e1) != cudaSuccess)
-                rc = fail(ELSES_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(cudaGetLastError()));
-        }
-        if (!rc) s->tuned_order[ns] = t_order[1] < t_order[0] ? 2 : 1;
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (rc) {
-        s->tuned_bps.clear();
-        s->tuned_order.clear();
-        s->tuned_half.clear();
-        return rc;
-    }
-    TRY(clear_status(s, st));        // the sampled columns may have flagged a breakdown
-    CUDA_TRY(cudaStreamSynchronize(st));
-    return prepare_columns(s);       // launch plan with the chosen shapes; columns invalidated
-}
-
 int check_built(elses_system s) {
     if (!s) return fail(ELSES_ERR_ARG, "null system");
     if (s->n <= 0 || !s->H.p) return fail(ELSES_ERR_STATE, "system not built");
@@ -843,9 +529,124 @@ DensityArgs density_args(elses_system s, double mu, double* rho, double* rhoE) {
     return d;
 }
 
-}  // namespace
+// rho columns of atoms [b, e) at mu: from V where it is formed, else from the eigen-factors of the
+// batch just computed (t = V w formed by k_eig_weights).
+static void density_batch(elses_system s, double mu, double* rho, double* rhoE, int b, int e, const double* V,
+                          int v0, const double* UP, int u0, bool factors, cudaStream_t st,
+                          const double* mu_dev = nullptr) {
+    DensityArgs d = density_args(s, mu, rho, rhoE);
+    d.mu_dev = mu_dev;
+    d.atom_begin = b;
+    d.atom_end = e;
+    d.V = V;
+    d.v_col0 = v0;
+    d.UP = UP;
+    d.up_block0 = u0;
+    s->tic(T_DENSITY, st);
+    if (factors) {
+        eig_density_weights(eig_args(s, b, e, nullptr), mu, mu_dev, s->p.kT, s->ewt.p, st);
+        s->stats.launches++;
+        d.T = s->ewt.p;
+    }
+    density_columns(d, st);
+    s->toc(st);
+    s->stats.launches++;
+}
+
+// mu_dev: when set, mu is read from device memory (the captured step of the graph form).
+int density_impl(elses_system s, double mu, double* rho, double* rhoE, cudaStream_t st,
+                 const double* mu_dev) {
+    if (s->atoms_done != s->n) return fail(ELSES_ERR_STATE, "density_matrix needs every column");
+    if (!mu_dev) TRY(clear_status(s, st));
+    if (!s->p.two_pass) {
+        density_batch(s, mu, rho, rhoE, 0, s->n, s->V.p, 0, s->UP.p, 0, s->v_lazy, st, mu_dev);
+    } else {
+        // second calculation of G (Eq. 3): recompute every batch, then its rho columns
+        for (int b = 0; b < s->n; b += s->batch_atoms) {
+            const int e = std::min(s->n, b + s->batch_atoms);
+            double* V;
+            double* UP;
+            int v0, u0;
+            TRY(run_batch(s, b, e, false, &V, &v0, &UP, &u0, st, true, false));
+            density_batch(s, mu, rho, rhoE, b, e, V, v0, UP, u0, true, st, mu_dev);
+        }
+    }
+    return 0;
+}
+
+int energy_force_eager(elses_system s, double* mu_host, double* e_band_host, double* f_free_host,
+                       double* forces_dev, cudaStream_t st) {
+    void* stream = (void*)st;
+    int warn = elses_green_columns(s, 0, s->M, 0, nullptr, nullptr, nullptr, stream);
+    if (warn < 0) return warn;
+    double mu = 0.0;
+    TRY(elses_find_mu(s, &mu, nullptr, stream));
+    TRY(density_impl(s, mu, s->rho.p, s->rhoE.p, st));
+    s->have_rho = true;
+    ReduceArgs r = reduce_args(s);
+    s->tic(T_BISECT, st);
+    scalars_at(r, mu, st);
+    s->toc(st);
+    s->stats.launches++;
+    if (forces_dev) {
+        const double* gh = s->rho.p;
+        const double* gs = s->rhoE.p;
+        if (s->p.force_mode == 1) {   // exact gradient of the truncated method: dF/dH, -dF/dS
+            TRY(s->adjH.ensure((size_t)s->nnzb * 16));
+            TRY(s->adjS.ensure((size_t)s->nnzb * 16));
+            TRY(adjoint_impl(s, mu, 0, s->n, s->adjH.p, s->adjS.p, -1.0, st));
+            gh = s->adjH.p;
+            gs = s->adjS.p;
+        }
+        s->tic(T_FORCE, st);
+        forces(s->pos.p, s->n, s->box, s->skd, s->row_ptr.p, s->col_idx.p, s->row_of.p, s->tmap.p, s->nnzb,
+               gh, gs, s->gblock.p, forces_dev, st);
+        s->toc(st);
+        s->stats.launches += 2;
+    }
+    BisectState h{};
+    CUDA_TRY(cudaMemcpyAsync(&h, s->bstate.p, sizeof h, cudaMemcpyDeviceToHost, st));
+    int rc = check_status(s, st);
+    if (rc < 0) return rc;
+    if (mu_host) *mu_host = mu;
+    if (e_band_host) *e_band_host = h.e_band;
+    if (f_free_host) *f_free_host = h.omega + mu * s->p.n_electrons;
+    return warn > 0 ? warn : rc;
+}
+
+}  // namespace elses
 
 extern "C" {
+
+int elses_density_matrix(elses_system s, double mu, double* rho_dev, double* rhoE_dev, void* stream) {
+    TRY(check_built(s));
+    if (!rho_dev) return fail(ELSES_ERR_ARG, "null rho");
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(density_impl(s, mu, rho_dev, rhoE_dev, st));
+    return check_status(s, st);
+}
+
+int elses_energies(elses_system s, double mu, double* n_host, double* e_band_host, double* omega_host,
+                   double* f_free_host, void* stream) {
+    TRY(check_built(s));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (s->atoms_done != s->n) return fail(ELSES_ERR_STATE, "energies need every column");
+    ReduceArgs r = reduce_args(s);
+    s->tic(T_BISECT, st);
+    scalars_at(r, mu, st);
+    s->toc(st);
+    s->stats.launches++;
+    BisectState h{};
+    CUDA_TRY(cudaMemcpyAsync(&h, s->bstate.p, sizeof h, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    s->collect();
+    if (n_host) *n_host = h.n_at;
+    if (e_band_host) *e_band_host = h.e_band;
+    if (omega_host) *omega_host = h.omega;
+    if (f_free_host) *f_free_host = h.omega + mu * s->p.n_electrons;
+    return ELSES_OK;
+}
+
 
 int elses_version(void) { return 1; }
 
@@ -1133,258 +934,6 @@ int elses_find_mu(elses_system s, double* mu_host, double* n_at_mu_host, void* s
     return ELSES_OK;
 }
 
-// rho columns of atoms [b, e) at mu: from V where it is formed, else from the eigen-factors of the
-// batch just computed (t = V w formed by k_eig_weights).
-static void density_batch(elses_system s, double mu, double* rho, double* rhoE, int b, int e, const double* V,
-                          int v0, const double* UP, int u0, bool factors, cudaStream_t st,
-                          const double* mu_dev = nullptr) {
-    DensityArgs d = density_args(s, mu, rho, rhoE);
-    d.mu_dev = mu_dev;
-    d.atom_begin = b;
-    d.atom_end = e;
-    d.V = V;
-    d.v_col0 = v0;
-    d.UP = UP;
-    d.up_block0 = u0;
-    s->tic(T_DENSITY, st);
-    if (factors) {
-        eig_density_weights(eig_args(s, b, e, nullptr), mu, mu_dev, s->p.kT, s->ewt.p, st);
-        s->stats.launches++;
-        d.T = s->ewt.p;
-    }
-    density_columns(d, st);
-    s->toc(st);
-    s->stats.launches++;
-}
-
-// mu_dev: when set, mu is read from device memory (the captured step of the graph form).
-static int density_impl(elses_system s, double mu, double* rho, double* rhoE, cudaStream_t st,
-                        const double* mu_dev = nullptr) {
-    if (s->atoms_done != s->n) return fail(ELSES_ERR_STATE, "density_matrix needs every column");
-    if (!mu_dev) TRY(clear_status(s, st));
-    if (!s->p.two_pass) {
-        density_batch(s, mu, rho, rhoE, 0, s->n, s->V.p, 0, s->UP.p, 0, s->v_lazy, st, mu_dev);
-    } else {
-        // second calculation of G (Eq. 3): recompute every batch, then its rho columns
-        for (int b = 0; b < s->n; b += s->batch_atoms) {
-            const int e = std::min(s->n, b + s->batch_atoms);
-            double* V;
-            double* UP;
-            int v0, u0;
-            TRY(run_batch(s, b, e, false, &V, &v0, &UP, &u0, st, true, false));
-            density_batch(s, mu, rho, rhoE, b, e, V, v0, UP, u0, true, st, mu_dev);
-        }
-    }
-    return 0;
-}
-
-int elses_density_matrix(elses_system s, double mu, double* rho_dev, double* rhoE_dev, void* stream) {
-    TRY(check_built(s));
-    if (!rho_dev) return fail(ELSES_ERR_ARG, "null rho");
-    cudaStream_t st = (cudaStream_t)stream;
-    TRY(density_impl(s, mu, rho_dev, rhoE_dev, st));
-    return check_status(s, st);
-}
-
-int elses_energies(elses_system s, double mu, double* n_host, double* e_band_host, double* omega_host,
-                   double* f_free_host, void* stream) {
-    TRY(check_built(s));
-    cudaStream_t st = (cudaStream_t)stream;
-    if (s->atoms_done != s->n) return fail(ELSES_ERR_STATE, "energies need every column");
-    ReduceArgs r = reduce_args(s);
-    s->tic(T_BISECT, st);
-    scalars_at(r, mu, st);
-    s->toc(st);
-    s->stats.launches++;
-    BisectState h{};
-    CUDA_TRY(cudaMemcpyAsync(&h, s->bstate.p, sizeof h, cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
-    s->collect();
-    if (n_host) *n_host = h.n_at;
-    if (e_band_host) *e_band_host = h.e_band;
-    if (omega_host) *omega_host = h.omega;
-    if (f_free_host) *f_free_host = h.omega + mu * s->p.n_electrons;
-    return ELSES_OK;
-}
-
-namespace {
-
-int energy_force_eager(elses_system s, double* mu_host, double* e_band_host, double* f_free_host,
-                       double* forces_dev, cudaStream_t st) {
-    void* stream = (void*)st;
-    int warn = elses_green_columns(s, 0, s->M, 0, nullptr, nullptr, nullptr, stream);
-    if (warn < 0) return warn;
-    double mu = 0.0;
-    TRY(elses_find_mu(s, &mu, nullptr, stream));
-    TRY(density_impl(s, mu, s->rho.p, s->rhoE.p, st));
-    s->have_rho = true;
-    ReduceArgs r = reduce_args(s);
-    s->tic(T_BISECT, st);
-    scalars_at(r, mu, st);
-    s->toc(st);
-    s->stats.launches++;
-    if (forces_dev) {
-        const double* gh = s->rho.p;
-        const double* gs = s->rhoE.p;
-        if (s->p.force_mode == 1) {   // exact gradient of the truncated method: dF/dH, -dF/dS
-            TRY(s->adjH.ensure((size_t)s->nnzb * 16));
-            TRY(s->adjS.ensure((size_t)s->nnzb * 16));
-            TRY(adjoint_impl(s, mu, 0, s->n, s->adjH.p, s->adjS.p, -1.0, st));
-            gh = s->adjH.p;
-            gs = s->adjS.p;
-        }
-        s->tic(T_FORCE, st);
-        forces(s->pos.p, s->n, s->box, s->skd, s->row_ptr.p, s->col_idx.p, s->row_of.p, s->tmap.p, s->nnzb,
-               gh, gs, s->gblock.p, forces_dev, st);
-        s->toc(st);
-        s->stats.launches += 2;
-    }
-    BisectState h{};
-    CUDA_TRY(cudaMemcpyAsync(&h, s->bstate.p, sizeof h, cudaMemcpyDeviceToHost, st));
-    int rc = check_status(s, st);
-    if (rc < 0) return rc;
-    if (mu_host) *mu_host = mu;
-    if (e_band_host) *e_band_host = h.e_band;
-    if (f_free_host) *f_free_host = h.omega + mu * s->p.n_electrons;
-    return warn > 0 ? warn : rc;
-}
-
-// The device work of one energy + force evaluation, enqueued with no host synchronisation (the
-// captured step of the graph form): the columns, the bisection's fixed sequence of launches
-// (those after convergence return at once), the density, the scalars and the forces, all at the
-// mu the bisection leaves in device memory. The same kernels and arguments as the eager path.
-int enqueue_step(elses_system s, double* forces_dev, cudaStream_t st) {
-    TRY(clear_status(s, st));
-    const bool stored = !s->p.two_pass;
-    for (int b = 0; b < s->n; b += s->batch_atoms) {
-        const int e = std::min(s->n, b + s->batch_atoms);
-        double *V = nullptr, *UP = nullptr;
-        int v0 = 0, u0 = 0;
-        TRY(run_batch(s, b, e, stored, &V, &v0, &UP, &u0, st, stored, false));
-    }
-    s->atom_done.assign(s->n, 1);
-    s->atoms_done = s->n;
-    ReduceArgs r = reduce_args(s);
-    s->tic(T_BISECT, st);
-    bisect_init(r, st);
-    for (int it = 0; it < s->p.max_bisect; ++it) bisect_step(r, st);
-    s->toc(st);
-    s->stats.launches += 3 + s->p.max_bisect;
-    const double* mu_dev = (const double*)((const char*)s->bstate.p + offsetof(BisectState, mu));
-    TRY(density_impl(s, 0.0, s->rho.p, s->rhoE.p, st, mu_dev));
-    s->tic(T_BISECT, st);
-    scalars_at_state(r, st);
-    s->toc(st);
-    s->stats.launches++;
-    if (forces_dev) {
-        const double* gh = s->rho.p;
-        const double* gs = s->rhoE.p;
-        if (s->p.force_mode == 1) {
-            TRY(adjoint_impl(s, 0.0, 0, s->n, s->adjH.p, s->adjS.p, -1.0, st, mu_dev));
-            gh = s->adjH.p;
-            gs = s->adjS.p;
-        }
-        s->tic(T_FORCE, st);
-        forces(s->pos.p, s->n, s->box, s->skd, s->row_ptr.p, s->col_idx.p, s->row_of.p, s->tmap.p, s->nnzb,
-               gh, gs, s->gblock.p, forces_dev, st);
-        s->toc(st);
-        s->stats.launches += 2;
-    }
-    return 0;
-}
-
-// What a captured step depends on besides device data: the buffers (allocation epoch), the
-// forces output, the parameters and the Krylov launch plan.
-std::vector<long long> graph_key(elses_system s, const double* forces_dev) {
-    std::vector<long long> k = {(long long)g_alloc_epoch, (long long)(uintptr_t)forces_dev, s->n, s->nnzb,
-                                s->nu_max, s->na_max, s->batch_atoms, s->user_hs ? 1 : 0, s->max_nb,
-                                s->max_cl, s->deg_cap};
-    auto add_bytes = [&k](const void* src, size_t bytes) {
-        std::vector<long long> w((bytes + 7) / 8, 0);
-        std::memcpy(w.data(), src, bytes);
-        k.insert(k.end(), w.begin(), w.end());
-    };
-    add_bytes(&s->p, sizeof(elses_params));
-    add_bytes(s->box, sizeof(s->box));
-    add_bytes(&s->skd, sizeof(s->skd));
-    for (int b = 0; b < s->n; b += s->batch_atoms) k.push_back(s->h_row_ptr[b]);   // batch pattern offsets
-    for (const auto& L : s->k3_launches) {
-        k.insert(k.end(), {L.batch_begin, L.batch_end, L.item_begin, L.item_count, L.na, L.grid, L.bps,
-                           (long long)L.scratch_off});
-    }
-    return k;
-}
-
-int capture_step(elses_system s, double* forces_dev) {
-    s->drop_graph();
-    if (!s->gstream) CUDA_TRY(cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking));
-    if (!s->side) {   // the second stream and its events exist before the capture
-        TRY(fork_side(s, s->gstream));
-        TRY(join_side(s, s->gstream));
-        CUDA_TRY(cudaStreamSynchronize(s->gstream));
-    }
-    const long long l0 = s->stats.launches, c0 = s->stats.columns, k0 = s->stats.krylov_launches;
-    CUDA_TRY(cudaStreamBeginCapture(s->gstream, cudaStreamCaptureModeRelaxed));
-    s->capturing = true;
-    int rc = enqueue_step(s, forces_dev, s->gstream);
-    s->capturing = false;
-    cudaGraph_t g = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(s->gstream, &g);
-    s->graph_launches = s->stats.launches - l0;
-    s->graph_krylov = s->stats.krylov_launches - k0;
-    s->graph_columns = s->stats.columns - c0;
-    s->stats.launches = l0;            // counted at every replay
-    s->stats.columns = c0;
-    s->stats.krylov_launches = k0;
-    if (rc >= 0 && ce != cudaSuccess) rc = fail(ELSES_ERR_CUDA, "stream capture: %s", cudaGetErrorString(ce));
-    if (rc >= 0 && cudaGraphInstantiate(&s->graph_exec, g, 0) != cudaSuccess) {
-        s->graph_exec = nullptr;
-        rc = fail(ELSES_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(cudaGetLastError()));
-    }
-    if (g) cudaGraphDestroy(g);
-    if (rc < 0) s->drop_graph();
-    return rc;
-}
-
-// The graph form: the first call with a new plan runs the eager path (and checks it), the next
-// captures the step, later calls replay it; one host synchronisation per call.
-int energy_force_graph(elses_system s, double* mu_host, double* e_band_host, double* f_free_host,
-                       double* forces_dev, cudaStream_t st) {
-    if (!s->graph_exec || graph_key(s, forces_dev) != s->graph_key) {
-        if (graph_key(s, forces_dev) != s->graph_key) {
-            s->drop_graph();
-            const int rc = energy_force_eager(s, mu_host, e_band_host, f_free_host, forces_dev, st);
-            if (rc >= 0) s->graph_key = graph_key(s, forces_dev);
-            return rc;
-        }
-        CUDA_TRY(cudaStreamSynchronize(st));   // the capture only records; nothing runs
-        TRY(capture_step(s, forces_dev));
-    }
-    CUDA_TRY(cudaGraphLaunch(s->graph_exec, st));
-    s->stats.launches += s->graph_launches;
-    s->stats.krylov_launches += s->graph_krylov;
-    s->stats.columns += s->graph_columns;
-    s->have_rho = true;
-    BisectState h{};
-    CUDA_TRY(cudaMemcpyAsync(&h, s->bstate.p, sizeof h, cudaMemcpyDeviceToHost, st));
-    const int rc = check_status(s, st);
-    s->collect_graph();
-    s->stats.bisect_steps = h.iter;
-    if (h.status & DEV_NONFINITE) return fail(ELSES_ERR_NONFINITE, "non-finite poles");
-    if (h.status & DEV_NO_BRACKET)
-        return fail(ELSES_ERR_NO_BRACKET, "N(lo)=%.17g N(hi)=%.17g do not bracket N_e=%.17g", h.n_lo, h.n_hi,
-                    s->p.n_electrons);
-    if (rc < 0) return rc;
-    s->mu = h.mu;
-    s->have_mu = true;
-    if (mu_host) *mu_host = h.mu;
-    if (e_band_host) *e_band_host = h.e_band;
-    if (f_free_host) *f_free_host = h.omega + h.mu * s->p.n_electrons;
-    return rc;
-}
-
-}  // namespace
-
 int elses_energy_force(elses_system s, double* mu_host, double* e_band_host, double* f_free_host,
                        double* forces_dev, void* stream) {
     TRY(check_built(s));
@@ -1392,31 +941,6 @@ int elses_energy_force(elses_system s, double* mu_host, double* e_band_host, dou
     if (forces_dev && s->user_hs) return fail(ELSES_ERR_STATE, "forces need the Slater-Koster H, S");
     if (s->p.graph) return energy_force_graph(s, mu_host, e_band_host, f_free_host, forces_dev, st);
     return energy_force_eager(s, mu_host, e_band_host, f_free_host, forces_dev, st);
-}
-
-int elses_autotune(elses_system s, int run, int max_classes, int* classes_out, int* n_host, void* stream) {
-    TRY(check_built(s));
-    if (max_classes < 0 || (max_classes > 0 && !classes_out)) return fail(ELSES_ERR_ARG, "bad class output");
-    if (run) {
-        if (s->p.k3_ctas_per_sm > 0) return fail(ELSES_ERR_STATE, "k3_ctas_per_sm fixes the launch shape");
-        TRY(autotune_impl(s, (cudaStream_t)stream));
-    }
-    int n = 0;
-    std::vector<char> seen(s->na_max / 16 + 1, 0);
-    for (const auto& L : s->k3_launches) {   // every class once, largest first within a batch
-        if (seen[L.key]) continue;
-        seen[L.key] = 1;
-        if (n < max_classes) {
-            const int key = L.key;
-            const bool by_atom = key < (int)s->tuned_order.size() && s->tuned_order[key] == 2;
-            classes_out[3 * n] = L.na;
-            classes_out[3 * n + 1] = L.bps;
-            classes_out[3 * n + 2] = s->p.schedule != 1 ? 0 : by_atom ? 2 : 1;
-        }
-        ++n;
-    }
-    if (n_host) *n_host = n;
-    return ELSES_OK;
 }
 
 int elses_cohp_spectrum(elses_system s, int n_z, const double* z_host, double* C_dev, double* Csig_dev,
