@@ -6,12 +6,13 @@
 // allocated at run time. The array is part of the library image: every GPU that loads the
 // library holds it until the process exits.
 //
-// Its address is looked up once per device (cudaGetSymbolAddress with that device current) on
-// the first call made on that device; that first call should therefore come before any stream
-// capture. Every call shares the one array: calls whose work overlaps on the GPU (different
-// streams, or several host threads) race on it and must be serialised by the caller.
-#include <mutex>
-
+// Its address is looked up (cudaGetSymbolAddress with the device current) at the start of every
+// call, not cached: after cudaDeviceReset the next context loads the module again and the array
+// may move, and a cached address would then point at freed memory. The lookup allocates nothing;
+// on the first call on a device it may load the library's device code, so that first call should
+// come before any stream capture. Every call shares the one array: calls whose work overlaps on
+// the GPU (different streams, or several host threads) race on it and must be serialised by the
+// caller.
 #include "internal.h"
 
 namespace elses {
@@ -19,28 +20,19 @@ namespace {
 
 constexpr int kStaticMaxBlocks = 4096;                          // reduction blocks supported
 constexpr size_t kStatePart = 4 * (size_t)kStaticMaxBlocks;      // partials: [block][4]
+constexpr size_t kStateSlot = 24;                               // bracket state, in doubles
 constexpr size_t kStaticDoubles = kStatePart + 32;              // + bracket state + ticket
+static_assert(sizeof(BisectState) <= kStateSlot * sizeof(double), "bracket state outgrew its slot");
+static_assert(kStateSlot + 1 <= kStaticDoubles - kStatePart, "no room for the ticket");
 
 static __device__ __align__(256) double g_static_scratch[kStaticDoubles];
 
-constexpr int kMaxDevices = 128;
-std::mutex g_setup_mutex;
-double* g_device_scratch[kMaxDevices] = {};
-
-// Device address of the static scratch on the current device (looked up on first use).
+// Device address of the static scratch on the current device (the device must be current).
 cudaError_t static_scratch(double** out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_device_scratch[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess) return e;
-        g_device_scratch[dev] = static_cast<double*>(p);
-    }
-    *out = g_device_scratch[dev];
+    *out = static_cast<double*>(p);
     return cudaSuccess;
 }
 
@@ -85,7 +77,7 @@ extern "C" int elses_find_mu_static(int n_columns, int nu_max, const double* eps
     r.max_iter = max_bisect > 0 ? max_bisect : 100;
     r.partials = base;
     r.state = reinterpret_cast<BisectState*>(base + kStatePart);
-    r.ticket = reinterpret_cast<unsigned*>(base + kStatePart + 24);
+    r.ticket = reinterpret_cast<unsigned*>(base + kStatePart + kStateSlot);
     // the ticket must start at zero; the state is written by the bracket kernel
     e = cudaMemsetAsync(r.ticket, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return report_error(ELSES_ERR_CUDA, "%s", cudaGetErrorString(e));

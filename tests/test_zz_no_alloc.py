@@ -25,11 +25,13 @@ def test_find_mu_static_matches_find_mu_on_two_calls(name):
     e_ref = s.energies(mu_ref)["E_band"]
     sp = s.spectra()
     torch.cuda.synchronize()
-    for call in range(2):
+    side = torch.cuda.Stream()
+    results = []
+    for call, stream in enumerate((None, None, side)):
         free_before = torch.cuda.mem_get_info()[0]
         mu, n, e = eg.find_mu_static(sp["eps"], sp["c"], sp["d"], sp["nu_eff"], w.kT,
-                                     w.n_electrons, g=sp["g"])
-        if call == 1:       # after the first call's one-time address lookup nothing moves
+                                     w.n_electrons, g=sp["g"], stream=stream)
+        if call >= 1:       # after the first call (which may load the device code) nothing moves
             assert torch.cuda.mem_get_info()[0] == free_before
         # two bisections with mu_tol = 1e-13 end within half a bracket of their own crossing
         # of N_e; the crossings differ by the rounding of two summation orders (the static
@@ -37,6 +39,10 @@ def test_find_mu_static_matches_find_mu_on_two_calls(name):
         assert abs(mu - mu_ref) <= 3e-13
         assert abs(n - n_ref) <= 1e-8
         assert abs(e - e_ref) / w.n_atoms <= gu.E_TOL_PER_ATOM
+        results.append((mu, n, e))
+    # the same kernels in the same order on the same data: equal bit for bit on every call and
+    # stream (the shared array is reset where it must start at zero)
+    assert results[0] == results[1] == results[2]
     s.close()
 
 
