@@ -38,7 +38,9 @@ extern "C" {
 #define ELSES_OK                  0
 #define ELSES_WARN_BREAKDOWN      1   /* some column stopped early (invariant subspace) */
 #define ELSES_ERR_ARG            -1   /* bad argument (NULL, size, box too small, ...)   */
-#define ELSES_ERR_NOT_SPD        -2   /* a projected overlap S' failed its Cholesky      */
+#define ELSES_ERR_NOT_SPD        -2   /* S is not positive definite: a Krylov vector w
+                                         with w^T S w < -(breakdown_tol ||H u_n||)^2, or a
+                                         projected overlap S' that fails its Cholesky     */
 #define ELSES_ERR_NONFINITE      -3   /* NaN or Inf in an input or a result              */
 #define ELSES_ERR_NO_BRACKET     -4   /* electron count not bracketed by the spectrum    */
 #define ELSES_ERR_TIMEOUT        -5   /* a bounded device-side iteration ran out         */
@@ -105,6 +107,8 @@ typedef struct elses_params {
                                clusters would leave the last slot of 32 atoms at most half full;
                                forces from the density matrix and per-column spaces only),
                                32 = one warp per column always                                   */
+    int    max_qr_sweeps;   /* cap on the implicit-shift QR sweeps of one projected eigenproblem
+                               (0: 30 nu); a column that needs more sets ELSES_ERR_TIMEOUT       */
 } elses_params;
 
 /* Counters and event timings of the calls since the last build (timing = 1 for the times). */
@@ -264,15 +268,19 @@ int elses_probe_fp64(double* gflops_host, void* stream);
 /* Allocation-free chemical-potential bisection. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory when they need mu -- an application
  * whose own allocator has already reserved the device memory, or a loop in which allocation
- * (and the synchronisation it implies) is not allowed. It runs the same bisection as
- * elses_find_mu (same kernels, same result) on caller-owned spectra in the layout of
+ * (and the synchronisation it implies) is not allowed. It runs the bisection kernels of
+ * elses_find_mu without their kept-pole window (every pole is summed at every step, in another
+ * order), so mu agrees with elses_find_mu to rounding (a few 1e-13 eV), on caller-owned spectra
+ * in the layout of
  * elses_get_spectra: eps, c, d, g double[n_columns][nu_max] and nu_eff int[n_columns] on the
  * device (g may be NULL unless e_band_host is requested); mu_tol <= 0 and max_bisect <= 0 take
  * the defaults 1e-13 and 100. It calls no cudaMalloc / cudaFree: its scratch (block partial sums,
  * bracket state, ticket) is one static device array of 4096 x 4 + 32 doubles (about 131 KB)
  * that every GPU loading the library holds until exit; a device that would need more than
- * 4096 reduction blocks is rejected with ELSES_ERR_CAPACITY. The first call on a device looks
- * the array's address up (make that first call before any stream capture). All calls share the
+ * 4096 reduction blocks is rejected with ELSES_ERR_CAPACITY. Every call looks the array's
+ * address up on the current device (nothing is cached, so a context re-created after
+ * cudaDeviceReset is followed); the first call on a device may load the library's device code,
+ * so make that first call before any stream capture. All calls share the
  * array and it keeps the last call's contents: calls that overlap on the GPU race and must be
  * serialised by the caller. Synchronises `stream` before returning. */
 int elses_find_mu_static(int n_columns, int nu_max, const double* eps_dev, const double* c_dev,

@@ -14,6 +14,7 @@ Arnoldi, lag b = number of starting vectors):
         while the basis has fewer than nu vectors:
             w = HU[:, m]; two CGS passes in the S inner product against every basis vector so far
             (h = SU^T w, w -= U h); Sw = S_C w; beta = sqrt(w^T Sw);
+            w^T Sw < -(1e-12 ||HU[:, m]||_2)^2 means S is not positive definite (error);
             beta <= 1e-12 ||HU[:, m]||_2 ends the extension (nu_eff = the basis size);
             u_{m+b} = w / beta
     and every basis vector u gets SU = S_C u (by a product) when it is made.
@@ -66,8 +67,12 @@ def block_arnoldi(Hc, Sc, jls, nu, breakdown_tol=BREAKDOWN_TOL):
                 h = SU[:, :n].T @ w
                 w = w - U[:, :n] @ h
             Sw = Sc @ w
-            beta = np.sqrt(max(float(w @ Sw), 0.0))
-            if beta <= breakdown_tol * np.linalg.norm(HU[:, m]):
+            wSw = float(w @ Sw)
+            hnorm = np.linalg.norm(HU[:, m])
+            if wSw < -(breakdown_tol * hnorm) ** 2:
+                raise krylov.NotPositiveDefinite(f"w^T S w = {wSw:.3e} < 0")
+            beta = np.sqrt(max(wSw, 0.0))
+            if beta <= breakdown_tol * hnorm:
                 extend = False
                 nu_eff = n
             else:

@@ -13,6 +13,7 @@ K_nu(H_C, e_j) of the cluster matrices, with a basis orthonormal in the S inner 
         two classical Gram-Schmidt passes in the S inner product:
             h = SU[:, 1..n]^T w ;  w = w - U[:, 1..n] h
         Sw = S_C w ;  beta = sqrt(w^T Sw)
+        if w^T Sw < -(1e-12 * ||HU[:, n]||_2)^2 : S is not positive definite (error)
         if beta <= 1e-12 * ||HU[:, n]||_2 : stop (invariant subspace, nu_eff = n)
         u_{n+1} = w / beta
     H' = U^T HU,  S' = U^T SU, each symmetrised as (X + X^T)/2
@@ -37,7 +38,8 @@ BREAKDOWN_TOL = 1e-12
 
 
 class NotPositiveDefinite(RuntimeError):
-    """The projected overlap S' failed its Cholesky factorisation."""
+    """S is not positive definite, against the premise of Eq. 1: a Krylov vector w has
+    w^T S w < 0 beyond rounding, or the projected overlap S' failed its Cholesky factorisation."""
 
 
 @dataclasses.dataclass
@@ -68,8 +70,12 @@ def arnoldi_column(Hc, Sc, jl, nu, breakdown_tol=BREAKDOWN_TOL):
             h = SU[:, :n + 1].T @ w
             w = w - U[:, :n + 1] @ h
         Sw = Sc @ w
-        beta = np.sqrt(max(float(w @ Sw), 0.0))
-        if beta <= breakdown_tol * np.linalg.norm(HU[:, n]):
+        wSw = float(w @ Sw)
+        hnorm = np.linalg.norm(HU[:, n])
+        if wSw < -(breakdown_tol * hnorm) ** 2:
+            raise NotPositiveDefinite(f"w^T S w = {wSw:.3e} < 0 at Krylov step {n + 1}")
+        beta = np.sqrt(max(wSw, 0.0))
+        if beta <= breakdown_tol * hnorm:
             nu_eff = n + 1
             break
         U[:, n + 1] = w / beta

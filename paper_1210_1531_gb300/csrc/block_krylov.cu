@@ -127,8 +127,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_block_krylov(const KrylovArgs a
                     part = fma4(w0, w1, s0, s1, part);
                 }
                 const double beta2 = warp_sum(part);
-                if (!(beta2 > 0.0)) {
-                    if (lane == 0) { flag(a.status, DEV_ARG); sh_bad = 1; }
+                if (!(beta2 > 0.0)) {   // NaN, or a start vector of S-norm <= 0: S is not SPD
+                    if (lane == 0) { flag(a.status, beta2 == beta2 ? DEV_NOT_SPD : DEV_NONFINITE); sh_bad = 1; }
                 } else {
                     const double inv = 1.0 / sqrt(beta2);
                     for (int sl = 0; sl < NS; ++sl) {
@@ -311,6 +311,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_block_krylov(const KrylovArgs a
                     const double beta = sqrt(fmax(beta2, 0.0));
                     if (!(beta2 == beta2)) {
                         if (lane == 0) { flag(a.status, DEV_NONFINITE); sh_ext = 0; sh_nueff = t; }
+                    } else if (beta2 < -(a.breakdown_tol * a.breakdown_tol) * sh_hh[warp]) {   // S not SPD
+                        if (lane == 0) { flag(a.status, DEV_NOT_SPD); sh_ext = 0; sh_nueff = t; }
                     } else if (beta <= a.breakdown_tol * sqrt(sh_hh[warp])) {
                         if (lane == 0) { sh_ext = 0; sh_nueff = t; }
                     } else {

@@ -139,6 +139,7 @@ struct EigArgs {
     double* g;
     double* V;              // [batch col][nu_max*nu_max] (row n = Krylov index, col k = eigen index)
     int* status;
+    int max_sweeps;         // QR sweeps allowed per column (0: 30 nu; DEV_TIMEOUT beyond)
 };
 __host__ __device__ size_t eig_tri_doubles(int nm);
 __host__ __device__ size_t eig_fac_doubles(int nm);

@@ -463,6 +463,11 @@ __device__ __forceinline__ int column_forward(const KrylovArgs& a, const Cluster
             nu_eff = n + 1;
             break;
         }
+        if (beta2 < -(a.breakdown_tol * a.breakdown_tol) * hh) {   // w^T S w < 0: S is not SPD
+            if (lane == 0) flag(a.status, DEV_NOT_SPD);
+            nu_eff = n + 1;
+            break;
+        }
         const double beta = sqrt(fmax(beta2, 0.0));
         if (beta <= a.breakdown_tol * sqrt(hh)) {
             nu_eff = n + 1;
@@ -874,6 +879,11 @@ __device__ __forceinline__ int column_forward_w(const KrylovArgs& a, const Clust
         const double beta2 = group_sum<W>(part);
         if (!(beta2 == beta2)) {   // NaN
             if (lane == 0) flag(a.status, DEV_NONFINITE);
+            nu_eff = n + 1;
+            break;
+        }
+        if (beta2 < -(a.breakdown_tol * a.breakdown_tol) * hh) {   // w^T S w < 0: S is not SPD
+            if (lane == 0) flag(a.status, DEV_NOT_SPD);
             nu_eff = n + 1;
             break;
         }

@@ -266,6 +266,7 @@ __global__ void __launch_bounds__(kChaseThreads) k_eig_chase(const EigArgs a) {
     bool ok = true;
     const double eps = 2.220446049250313e-16;
     int hi = nu - 1, sweeps = 0;
+    const int max_sweeps = a.max_sweeps > 0 ? a.max_sweeps : 30 * nu;
     while (hi > 0 && ok) {
         if (fabs(E[hi - 1]) <= eps * (fabs(D[hi - 1]) + fabs(D[hi]))) {
             E[hi - 1] = 0.0;
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(kChaseThreads) k_eig_chase(const EigArgs a) {
         int lo = hi - 1;
         while (lo > 0 && fabs(E[lo - 1]) > eps * (fabs(D[lo - 1]) + fabs(D[lo]))) --lo;
         if (lo > 0) E[lo - 1] = 0.0;
-        if (++sweeps > 30 * nu || nrot + (hi - lo) > cap) {
+        if (++sweeps > max_sweeps || nrot + (hi - lo) > cap) {
             ok = false;
             break;
         }

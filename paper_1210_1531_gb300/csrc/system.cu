@@ -310,6 +310,7 @@ EigArgs eig_args(elses_system s, int b, int e, double* V) {
     ea.g = s->gg.p;
     ea.V = V;
     ea.status = s->counters.p + 2;
+    ea.max_sweeps = s->p.max_qr_sweeps;   // 0: 30 nu of the column
     return ea;
 }
 
@@ -685,6 +686,7 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
     if (p.krylov_block < 0 || p.krylov_block > 1) return fail(ELSES_ERR_ARG, "krylov_block must be 0 or 1");
     if (p.batch_atoms < 0) return fail(ELSES_ERR_ARG, "batch_atoms must be >= 0");
     if (p.k3_lanes != 0 && p.k3_lanes != 32) return fail(ELSES_ERR_ARG, "k3_lanes must be 0 or 32");
+    if (p.max_qr_sweeps < 0) return fail(ELSES_ERR_ARG, "max_qr_sweeps must be >= 0");
     if (p.krylov_block) {
         if (p.nu < 4) return fail(ELSES_ERR_ARG, "a block space needs nu >= 4");
         for (int c = 0; c < p.n_classes; ++c)

@@ -80,3 +80,43 @@ def test_block_space_arguments(eg):
     with pytest.raises(eg.ElsesError) as err:
         eg.System(pos, w.box, w.sk, 0.0, 16, 0.1, w.n_electrons, krylov_block=True, exact_forces=True)
     assert err.value.code == -8
+
+
+def test_indefinite_overlap_is_not_spd(eg):
+    """Eq. 1 needs S positive definite. User values with the off-site overlap scaled by 3 make S
+    indefinite (lambda_min < 0, library eigvalsh): the Krylov build meets w^T S w < 0 and
+    elses_green_columns reports ELSES_ERR_NOT_SPD instead of a silently truncated space; the
+    oracle raises on the same input."""
+    from oracle import hamiltonian, krylov
+    w = wl.make("diamond_64")
+    s = eg.system_for(w)
+    H, S = s.hs()
+    rp, ci = (gu.to_np(t) for t in s.pattern())
+    onsite = torch.tensor(np.repeat(np.arange(w.n_atoms), np.diff(rp)) == ci, device="cuda")
+    eye = torch.eye(4, dtype=torch.float64, device="cuda")
+    S3 = torch.where(onsite[:, None, None], S, 3.0 * S)
+    S3_dense = hamiltonian.bsr_to_dense(rp, ci, gu.to_np(S3))
+    assert np.linalg.eigvalsh(S3_dense).min() < -0.1
+    assert torch.equal(S[onsite], eye.expand(int(onsite.sum()), 4, 4))
+    with pytest.raises(krylov.NotPositiveDefinite):
+        krylov.arnoldi_column(hamiltonian.bsr_to_dense(rp, ci, gu.to_np(H)), S3_dense, 0, w.nu)
+    s.set_hs(H, S3)
+    with pytest.raises(eg.ElsesError) as err:
+        s.green_columns()
+    assert err.value.code == -2
+    s.set_hs(H, S)                                        # the valid overlap builds again
+    assert s.green_columns() == 0
+
+
+def test_qr_sweep_cap_reports_timeout(eg):
+    """The implicit-shift QR chase of the projected eigenproblem is a bounded loop: with its cap
+    at one sweep per column (a 30 x 30 tridiagonal needs about two per eigenvalue) the columns
+    run out and elses_green_columns returns ELSES_ERR_TIMEOUT; nothing waits or spins. With the
+    default cap (30 nu) the same system solves."""
+    w = wl.make("diamond_64")
+    s = eg.system_for(w, max_qr_sweeps=1)
+    with pytest.raises(eg.ElsesError) as err:
+        s.green_columns()
+    assert err.value.code == -5
+    s.close()
+    assert eg.system_for(w).green_columns() == 0

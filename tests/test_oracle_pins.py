@@ -125,6 +125,20 @@ def test_s_positive_definite_larger_systems():
     assert lam > 0.1
 
 
+def test_indefinite_overlap_is_reported_not_truncated(diamond64):
+    """Eq. 1 needs S positive definite. Scaling the off-site overlap by 3 makes S indefinite
+    (library eigvalsh: lambda_min < 0); the Krylov build then meets a vector with w^T S w < 0 and
+    reports it instead of treating it as a breakdown. The unscaled S (lambda_min > 0) builds."""
+    H, S = hamiltonian.dense(diamond64.pos, diamond64.box, diamond64.sk)
+    I = np.eye(len(S))
+    S3 = I + 3.0 * (S - I)
+    assert np.linalg.eigvalsh(S3).min() < -0.1 and np.linalg.eigvalsh(S).min() > 0.1
+    for j in (0, 77, 201):
+        with pytest.raises(krylov.NotPositiveDefinite):
+            krylov.arnoldi_column(H, S3, j, 30)
+        assert krylov.arnoldi_column(H, S, j, 30).nu_eff == 30
+
+
 # ----------------------------------------------------------------------------- exact path
 def test_exact_matches_library_generalized_eigh(diamond64):
     H, S = hamiltonian.dense(diamond64.pos, diamond64.box, diamond64.sk)
