@@ -273,6 +273,8 @@ def make(name: str) -> Workload:
     diamond_64       64-atom diamond (2x2x2 cells), sigma 0.05 A, cluster = whole system, nu 30
     diamond_4096     4096-atom diamond (8x8x8 cells), sigma 0.1 A, cluster radius 6 A, nu 30
     composite_32768  32768-atom graphite + diamond grains, cluster radius 6 A, nu 20/30/40 by size
+                     (<= 100 cluster atoms: graphite interior; <= 140: grain boundaries; larger:
+                     diamond grain interior)
     amorphous_1m     1,048,576-atom dense disordered carbon (3.0 g/cm3), cluster radius 5 A, nu 30
     """
     sk = sk_params()
@@ -285,7 +287,7 @@ def make(name: str) -> Workload:
     if name == "composite_32768":
         pos, box, _ = composite(32768)
         return Workload(name, pos, box, sk, r_cluster=6.0, nu=30,
-                        nu_classes=((100, 20), (200, 30), (1 << 30, 40)))
+                        nu_classes=((100, 20), (140, 30), (1 << 30, 40)))
     if name == "amorphous_1m":
         pos, box = amorphous()
         return Workload(name, pos, box, sk, r_cluster=5.0, nu=30)
