@@ -89,6 +89,7 @@ int capture_step(elses_system s, double* forces_dev) {
     s->capturing = true;
     int rc = enqueue_step(s, forces_dev, s->gstream);
     s->capturing = false;
+    s->graph_v_lazy = s->v_lazy;
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(s->gstream, &g);
     s->graph_launches = s->stats.launches - l0;
@@ -125,6 +126,11 @@ int energy_force_graph(elses_system s, double* mu_host, double* e_band_host, dou
     s->stats.launches += s->graph_launches;
     s->stats.krylov_launches += s->graph_krylov;
     s->stats.columns += s->graph_columns;
+    // the host-side state the captured step leaves (a rebuild since the capture reset it): every
+    // column computed, V formed or left to the kept factors as at the capture
+    s->atom_done.assign(s->n, 1);
+    s->atoms_done = s->n;
+    s->v_lazy = s->graph_v_lazy;
     s->have_rho = true;
     BisectState h{};
     CUDA_TRY(cudaMemcpyAsync(&h, s->bstate.p, sizeof h, cudaMemcpyDeviceToHost, st));

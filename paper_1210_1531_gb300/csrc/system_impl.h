@@ -105,6 +105,7 @@ struct elses_system_s {
     DevBuf<int> nu_eff, order;
     DevBuf<double> rho, rhoE, gblock;
     DevBuf<double> ascratch, adjH, adjS;   // exact-gradient scratch and its pattern gradients
+    DevBuf<unsigned long long> adj_acc;    // their exact fixed-point sums (AdjointArgs::acc)
     DevBuf<double> bstore;                 // per-column bases kept for the exact gradient
     size_t bstride = 0, bvec = 0;
     bool use_store = false;
@@ -176,6 +177,7 @@ struct elses_system_s {
     cudaStream_t gstream = nullptr;       // capture stream (the legacy stream cannot capture)
     std::vector<long long> graph_key;
     long long graph_launches = 0, graph_krylov = 0, graph_columns = 0;
+    bool graph_v_lazy = false;            // v_lazy as the captured step leaves it
     void drop_graph() {
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         graph_exec = nullptr;
