@@ -9,7 +9,14 @@ Positions are resident in HBM when the timed region starts (value); the e2e figu
 same step through the public API from pinned host positions, with the host->device copy of the
 positions and the device->host read of forces and energies inside the timed region.
 
-    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+After the timed region the oracle runs on every host core (the cpu_baseline leg): on all 16384
+columns of that system at the GPU's chemical potential, timed, and its rho and rhoE columns are
+compared with the library's element by element (max_drho, max_drhoE; the run fails above the
+1e-10 gate). The same is done, on seeded column samples, for the two further systems reported
+beside it: the 32768-atom sp2-sp3 composite (uneven clusters, nu 20/30/40 by size) and the
+10^6-atom dense carbon (streamed batches).
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--no-extra]
 
 With N > 1 (torchrun) each rank runs an independent replica (the path has no exchange step on
 one system); value is the total columns of all ranks / the slowest rank's time.
@@ -35,13 +42,15 @@ DESCRIPTION = {"diamond_4096": "disordered diamond (8x8x8 cells, sigma 0.1 A)",
                "amorphous_1m": "dense disordered carbon (3.0 g/cm3, sigma 0.3 A)",
                "diamond_64": "disordered diamond (2x2x2 cells, sigma 0.05 A)"}
 FP64_NOMINAL_GFLOPS = 152 * 2 * 2 * 2.07     # SMs x FP64 FMA/clk/SM x 2 flops x GHz
-# DRAM bytes (read + write) of one k_krylov launch on the 4096-atom step, from the ncu capture in
-# profiles/k_krylov_diamond4096.md; valid only while krylov.cu is the source that was captured.
-# DRAM bytes (read + write) of the k_krylov launches of one 4096-atom step, from one ncu capture
-# of the source whose sha256 prefix (krylov.cu + krylov.cuh) is given; reported per launch, null
-# once that source changes
+RHO_GATE = 1e-10                             # |delta rho_ij| against the same-algorithm oracle
+# DRAM bytes (read + write) of the k_krylov launches of one 4096-atom step from one ncu capture,
+# valid for the Krylov source whose sha256 prefix (krylov.cu + krylov.cuh) is given; reported
+# per launch, and null once that source changes
 KRYLOV_TRAFFIC = {"krylov_sha256_prefix": "1dea01a43985331b", "bytes_per_step": 176.29e9,
                   "launches_per_step": 2}
+# further systems timed after the main one: (steps, warm-up steps, plain-form steps, plain-form
+# warm-up steps, sampled columns checked against the oracle)
+EXTRA = {"composite_32768": (3, 2, 3, 1, 256), "amorphous_1m": (1, 1, 1, 0, 128)}
 
 
 def parse():
@@ -52,46 +61,45 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=2048)
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="columns of the main system the oracle runs on (0: all of them)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the composite and 10^6-atom systems reported beside the main one")
     ap.add_argument("--k3-ctas", type=int, default=0, help="Krylov CTAs per SM (0: as many as fit)")
     ap.add_argument("--no-exact", action="store_true",
                     help="skip the energy + exact-force step (gradient through the truncated Krylov build)")
     return ap.parse_args()
 
 
-# ----------------------------------------------------------------------------- oracle timing
+# ----------------------------------------------------------------------------- oracle (cpu_baseline leg)
 def _oracle_worker(args):
-    name, cols = args
-    os.environ["OMP_NUM_THREADS"] = "1"
-    import workloads as wl
+    """Oracle columns of one chunk at mu: timed; slim records (pattern, rho, rhoE) returned."""
+    w, cols, mu = args
     from oracle import pipeline
-    w = wl.make(name)
     t0 = time.perf_counter()
-    res = pipeline.columns(w, cols)
-    mu = 0.0
-    for c in res:
-        pipeline.rho_column(c, mu, w.kT)
-    return time.perf_counter() - t0, len(res)
+    out = []
+    for c in pipeline.columns(w, cols):
+        r, rE = pipeline.rho_column(c, mu, w.kT)
+        out.append((c.j, c.pattern, r, rE))
+    return time.perf_counter() - t0, out
 
 
-def oracle_columns_per_s(name: str, n_sample: int):
-    """The oracle as it stands on a bounded seeded sample of columns, on every host core."""
+def oracle_columns(w, cols, mu):
+    """The oracle as it stands on the given columns of workload w at chemical potential mu, one
+    spawned process per host core (spawned, not forked: this process holds a CUDA context).
+    Returns (columns/s over the timed wall of the chunks, cores used, {j: (pattern, rho, rhoE)})."""
     import multiprocessing as mp
 
-    import workloads as wl
-    w = wl.make(name)
-    cols = wl.sample_columns(4 * w.n_atoms, n_sample)
-    cores = os.cpu_count() or 1
-    chunks = [(name, cols[i::cores]) for i in range(cores) if len(cols[i::cores])]
-    ctx = mp.get_context("spawn")
+    cores = max(1, min(os.cpu_count() or 1, len(cols)))
+    chunks = [cols[i::cores] for i in range(cores)]
     env_prev = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
     os.environ["OMP_NUM_THREADS"] = "1"
     os.environ["OPENBLAS_NUM_THREADS"] = "1"
     try:
-        with ctx.Pool(len(chunks)) as pool:
-            pool.map(_oracle_worker, [(name, c[:1]) for _, c in chunks])      # import / setup
+        with mp.get_context("spawn").Pool(cores) as pool:
+            pool.map(_oracle_worker, [(w, c[:1], mu) for c in chunks])       # import / setup
             t0 = time.perf_counter()
-            out = pool.map(_oracle_worker, chunks)
+            out = pool.map(_oracle_worker, [(w, c, mu) for c in chunks])
             wall = time.perf_counter() - t0
     finally:
         for k, v in env_prev.items():
@@ -99,8 +107,63 @@ def oracle_columns_per_s(name: str, n_sample: int):
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
-    n = sum(o[1] for o in out)
-    return n / wall, len(chunks), f"{n} seeded columns of {name} (Krylov build, projected eigenproblem, spectra, rho column), one process per core"
+    recs = {int(r[0]): r[1:] for _, part in out for r in part}
+    return len(recs) / wall, cores, recs
+
+
+def _block_ids(row_ptr, col_idx, J, pattern):
+    """Blocks e = (I, J) of the pattern atoms I of atom J's columns."""
+    import numpy as np
+    out = np.empty(len(pattern), dtype=np.int64)
+    for p, I in enumerate(pattern):
+        lo, hi = int(row_ptr[I]), int(row_ptr[I + 1])
+        out[p] = lo + int(np.searchsorted(col_idx[lo:hi], J))
+    return out
+
+
+def gather_plan(row_ptr, col_idx, cols):
+    """Where the pattern rows of the given columns sit in a BSR array [nnzb][4][4] (x[e][a][b] =
+    X_(I,a),(J,b) for e = (I, J)): per column its pattern atoms (row J of the symmetric pattern),
+    and for all columns together the block index e and orbital b of each pattern atom's row."""
+    import numpy as np
+    pats = [col_idx[row_ptr[j // 4]:row_ptr[j // 4 + 1]] for j in cols]
+    ids = [_block_ids(row_ptr, col_idx, j // 4, pt) for j, pt in zip(cols, pats)]
+    e = np.concatenate(ids)
+    b = np.concatenate([np.full(len(i), j % 4) for j, i in zip(cols, ids)])
+    return pats, e, b
+
+
+def split_columns(cols, pats, g, gE):
+    """{j: (pattern atoms, rho (len,4), rhoE (len,4))} from the gathered rows, in plan order."""
+    out, q = {}, 0
+    for j, pt in zip(cols, pats):
+        out[int(j)] = (pt, g[q:q + len(pt)], gE[q:q + len(pt)])
+        q += len(pt)
+    return out
+
+
+def gpu_rho_columns(system, mu, cols):
+    """The library's rho and rhoE (elses_density_matrix) on the pattern rows of the given
+    columns, gathered on the device."""
+    import torch
+    rp, ci = (t.cpu().numpy() for t in system.pattern())
+    rho, rhoE = system.density_matrix(mu)
+    pats, e, b = gather_plan(rp, ci, cols)
+    e, b = torch.as_tensor(e, device="cuda"), torch.as_tensor(b, device="cuda")
+    return split_columns(cols, pats, rho[e, :, b].cpu().numpy(), rhoE[e, :, b].cpu().numpy())
+
+
+def compare_rho(gpu, oracle):
+    """Largest element-wise |delta rho| and |delta rhoE| over the columns (same pattern rows)."""
+    import numpy as np
+    dr = dE = 0.0
+    for j, (pt, r, rE) in oracle.items():
+        gpt, gr, grE = gpu[j]
+        if not np.array_equal(np.asarray(pt), np.asarray(gpt)):
+            return float("inf"), float("inf")
+        dr = max(dr, float(np.abs(gr - r).max()))
+        dE = max(dE, float(np.abs(grE - rE).max()))
+    return dr, dE
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -180,6 +243,122 @@ def krylov_traffic():
     return KRYLOV_TRAFFIC["bytes_per_step"] / KRYLOV_TRAFFIC["launches_per_step"]
 
 
+STAT_KEYS = ("launches", "krylov_launches", "t_krylov_ms", "t_eig_ms", "t_bisect_ms",
+             "t_density_ms", "t_force_ms", "krylov_flops", "t_adjoint_ms", "adjoint_flops")
+PHASES = ("t_krylov_ms", "t_eig_ms", "t_bisect_ms", "t_density_ms", "t_force_ms")
+
+
+class Runner:
+    """One workload on the current device: Systems of it, and their timed energy + force steps
+    (each step: rebuild at the resident positions, then elses_energy_force)."""
+
+    def __init__(self, eg, w, k3_ctas, stream, flush):
+        import torch
+        self.eg, self.w, self.k3_ctas, self.stream, self.flush = eg, w, k3_ctas, stream, flush
+        self.pos_dev = torch.tensor(w.pos, dtype=torch.float64, device="cuda")
+        self.forces = torch.empty((w.n_atoms, 3), dtype=torch.float64, device="cuda")
+
+    def make(self, schedule, exact_forces=False, autotune=False, graph=False):
+        w = self.w
+        return self.eg.System(self.pos_dev, w.box, w.sk, w.r_cluster, w.nu, w.kT, w.n_electrons,
+                              nu_classes=w.nu_classes, schedule=schedule, timing=True,
+                              k3_ctas_per_sm=self.k3_ctas, exact_forces=exact_forces,
+                              autotune=autotune and self.k3_ctas == 0, graph=graph)
+
+    def step(self, s):
+        s.rebuild(self.pos_dev)
+        return s.energy_force(self.forces)
+
+    def timed(self, s, k, w_steps, barrier=None):
+        """w_steps untimed steps, then k steps each timed with CUDA events on the stream; the
+        counters of each step (reset by its rebuild) are accumulated."""
+        import torch
+        for _ in range(w_steps):
+            self.step(s)
+        torch.cuda.synchronize()
+        if barrier:
+            barrier()
+            torch.cuda.synchronize()
+        acc = dict.fromkeys(STAT_KEYS, 0.0)
+        times, out = [], None
+        for _ in range(k):
+            self.flush.zero_()                  # L2 flush between timed steps (not timed)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(self.stream)
+            out = self.step(s)
+            b.record(self.stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+            st = s.stats()
+            for key in STAT_KEYS:
+                acc[key] += st[key]
+        torch.cuda.synchronize()
+        if barrier:
+            barrier()
+            torch.cuda.synchronize()
+        acc["bisect_steps"] = s.stats()["bisect_steps"]
+        return times, acc, out
+
+
+def roofline(stats, peak_probe, traffic=None):
+    """Roofline of the dominant kernel (Krylov build + projection) from its event-timed phase and
+    the algorithmic flops the kernel counts per column (formula in include/elses.h, elses_stats)."""
+    k_launch_ms = stats["t_krylov_ms"] / max(1, stats["krylov_launches"])
+    flops_per_launch = stats["krylov_flops"] / max(1.0, stats["krylov_launches"])
+    achieved = flops_per_launch / (k_launch_ms * 1e-3) / 1e9      # GFLOP/s
+    return {"bound": "alu", "kernel": "k_krylov (a3 Krylov build + a4 projection)",
+            "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+            "frac": achieved / FP64_NOMINAL_GFLOPS, "traffic": traffic,
+            "peak_probe": peak_probe, "frac_of_probe": achieved / peak_probe if peak_probe else None,
+            "flops_per_launch": flops_per_launch, "launch_ms": k_launch_ms,
+            "peak_note": "FP64 FMA pipe: 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz (nominal 1.26 TFLOP/s); "
+                         "peak_probe = measured FMA-chain throughput"}
+
+
+def shapes(tuned):
+    return {f"{k}-atom clusters": f"{b} CTAs/SM, queue by {o}" for k, (b, o) in tuned.items()}
+
+
+def extra_record(eg, wl, name, k3_ctas, stream, flush, peak_probe, check):
+    """A further system in the production form against the plain form, with the Krylov roofline
+    and the library's rho on seeded columns checked against the oracle (cpu_baseline leg)."""
+    import numpy as np
+    steps, warm, p_steps, p_warm, n_check = EXTRA[name]
+    w = wl.make(name)
+    M = 4 * w.n_atoms
+    r = Runner(eg, w, k3_ctas, stream, flush)
+    batched = r.make(1, autotune=True, graph=True)
+    tuned = batched.autotune_shapes()
+    times, stats, out = r.timed(batched, steps, warm)
+    ms = sum(times) / len(times)
+    mu = out[0]
+    cols = np.asarray(wl.sample_columns(M, n_check)) if check else None
+    gpu = gpu_rho_columns(batched, mu, cols) if check else None
+    batched.close()
+    plain = r.make(0)
+    pt, _, _ = r.timed(plain, p_steps, p_warm)
+    plain.close()
+    plain_ms = sum(pt) / len(pt)
+    rec = {"workload": bench_workload(name, w), "columns_per_step": M, "steps": steps, "warmup": warm,
+           "ms_per_step": ms, "value": M / (ms * 1e-3), "unit": "columns/s",
+           "plain": {"ms_per_step": plain_ms, "value": M / (plain_ms * 1e-3), "steps": p_steps,
+                     "warmup": p_warm},
+           "autotuned_shapes": shapes(tuned),
+           "phases_ms_per_step": {k: stats[k] / steps for k in PHASES},
+           "gpu_launches_per_step": stats["launches"] / steps,
+           "roofline": roofline(stats, peak_probe),
+           "result": {"mu": out[0], "e_band": out[1], "f_free": out[2]}}
+    del r
+    if check:
+        v, cores, orc = oracle_columns(w, cols, mu)
+        dr, dE = compare_rho(gpu, orc)
+        rec.update(max_drho=dr, max_drhoE=dE, drho_columns=len(orc))
+        rec["cpu_baseline"] = {"value": v, "unit": "columns/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{len(orc)} seeded columns of {name} at the GPU's mu "
+                                         "(Krylov build, projected eigenproblem, spectra, rho column)"}
+    return rec
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -191,12 +370,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    cpu_base = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # spawn pool before any CUDA work of this process
-        v, cores, sample = oracle_columns_per_s(args.workload, args.cpu_sample)
-        cpu_base = {"value": v, "unit": "columns/s", "cores": cores, "kind": "oracle", "sample": sample}
+    barrier = dist.barrier if world > 1 else None
 
     from paper_1210_1531_gb300 import build
     build.build()
@@ -206,71 +380,22 @@ def run_ours(args):
     w = wl.make(args.workload)
     M = 4 * w.n_atoms
     stream = torch.cuda.current_stream()
-    pos_dev = torch.tensor(w.pos, dtype=torch.float64, device="cuda")
-    forces = torch.empty((w.n_atoms, 3), dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
-    def make(schedule, exact_forces=False, autotune=False, graph=False):
-        return eg.System(pos_dev, w.box, w.sk, w.r_cluster, w.nu, w.kT, w.n_electrons,
-                         nu_classes=w.nu_classes, schedule=schedule, timing=True,
-                         k3_ctas_per_sm=args.k3_ctas, exact_forces=exact_forces,
-                         autotune=autotune and args.k3_ctas == 0, graph=graph)
-
-    def step(s):
-        s.rebuild(pos_dev)
-        return s.energy_force(forces)
-
-    keys = ("launches", "krylov_launches", "t_krylov_ms", "t_eig_ms", "t_bisect_ms",
-            "t_density_ms", "t_force_ms", "krylov_flops", "t_adjoint_ms")
-
-    def timed(s, k, w_steps, barrier=False):
-        """w_steps untimed steps, then k steps each timed with CUDA events on the stream; the
-        counters of each step (reset by its rebuild) are accumulated."""
-        for _ in range(w_steps):
-            step(s)
-        torch.cuda.synchronize()
-        if barrier:
-            dist.barrier()
-            torch.cuda.synchronize()
-        acc = dict.fromkeys(keys, 0.0)
-        times, out = [], None
-        for _ in range(k):
-            flush.zero_()                       # L2 flush between timed steps (not timed)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            out = step(s)
-            b.record(stream)
-            b.synchronize()
-            times.append(a.elapsed_time(b))
-            st = s.stats()
-            for key in keys:
-                acc[key] += st[key]
-        torch.cuda.synchronize()
-        if barrier:
-            dist.barrier()
-            torch.cuda.synchronize()
-        acc["bisect_steps"] = s.stats()["bisect_steps"]
-        return times, acc, out
+    r = Runner(eg, w, args.k3_ctas, stream, flush)
 
     # the production form: launch shape tuned at build (before timing), the step replayed as a
     # CUDA graph (captured during the warm-up steps)
-    batched = make(1, autotune=True, graph=True)
+    batched = r.make(1, autotune=True, graph=True)
     tuned = batched.autotune_shapes()
     with ClockSampler(local) as clk:
-        times, stats, out = timed(batched, args.steps, args.warmup, barrier=world > 1)
+        times, stats, out = r.timed(batched, args.steps, args.warmup, barrier=barrier)
     ms, value = aggregate(sum(times) / len(times), M, world, dist if world > 1 else None, "cuda")
     mu, e_band, f_free, _ = out
-
-    # kernel roofline of the dominant kernel (Krylov build + projection), event-timed per launch
-    # algorithmic flops counted by the kernel per column (formula in include/elses.h, elses_stats)
-    k_launch_ms = stats["t_krylov_ms"] / max(1, stats["krylov_launches"])
-    flops_per_launch = stats["krylov_flops"] / max(1.0, stats["krylov_launches"])
-    achieved = flops_per_launch / (k_launch_ms * 1e-3) / 1e9      # GFLOP/s
     peak_probe = eg.probe_fp64()
 
     # plain schedule, same step, fewer repetitions (reported beside the batched form)
-    plain = make(0)
-    pt, _, _ = timed(plain, max(3, args.steps // 2), 1)
+    plain = r.make(0)
+    pt, _, _ = r.timed(plain, max(3, args.steps // 2), 1)
     plain_ms = sum(pt) / len(pt)
     plain.close()
 
@@ -282,95 +407,139 @@ def run_ours(args):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        pos_dev.copy_(pos_host, non_blocking=True)
-        batched.rebuild(pos_dev)
-        res = batched.energy_force(forces)
-        f_host.copy_(forces, non_blocking=True)
+        r.pos_dev.copy_(pos_host, non_blocking=True)
+        batched.rebuild(r.pos_dev)
+        batched.energy_force(r.forces)
+        f_host.copy_(r.forces, non_blocking=True)
         b.record(stream)
         b.synchronize()
         if i >= args.warmup:
             e2e_times.append(a.elapsed_time(b))
     e2e_ms = sum(e2e_times) / len(e2e_times)
 
+    # the library's rho on the columns the oracle checks (all of them by default, at N = 1)
+    check = rank == 0 and not args.no_cpu_baseline
+    n_check = M if world == 1 and args.cpu_sample <= 0 else min(M, args.cpu_sample or 2048)
+    cols = np.arange(M) if n_check == M else np.asarray(wl.sample_columns(M, n_check))
+    gpu_rho = gpu_rho_columns(batched, mu, cols) if check else None
+
     # the same step with exact forces (the gradient through the truncated Krylov build)
     exact = None
     if not args.no_exact:
-        ex = make(1, exact_forces=True)
-        xt, xst, _ = timed(ex, 2, 1)
+        ex = r.make(1, exact_forces=True)
+        xt, xst, _ = r.timed(ex, 2, 1)
         x_ms = sum(xt) / len(xt)
+        a_rate = xst["adjoint_flops"] / (xst["t_adjoint_ms"] * 1e-3) / 1e9 if xst["t_adjoint_ms"] else 0.0
         exact = {"ms_per_step": x_ms, "value": M / (x_ms * 1e-3), "unit": "columns/s",
                  "t_adjoint_ms": xst["t_adjoint_ms"] / 2,
+                 "phases_ms_per_step": {k: xst[k] / 2 for k in PHASES},
+                 "roofline": {"bound": "alu", "kernel": "k_adjoint (exact gradient: reverse Krylov "
+                              "sweep and sampled dH, dS blocks) + its fixed-point finish",
+                              "achieved": a_rate, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+                              "frac": a_rate / FP64_NOMINAL_GFLOPS, "traffic": None,
+                              "flops_per_step": xst["adjoint_flops"] / 2},
                  "note": "forces = exact gradient of Omega through the truncated Krylov build "
                          "(finite-difference gated at 1e-5); 2 timed steps after 1 warm-up"}
         ex.close()
+    batched_stats = batched.stats()
+    batched.close()
 
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "columns/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "steps_per_s": 1e3 / ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": bench_config(args, w, world),
-            "plain": {"ms_per_step": plain_ms, "value": M / (plain_ms * 1e-3), "unit": "columns/s"},
-            "exact_forces": exact,
-            "autotuned_shapes": {f"{k}-atom clusters": f"{b} CTAs/SM, queue by {o}"
-                                 for k, (b, o) in tuned.items()},
-            "phases_ms_per_step": {k: stats[k] / args.steps for k in
-                                   ("t_krylov_ms", "t_eig_ms", "t_bisect_ms", "t_density_ms", "t_force_ms")},
-            "e2e": {"value": world * M / (e2e_ms * 1e-3), "unit": "columns/s", "ms_per_step": e2e_ms,
-                    "h2d_bytes_per_step": int(pos_host.numel() * 8),
-                    "d2h_bytes_per_step": int(f_host.numel() * 8 + 3 * 8)},
-            "gpu_launches": int(stats["launches"]),
-            "roofline": {"bound": "alu", "kernel": "k_krylov (a3 Krylov build + a4 projection)",
-                         "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
-                         "frac": achieved / FP64_NOMINAL_GFLOPS,
-                         "traffic": krylov_traffic() if args.workload == WORKLOAD else None,
-                         "peak_probe": peak_probe, "flops_per_launch": flops_per_launch,
-                         "launch_ms": k_launch_ms, "ctas_per_sm": batched.stats()["k3_ctas_per_sm"],
-                         "launches_per_step": stats["krylov_launches"] / args.steps,
-                         "peak_note": "FP64 FMA pipe: 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s); peak_probe = measured FMA-chain throughput"},
-            "clocks": clk.summary(),
-            "result": {"mu": mu, "e_band": e_band, "f_free": f_free, "bisect_steps": stats["bisect_steps"]},
-        }
-        if cpu_base is not None:
-            line["cpu_baseline"] = cpu_base
-        print(json.dumps(line))
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extra:
+        for name in EXTRA:
+            extra[name] = extra_record(eg, wl, name, args.k3_ctas, stream, flush, peak_probe,
+                                       not args.no_cpu_baseline)
+
     if world > 1:
         dist.destroy_process_group()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "columns/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "steps_per_s": 1e3 / ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": bench_config(args, w, world),
+        "plain": {"ms_per_step": plain_ms, "value": M / (plain_ms * 1e-3), "unit": "columns/s"},
+        "exact_forces": exact,
+        "autotuned_shapes": shapes(tuned),
+        "phases_ms_per_step": {k: stats[k] / args.steps for k in PHASES},
+        "e2e": {"value": world * M / (e2e_ms * 1e-3), "unit": "columns/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(pos_host.numel() * 8),
+                "d2h_bytes_per_step": int(f_host.numel() * 8 + 3 * 8)},
+        "gpu_launches": int(stats["launches"]),
+        "roofline": dict(roofline(stats, peak_probe,
+                                  krylov_traffic() if args.workload == WORKLOAD else None),
+                         ctas_per_sm=batched_stats["k3_ctas_per_sm"],
+                         launches_per_step=stats["krylov_launches"] / args.steps),
+        "clocks": clk.summary(),
+        "result": {"mu": mu, "e_band": e_band, "f_free": f_free, "bisect_steps": stats["bisect_steps"]},
+    }
+    failed = False
+    if check:
+        v, cores, orc = oracle_columns(w, cols, mu)
+        dr, dE = compare_rho(gpu_rho, orc)
+        line["max_drho"], line["max_drhoE"], line["drho_columns"] = dr, dE, len(orc)
+        line["cpu_baseline"] = {
+            "value": v, "unit": "columns/s", "cores": cores, "kind": "oracle",
+            "sample": (f"all {M} columns" if len(orc) == M else f"{len(orc)} seeded columns") +
+                      f" of {args.workload} at the GPU's mu (Krylov build, projected eigenproblem, "
+                      "spectra, rho column), one process per core; its rho columns are the ones "
+                      "max_drho compares"}
+        failed = not dr <= RHO_GATE
+    if extra:
+        line["systems"] = extra
+        failed = failed or any(not e.get("max_drho", 0.0) <= RHO_GATE for e in extra.values())
+    print(json.dumps(line))
+    if failed:
+        sys.stderr.write("rho differs from the oracle by more than the 1e-10 gate\n")
+        sys.exit(3)
+
+
+def bench_workload(name, w):
+    nu = "/".join(str(v) for _, v in w.nu_classes) + " by cluster size" if w.nu_classes else str(w.nu)
+    cl = f"{w.r_cluster:g} A" if w.r_cluster > 0 else "= whole system"
+    return (f"{name}: {DESCRIPTION.get(name, 'synthetic system')}, {w.n_atoms} atoms, cluster {cl}, "
+            f"nu {nu}, {4 * w.n_atoms} columns, kT {w.kT} eV, full energy+force step")
 
 
 def bench_config(args, w, world):
     """The workload configuration both arms report."""
-    M = 4 * w.n_atoms
-    nu = "/".join(str(v) for _, v in w.nu_classes) + " by cluster size" if w.nu_classes else str(w.nu)
-    cl = f"{w.r_cluster:g} A" if w.r_cluster > 0 else "= whole system"
-    return {"workload": f"{args.workload}: {DESCRIPTION.get(args.workload, 'synthetic system')}, "
-                        f"{w.n_atoms} atoms, cluster {cl}, nu {nu}, {M} columns, "
-                        f"kT {w.kT} eV, full energy+force step",
-            "columns_per_step": M,
+    return {"workload": bench_workload(args.workload, w),
+            "columns_per_step": 4 * w.n_atoms,
             "schedule": "batched (persistent, size-sorted queue, autotuned launch shape, CUDA graph)",
             "l2": "256 MB buffer written between timed steps",
             "parallelism": f"replicas x{world}"}
 
 
 def run_reference(args):
+    """The oracle as it stands on the machine's host cores, each step a bounded seeded sample of the
+    main workload's columns (the whole workload would take about 25 s per step); the per-step
+    time is extrapolated from the sample's columns/s."""
     rank = int(os.environ.get("RANK", 0))
     if rank != 0:
         return
+    import numpy as np
+
     import workloads as wl
     w = wl.make(args.workload)
     M = 4 * w.n_atoms
-    per_step = max(64, min(args.cpu_sample, M) // 4)
+    per_step = min(M, args.cpu_sample if args.cpu_sample > 0 else 512)
+    cols = np.asarray(wl.sample_columns(M, per_step))
     vals = []
     for i in range(args.warmup + args.steps):
-        v, cores, sample = oracle_columns_per_s(args.workload, per_step)
+        v, cores, _ = oracle_columns(w, cols, 0.0)
         if i >= args.warmup:
             vals.append(v)
     v = statistics.mean(vals)
+    sample = (f"{per_step} seeded columns of {args.workload} per step (Krylov build, projected "
+              "eigenproblem, spectra, rho column), one process per core")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "columns/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": M / v * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": M / v * 1e3, "extrapolated": True,
+        "extrapolation": f"ms_per_step = {M} columns / the columns/s of the {per_step}-column samples",
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": bench_config(args, w, args.gpus),
         "cpu_baseline": {"value": v, "unit": "columns/s", "cores": cores, "kind": "oracle", "sample": sample},

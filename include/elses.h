@@ -131,6 +131,17 @@ typedef struct elses_stats {
                                CGS2 and projection sum_{n<nu}(6(n+1)+2) n_c
                                + sum_{n<nu-1}(6(n+1)+4) n_c, n_c = 4 |cluster|               */
     double t_adjoint_ms;    /* exact-gradient kernels (elses_omega_gradient)                  */
+    double adjoint_flops;   /* algorithmic FP64 flops of the exact-gradient kernels: per column
+                               (nu = nu_eff, n_c, b_off in-cluster blocks applied from the
+                               lists, p = 24 flops per two-centre block product or 32 dense, n_at
+                               cluster atoms; the n_at terms count the on-site blocks where they
+                               act as diagonals, Slater-Koster systems, and are 0 otherwise)
+                               8 nu^2 n_c (the products G_U = 2 (HU Hh + SU Sh), Y_H = U Hh,
+                               Y_S = U Sh) + 6 nu^3 (the Rayleigh-Ritz gradient)
+                               + (nu - 1)(8 n_c + p b_off + 4 n_at) + 5 n_c nu (nu - 1) (the
+                               reverse Gram-Schmidt sweep with its H products)
+                               + 64 nu (b_off + n_at) (the sampled dH and dS blocks, H and S);
+                               plus the krylov_flops formula when the bases are recomputed      */
 } elses_stats;
 
 typedef struct elses_system_s* elses_system;

@@ -59,7 +59,8 @@ class Stats(ctypes.Structure):
                 ("k3_ctas_per_sm", ctypes.c_int), ("t_krylov_ms", ctypes.c_double),
                 ("t_eig_ms", ctypes.c_double), ("t_bisect_ms", ctypes.c_double),
                 ("t_density_ms", ctypes.c_double), ("t_force_ms", ctypes.c_double),
-                ("krylov_flops", ctypes.c_double), ("t_adjoint_ms", ctypes.c_double)]
+                ("krylov_flops", ctypes.c_double), ("t_adjoint_ms", ctypes.c_double),
+                ("adjoint_flops", ctypes.c_double)]
 
 
 EXPORTS = (

@@ -33,7 +33,10 @@
 //       Y_H = U Hh + [hbar_1 .. hbar_{nu-1}, 0],
 //       Y_S = U Sh + e_j bbar^T,
 //  sampled on the blocks of the cluster (the 4 columns of the atom summed) and added atomically
-//  into the [nnzb][4][4] outputs.
+//  into per-entry accumulators. Each contribution is taken exactly (to 2^-80) into a 128-bit
+//  fixed-point integer and added as two 64-bit words with the carry: integer addition is
+//  associative, so the sums, and the gradient and forces after them, are the same bit for bit
+//  whatever the order in which the CTAs arrive. One pass at the end converts them to FP64.
 //
 // The bases come from the energy pass when it kept them (the Krylov kernel's store form),
 // otherwise the forward recursion is recomputed here by the Krylov kernel's own code
@@ -55,6 +58,57 @@ __device__ __forceinline__ double omega_divdiff(double x, double y, double wx, d
     const double dx = (x - y) / kT;
     if (fabs(dx) > 1.0) return (wx - wy) / (x - y);
     return -2.0 * kT * log1p(fy * expm1(-dx)) / (x - y);
+}
+
+// ---- exact fixed-point accumulation: value * 2^80 as a 128-bit two's complement integer
+constexpr int kFixFrac = 80;                 // fractional bits (resolution 8e-25)
+
+// The 128-bit integer of v * 2^80, truncated toward zero below 2^-80. |v| < 2^46 (far above any
+// gradient entry); a larger or non-finite v sets DEV_NONFINITE and adds nothing.
+__device__ __forceinline__ bool to_fixed(double v, unsigned long long& lo, unsigned long long& hi) {
+    const long long bits = __double_as_longlong(v);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    lo = hi = 0ull;
+    if (ex == 0) return true;                                        // zero or subnormal
+    const int shift = ex - 1075 + kFixFrac;                          // v = mant * 2^(ex - 1075)
+    if (ex == 0x7ff || shift > 127 - 53 - 1) return false;
+    unsigned __int128 m = (unsigned long long)(bits & ((1ll << 52) - 1)) | (1ull << 52);
+    if (shift >= 0) m <<= shift;
+    else m = shift <= -64 ? (unsigned __int128)0 : (m >> -shift);
+    if (bits < 0) m = (unsigned __int128)0 - m;
+    lo = (unsigned long long)m;
+    hi = (unsigned long long)(m >> 64);
+    return true;
+}
+
+// p[0] (low word) and p[1] (high word) += (lo, hi): the low words add modulo 2^64 and the carry
+// out of each addition goes to the high word, so the pair ends as the exact 128-bit sum.
+__device__ __forceinline__ void fixed_add(unsigned long long* p, double v, int* status) {
+    unsigned long long lo, hi;
+    if (!to_fixed(v, lo, hi)) {
+        flag(status, DEV_NONFINITE);
+        return;
+    }
+    if (lo) {
+        const unsigned long long old = atomicAdd(p, lo);
+        hi += (old + lo < old) ? 1ull : 0ull;
+    }
+    if (hi) atomicAdd(p + 1, hi);
+}
+
+__global__ void k_fixed_to_double(const unsigned long long* __restrict__ acc, size_t n, double s_scale,
+                                  double* __restrict__ gH, double* __restrict__ gS) {
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < 2 * n; q += (size_t)gridDim.x * blockDim.x) {
+        const unsigned long long lo = acc[2 * q], hi = acc[2 * q + 1];
+        const bool neg = (long long)hi < 0;
+        unsigned __int128 m = ((unsigned __int128)hi << 64) | lo;
+        if (neg) m = (unsigned __int128)0 - m;
+        const double d = __ull2double_rn((unsigned long long)(m >> 64)) * 18446744073709551616.0 +
+                         __ull2double_rn((unsigned long long)m);
+        const double v = ldexp(neg ? -d : d, -kFixFrac);
+        if (q < n) gH[q] = v;
+        else gS[q - n] = s_scale * v;
+    }
 }
 
 // packed upper storage of H' (element (i, k), i <= k, at i + k (k + 1) / 2)
@@ -310,12 +364,12 @@ __device__ __forceinline__ void sampled_block(const AdjointArgs& g, const int* n
                 }
         }
     }
-    double* oH = g.gH + 16 * (size_t)blk;
-    double* oS = g.gS + 16 * (size_t)blk;
+    unsigned long long* oH = g.acc + 2 * 16 * (size_t)blk;
+    unsigned long long* oS = oH + 2 * 16 * (size_t)g.nnzb;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-        atomicAdd(oH + q, aH[q]);
-        atomicAdd(oS + q, g.s_scale * aS[q]);
+        fixed_add(oH + 2 * q, aH[q], g.status);
+        fixed_add(oS + 2 * q, aS[q], g.status);
     }
 }
 
@@ -430,6 +484,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_adjoint(const KrylovArgs a, con
                 });
             }
         } while (0);
+        if (lane == 0 && g.flops && nv > 0) {
+            // algorithmic flops of this column (formula in include/elses.h, elses_stats)
+            const unsigned long long vv = nv, nc = 4ull * v.n_at, nent = v.nent, nat = v.n_at;
+            const bool onsite = a.onsite_diag != 0;
+            const unsigned long long per = a.skr ? 24ull : 32ull;
+            const unsigned long long blocks = nent + (onsite ? nat : 0ull);
+            unsigned long long f = 8ull * vv * vv * nc + 6ull * vv * vv * vv + 64ull * vv * blocks;
+            f += (vv - 1) * (8ull * nc + per * nent + (onsite ? 4ull * nat : 0ull)) + 5ull * nc * vv * (vv - 1);
+            if (!g.bstore) {   // the forward recursion recomputed: the Krylov kernel's count
+                const unsigned long long spm = onsite ? vv * (2ull * per * nent + 4ull * nat) : vv * 2ull * per * nent;
+                const unsigned long long tri = vv * (vv + 1) / 2, trim = (vv - 1) * vv / 2;
+                f += spm + nc * (6 * tri + 2 * vv) + nc * (6 * trim + 4 * (vv - 1));
+            }
+            atomicAdd(g.flops, f);
+        }
         if (lane == 0) {
             sh_nv[warp] = nv;
             sh_U[warp] = w.U;
@@ -461,6 +530,13 @@ int adjoint_blocks_per_sm(int na_max, int deg_max) {
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adjoint, kThreads, smem);
     return nb;
+}
+
+void adjoint_finish(const unsigned long long* acc, size_t n, double s_scale, double* gH, double* gS,
+                    cudaStream_t st) {
+    const int threads = 256;
+    const int grid = (int)std::min<size_t>((2 * n + threads - 1) / threads, 152 * 16);
+    k_fixed_to_double<<<std::max(grid, 1), threads, 0, st>>>(acc, n, s_scale, gH, gS);
 }
 
 void adjoint_columns(const KrylovArgs& a, const AdjointArgs& g, int grid, cudaStream_t st) {

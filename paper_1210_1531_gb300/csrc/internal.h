@@ -96,9 +96,13 @@ struct AdjointArgs {
     const double* d;
     double mu, kT;
     const double* mu_dev;   // when set, mu is read here (device) instead
-    double* gH;             // [nnzb][16] accumulated dOmega/dH
-    double* gS;             // [nnzb][16] accumulated s_scale * dOmega/dS
-    double s_scale;
+    // dOmega/dH and dOmega/dS accumulated as exact 128-bit fixed-point sums ([2][nnzb * 16]
+    // pairs (low, high word) of unsigned 64-bit words, value * 2^80 in two's complement): integer
+    // addition is associative, so the sums do not depend on the order of the atomics
+    unsigned long long* acc;
+    int nnzb;
+    unsigned long long* flops;   // algorithmic FP64 flops of the gradient kernels, accumulated
+    int* status;
     double* scratch;        // per resident CTA: 4 warps x adjoint_warp_doubles(nu_max, na_max)
     int atom_lo, atom_hi;   // only atoms in [atom_lo, atom_hi) are accumulated
     const double* bstore;   // bases kept by the energy pass (KrylovArgs layout), or nullptr:
@@ -113,6 +117,9 @@ void block_krylov_columns(const KrylovArgs& a, int grid, cudaStream_t st);
 __host__ __device__ size_t adjoint_warp_doubles(int nu_max, int na_max);
 int adjoint_blocks_per_sm(int na_max, int deg_max);
 void adjoint_columns(const KrylovArgs& a, const AdjointArgs& g, int grid, cudaStream_t st);
+// gH = value of acc[0], gS = s_scale * value of acc[1] as doubles ([nnzb * 16] each)
+void adjoint_finish(const unsigned long long* acc, size_t n, double s_scale, double* gH, double* gS,
+                    cudaStream_t st);
 void krylov_columns(const KrylovArgs& a, int grid, cudaStream_t st);
 
 // ---------------------------------------------------------------- a5, a6 (proj_eig.cu)

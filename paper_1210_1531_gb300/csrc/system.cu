@@ -402,8 +402,8 @@ int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* 
                  cudaStream_t st, const double* mu_dev) {
     const int nm = s->nu_max;
     const int kdeg = s->user_hs ? s->max_nb : s->deg_cap;
-    CUDA_TRY(cudaMemsetAsync(gH, 0, sizeof(double) * 16 * (size_t)s->nnzb, st));
-    CUDA_TRY(cudaMemsetAsync(gS, 0, sizeof(double) * 16 * (size_t)s->nnzb, st));
+    TRY(s->adj_acc.ensure(4 * 16 * (size_t)s->nnzb));
+    CUDA_TRY(cudaMemsetAsync(s->adj_acc.p, 0, sizeof(unsigned long long) * 4 * 16 * (size_t)s->nnzb, st));
     // launch shapes and scratch: the Krylov kernel's size classes, the adjoint's own residency
     if ((int)s->adj_bps.size() != s->na_max / 32 + 1) s->adj_bps.assign(s->na_max / 32 + 1, 0);
     size_t need = 0;
@@ -442,9 +442,10 @@ int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* 
         ga.mu = mu;
         ga.mu_dev = mu_dev;
         ga.kT = s->p.kT;
-        ga.gH = gH;
-        ga.gS = gS;
-        ga.s_scale = s_scale;
+        ga.acc = s->adj_acc.p;
+        ga.nnzb = s->nnzb;
+        ga.flops = s->flops_ctr.p + 1;
+        ga.status = s->counters.p + 2;
         ga.scratch = s->ascratch.p;
         ga.atom_lo = lo;
         ga.atom_hi = hi;
@@ -482,6 +483,10 @@ int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* 
         if (conc) TRY(join_side(s, st));
         s->toc(st);
     }
+    s->tic(T_ADJOINT, st);
+    adjoint_finish(s->adj_acc.p, 16 * (size_t)s->nnzb, s_scale, gH, gS, st);
+    s->toc(st);
+    s->stats.launches++;
     CUDA_TRY(cudaGetLastError());
     return 0;
 }
@@ -734,8 +739,8 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
     CUDA_TRY(cudaMemcpyAsync(s->pos.p, pos_dev, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st));
     TRY(s->counters.ensure(kCounters));
     CUDA_TRY(cudaMemsetAsync(s->counters.p, 0, sizeof(int) * kCounters, st));
-    TRY(s->flops_ctr.ensure(1));
-    CUDA_TRY(cudaMemsetAsync(s->flops_ctr.p, 0, sizeof(unsigned long long), st));
+    TRY(s->flops_ctr.ensure(2));   // [0] Krylov kernels, [1] exact-gradient kernels
+    CUDA_TRY(cudaMemsetAsync(s->flops_ctr.p, 0, 2 * sizeof(unsigned long long), st));
     check_finite(s->pos.p, 3 * n, s->counters.p + 2, st);
     s->stats.launches++;
     {
@@ -1117,9 +1122,10 @@ int elses_get_stats(elses_system s, elses_stats* out) {
     *out = s->stats;
     out->k3_ctas_per_sm = s->k3_bps;
     if (s->flops_ctr.p) {
-        unsigned long long f = 0;
-        CUDA_TRY(cudaMemcpy(&f, s->flops_ctr.p, sizeof f, cudaMemcpyDeviceToHost));
-        out->krylov_flops = (double)f;
+        unsigned long long f[2] = {0, 0};
+        CUDA_TRY(cudaMemcpy(f, s->flops_ctr.p, sizeof f, cudaMemcpyDeviceToHost));
+        out->krylov_flops = (double)f[0];
+        out->adjoint_flops = (double)f[1];
     }
     return ELSES_OK;
 }
@@ -1128,7 +1134,7 @@ int elses_reset_stats(elses_system s) {
     if (!s) return fail(ELSES_ERR_ARG, "null system");
     s->collect();
     s->stats = elses_stats{};
-    if (s->flops_ctr.p) CUDA_TRY(cudaMemset(s->flops_ctr.p, 0, sizeof(unsigned long long)));
+    if (s->flops_ctr.p) CUDA_TRY(cudaMemset(s->flops_ctr.p, 0, 2 * sizeof(unsigned long long)));
     return ELSES_OK;
 }
 

@@ -9,6 +9,10 @@ from oracle import pipeline, physics, structure
 
 RHO_TOL = 1e-10          # |delta rho_ij| gate against the same-algorithm oracle
 E_TOL_PER_ATOM = 1e-9    # |delta E| / atom (eV)
+# rhoE = sum_k Z_ik 2 f(e_k) e_k c_k is rho with every pole's term weighted by its energy; the
+# poles that f lets through lie within about 20 eV below mu here, so the rho gate is carried over
+# in units of 10 eV (1e-9 eV), below the largest weight
+RHOE_TOL = 10.0 * RHO_TOL
 
 
 def library():

@@ -84,46 +84,100 @@ def d4096(eg):
 
 
 def test_diamond4096_sampled_atoms_match_oracle(d4096):
+    """The first 8 of the 32 seeded finite-difference atoms: each atom's 4 columns summed."""
     w, s, mu = d4096["w"], d4096["sys"], d4096["mu"]
-    for J in (0, 2345):
+    for J in wl.fd_atoms(w.n_atoms)[:8]:
+        J = int(J)
         dH, dS = s.omega_gradient(mu, J, J + 1)
         _, _, oH, oS, _ = adjoint.pattern_gradient(w, mu, cols=np.arange(4 * J, 4 * J + 4))
         assert _rel(gu.to_np(dH), oH) < GRAD_TOL, J
         assert _rel(gu.to_np(dS), oS) < GRAD_TOL, J
 
 
+FD_TOL = 1e-5            # relative to the largest force component
+
+
 @pytest.mark.slow
 def test_diamond4096_exact_forces_match_finite_differences(eg, d4096):
-    """nu = 30: exact forces against fourth-order central differences of Omega at fixed mu, for
-    atoms whose clusters do not change within the displacements; the density-matrix forces miss
-    by far more than the gate."""
+    """nu = 30 on the 4096-atom system, the 32 seeded atoms of the finite-difference check x 3
+    axes: exact forces against fourth-order central differences of Omega at fixed mu, each side
+    evaluated by the GPU path, with step h = 1e-4 A. A component is checked when no cluster
+    changes within the displacements (the lists are frozen across each pair); at least 90% of the
+    96 must be.
+
+    At a truncated nu, Omega(R) has features far narrower than 1e-4 A around some atoms: an
+    unconverged Ritz value of a column whose cluster holds the atom can move by tenths of an eV
+    within 1e-4 A. There the h = 1e-4 difference is not converged -- its own error, measured
+    against h = 1e-5, exceeds the gate -- and the component is gated against the h = 1e-5
+    difference instead (whose h^4 error is then far below the gate). The density-matrix forces
+    miss by far more than the gate (the truncation error of the Krylov space, which moves with
+    H)."""
     w, s, mu, F = d4096["w"], d4096["sys"], d4096["mu"], d4096["F"]
-    h = 1e-4
     F_hf = gu.to_np(eg.system_for(w).energy_force()[3])
     scale = np.abs(F).max()
+    gate = FD_TOL * scale
     assert abs(F.sum(axis=0)).max() < 1e-9 * scale * len(F)
     probe = eg.system_for(w)
     ref_cl = [tuple(structure.cluster(w.pos, w.box, J, w.r_cluster)) for J in range(w.n_atoms)]
-    checked, hf_gap = 0, 0.0
-    for K, m in ((7, 0), (1500, 1), (3001, 2), (4095, 0)):
-        vals, frozen = {}, True
+
+    def frozen(K, m, h):
         for t in (h, -h, 2 * h, -2 * h):
             p = w.pos.copy()
             p[K, m] += t
             near = structure.cluster(p, w.box, K, w.r_cluster)
-            frozen &= all(tuple(structure.cluster(p, w.box, J, w.r_cluster)) == ref_cl[J] for J in near)
-            frozen &= tuple(near) == ref_cl[K]
+            if tuple(near) != ref_cl[K]:
+                return False
+            if any(tuple(structure.cluster(p, w.box, J, w.r_cluster)) != ref_cl[J] for J in near):
+                return False
+        return True
+
+    def fd(K, m, h):
+        vals = {}
+        for t in (h, -h, 2 * h, -2 * h):
+            p = w.pos.copy()
+            p[K, m] += t
             probe.rebuild(torch.as_tensor(p, dtype=torch.float64).cuda())
             probe.green_columns()
             vals[t] = probe.energies(mu)["Omega"]
-        if not frozen:
-            continue
-        fd = -(8 * (vals[h] - vals[-h]) - (vals[2 * h] - vals[-2 * h])) / (12 * h)
-        assert abs(F[K, m] - fd) <= 1e-5 * scale, (K, m, F[K, m], fd)
-        hf_gap = max(hf_gap, abs(F_hf[K, m] - fd) / scale)
-        checked += 1
-    assert checked >= 3
+        return -(8 * (vals[h] - vals[-h]) - (vals[2 * h] - vals[-2 * h])) / (12 * h)
+
+    checked, refined, skipped, bad, hf_gap = [], [], [], [], 0.0
+    for K in wl.fd_atoms(w.n_atoms):
+        K = int(K)
+        for m in range(3):
+            if not frozen(K, m, 1e-4):
+                skipped.append((K, m))
+                continue
+            best = fd(K, m, 1e-4)
+            if abs(F[K, m] - best) > gate:
+                fine = fd(K, m, 1e-5)
+                if abs(best - fine) > gate:          # the h = 1e-4 difference is not converged
+                    refined.append((K, m, best, fine))
+                    best = fine
+                if abs(F[K, m] - best) > gate:
+                    bad.append((K, m, F[K, m], best))
+            hf_gap = max(hf_gap, abs(F_hf[K, m] - best) / scale)
+            checked.append((K, m))
+    assert not bad, bad
+    assert len(checked) >= 0.9 * 96, f"only {len(checked)} of 96 components frozen; skipped {skipped}"
+    assert len(refined) <= len(checked) // 4, refined
     assert hf_gap > 1e-3
+
+
+def test_gradient_and_exact_forces_are_bit_reproducible(eg):
+    """The per-column contributions are summed as exact 128-bit fixed-point integers, whose
+    atomic additions commute: two systems, and repeated calls, give the same bits although the
+    CTAs reach the accumulators in different orders (the 4096-atom system: many CTAs per block)."""
+    w = wl.make("diamond_4096")
+    a = eg.system_for(w, exact_forces=True, schedule=1)
+    b = eg.system_for(w, exact_forces=True)
+    ra, rb = a.energy_force(), b.energy_force()
+    assert ra[0] == rb[0] and np.array_equal(gu.to_np(ra[3]), gu.to_np(rb[3]))
+    g1 = a.omega_gradient(ra[0], 100, 400)
+    g2 = a.omega_gradient(ra[0], 100, 400)
+    assert all(torch.equal(x, y) for x, y in zip(g1, g2))
+    st = a.stats()
+    assert st["adjoint_flops"] > 0 and st["t_adjoint_ms"] >= 0
 
 
 def test_kept_bases_equal_recomputed_bases(eg, d64):
