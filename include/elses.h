@@ -124,10 +124,11 @@ typedef struct elses_stats {
     double t_density_ms;    /* density-matrix kernels (a8)                                   */
     double t_force_ms;      /* force kernels (a10)                                           */
     double krylov_flops;    /* algorithmic FP64 flops of the Krylov kernels (a3, a4): per column
-                               nu_eff sparse products with H and with S (per off-site block: 24
-                               flops in the two-centre form of Slater-Koster systems, 32 for a
-                               dense 4x4 block; on-site H diagonal 4 per atom, on-site S = I
-                               none) plus
+                               nu_eff sparse products with H and with S of the same vector, formed
+                               together (per off-site block: 43 flops in the two-centre form of
+                               Slater-Koster systems -- the projection t = u . x_p, 5 flops,
+                               shared by the H and the S block, 19 each -- 64 for two dense 4x4
+                               blocks; on-site H diagonal 4 per atom, on-site S = I none) plus
                                CGS2 and projection sum_{n<nu}(6(n+1)+2) n_c
                                + sum_{n<nu-1}(6(n+1)+4) n_c, n_c = 4 |cluster|               */
     double t_adjoint_ms;    /* exact-gradient kernels (elses_omega_gradient)                  */

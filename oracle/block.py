@@ -1,4 +1,4 @@
-"""Block ("multiple starting vectors") Krylov build per atom (oracle; test only).
+"""Block Krylov build per atom, one space started by the atom's 4 orbitals (oracle; test only).
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 

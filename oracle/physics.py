@@ -11,8 +11,8 @@ Z_ik c_k) the integral is done by residues: Im 1/(e + i0 - e_k) = -pi delta(e - 
     Omega    = sum_j sum_k d_k c_k w(e_k),   w(e) = -2 kT ln(1 + exp(-(e - mu)/kT))
     F_free   = Omega + mu N_e
 
-mu is found "in the bisection method" after the first calculation of G (Eq. 3 and the text
-after it). The bisection reading: bracket [min e - 40 kT, max e + 40 kT] over all poles; at
+mu is found by bisection on N(mu) = N_e once G has been computed the first time (Eq. 3 and
+the text after it). The bisection reading: bracket [min e - 40 kT, max e + 40 kT] over all poles; at
 each step mid = (lo + hi)/2 replaces lo if N(mid) < N_e, else hi; stop when hi - lo < 1e-13 eV
 or after 100 steps; mu = (lo + hi)/2. No sign change on the bracket is an error.
 

@@ -2,13 +2,16 @@
 // S' = U^T S U, for every column j = 4J + alpha of a batch of atoms.
 //
 // The paper generates G = (zS - H)^-1 column by column (Eq. 1 with b = e_j) with a Krylov
-// ("multiple Arnoldi") solver on the local cluster of j. The reading built here (the oracle's):
+// solver (the paper's multiple Arnoldi method) on the local cluster of j. The reading built
+// here (the oracle's):
 //     u_1 = e_j / sqrt(S_jj); for n = 1..nu: HU_n = H_C u_n; stop at n = nu;
 //     w = HU_n; two classical Gram-Schmidt passes h = SU^T w, w -= U h;
 //     Sw = S_C w; beta = sqrt(w^T Sw); stop if beta <= tol ||HU_n||_2; u_{n+1} = w / beta,
-// with SU_{n+1} = Sw / beta (S u_{n+1} by linearity; the oracle recomputes it by a product,
-// which agrees to rounding). H'[k][n] = u_k . HU_n and S'[k][n] = u_k . SU_n are formed for
-// k <= n as the columns appear (the oracle symmetrises full products; same values to rounding).
+// with SU_{n+1} = Sw / beta and HU_{n+1} = Hw / beta (the products of u_{n+1} by linearity,
+// Hw and Sw formed in one pass over the cluster; the oracle forms S u_{n+1} and H u_{n+1} by
+// products, which agree to rounding). H'[k][n] = u_k . HU_n and S'[k][n] = u_k . SU_n are formed
+// for k <= n as the columns appear (the oracle symmetrises full products; same values to
+// rounding).
 //
 // GB300 layout: one CTA of 4 warps per atom J, one warp per orbital column alpha; the CTA
 // builds an ELL view of the cluster sub-matrix (atoms sorted by in-cluster degree and assigned
@@ -70,8 +73,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_krylov(const KrylovArgs a) {
             const int alpha = warp;
             const int j = 4 * J + alpha;
             const int n_at = v.n_at, NP = v.NS * 32;
-            double* A = vec + (size_t)(warp * 2) * NA * 4;    // u_n (gather source of H u)
-            double* B = A + (size_t)NA * 4;                      // H u_n, then w
+            double* A = vec + (size_t)(warp * 2) * NA * 4;    // the warp's two shared vectors:
+            double* B = A + (size_t)NA * 4;                      // H u_n then w, and H w
             int nu = 0, jp = 0;
             double *Ucol = Uw, *SUcol = SUw, *HUcol = nullptr, *hess = nullptr;
             if constexpr (kStore) {
@@ -94,15 +97,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_krylov(const KrylovArgs a) {
                 a.nu_eff[j] = nu_eff;
                 if (nu_eff < nu) flag(a.status, DEV_BREAKDOWN);
                 if (a.flops) {
-                    // sparse products: nu_eff with H and nu_eff with S, per off-site block 24 flops
-                    // in the two-centre form (32 as a dense block), on-site H diagonal 4 per atom,
+                    // sparse products: nu_eff of H and S together, per off-site block 43 flops
+                    // in the two-centre form (the projection t = u.x_p, 5 flops, shared by the two
+                    // blocks of 19) or 64 as two dense blocks, on-site H diagonal 4 per atom,
                     // on-site S = I none; dense CGS2 +
                     // projection: sum_{n<nu}(6(n+1)+2) n_c + sum_{n<nu-1}(6(n+1)+4) n_c
                     const bool onsite = a.onsite_diag != 0;
                     const unsigned long long nent = (unsigned long long)v.nent;
                     const unsigned long long nc = 4ull * n_at, vv = (unsigned long long)nu_eff;
-                    const unsigned long long per = a.skr ? 24ull : 32ull;   // flops per off-site block product
-                    const unsigned long long spm = onsite ? vv * (2ull * per * nent + 4ull * n_at) : vv * 2ull * per * nent;
+                    const unsigned long long pair = a.skr ? 43ull : 64ull;   // flops per block pair (H, S)
+                    const unsigned long long spm = onsite ? vv * (pair * nent + 4ull * n_at) : vv * pair * nent;
                     const unsigned long long tri = vv * (vv + 1) / 2;          // sum_{n<v} (n+1)
                     const unsigned long long trim = vv > 0 ? (vv - 1) * vv / 2 : 0;  // sum_{n<v-1} (n+1)
                     const unsigned long long dense = nc * (6 * tri + 2 * vv) + (vv > 0 ? nc * (6 * trim + 4 * (vv - 1)) : 0);
@@ -177,8 +181,8 @@ __global__ void __launch_bounds__(kHalfThreads, 6) k_krylov_half(const KrylovArg
                     const bool onsite = a.onsite_diag != 0;
                     const unsigned long long nent = (unsigned long long)v.nent;
                     const unsigned long long nc = 4ull * n_at, vv = (unsigned long long)nu_eff;
-                    const unsigned long long per = a.skr ? 24ull : 32ull;
-                    const unsigned long long spm = onsite ? vv * (2ull * per * nent + 4ull * n_at) : vv * 2ull * per * nent;
+                    const unsigned long long pair = a.skr ? 43ull : 64ull;
+                    const unsigned long long spm = onsite ? vv * (pair * nent + 4ull * n_at) : vv * pair * nent;
                     const unsigned long long tri = vv * (vv + 1) / 2;
                     const unsigned long long trim = vv > 0 ? (vv - 1) * vv / 2 : 0;
                     const unsigned long long dense = nc * (6 * tri + 2 * vv) + (vv > 0 ? nc * (6 * trim + 4 * (vv - 1)) : 0);

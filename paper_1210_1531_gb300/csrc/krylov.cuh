@@ -153,6 +153,97 @@ __device__ __forceinline__ void sub_basis(const double* Ub, int NP, int p, const
     }
 }
 
+// y_H = H x and y_S = S x in one pass over the lane's list entries (x gathered once per entry for
+// both; in the two-centre form the projection t = u . x_p is shared by the H and S blocks, 23
+// FP64 instructions per entry instead of 2 x 13). Each product is the one spmv_w forms, bit for
+// bit: y_H with the diagonal of H's on-site block, y_S with the identity on-site (Slater-Koster
+// systems), or both with the on-site blocks as list entries. yH and yS may be shared or global.
+template <int W>
+__device__ __forceinline__ void spmv_hs_w(const double* __restrict__ Hv, const double* __restrict__ Sv,
+                                          const double* __restrict__ skr, const Ent* __restrict__ ent,
+                                          int kmax, int NS, const double* x, double* yH, double* yS,
+                                          int lane, bool onsite, const int* eself) {
+    for (int s = 0; s < NS; ++s) {
+        const int p = s * W + lane, po = 4 * p;
+        double2 h01 = make_double2(0.0, 0.0), h23 = h01, s01 = h01, s23 = h01;
+        if (onsite) {
+            s01 = *reinterpret_cast<const double2*>(x + po);
+            s23 = *reinterpret_cast<const double2*>(x + po + 2);
+            h01 = s01;
+            h23 = s23;
+            const int es = eself[p];
+            if (es >= 0) {
+                const double* d = Hv + 16 * (size_t)es;
+                h01.x *= __ldg(d); h01.y *= __ldg(d + 5); h23.x *= __ldg(d + 10); h23.y *= __ldg(d + 15);
+            }
+        }
+        st4(yH + po, h01, h23);
+        st4(yS + po, s01, s23);
+    }
+    int cur = -1;
+    double h0 = 0.0, h1 = 0.0, h2 = 0.0, h3 = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int k = 0; k < kmax; ++k) {
+        const Ent en = ent[W * k + lane];
+        if (en.blk >= 0) {
+            const int sl = en.p4 >> 16, p4 = en.p4 & 0xffff;
+            if (sl != cur) {
+                if (cur >= 0) {
+                    const int po = 4 * (cur * W + lane);
+                    st4(yH + po, make_double2(h0, h1), make_double2(h2, h3));
+                    st4(yS + po, make_double2(s0, s1), make_double2(s2, s3));
+                }
+                cur = sl;
+                const int po = 4 * (sl * W + lane);
+                double2 a, b;
+                ld4(yH + po, a, b);
+                h0 = a.x; h1 = a.y; h2 = b.x; h3 = b.y;
+                ld4(yS + po, a, b);
+                s0 = a.x; s1 = a.y; s2 = b.x; s3 = b.y;
+            }
+            const double2 x01 = *reinterpret_cast<const double2*>(x + p4);
+            const double2 x23 = *reinterpret_cast<const double2*>(x + p4 + 2);
+            if (skr) {
+                // two-centre blocks (as in spmv_w): t = u.x_p; y_s += V_ss x_s + V_sp t;
+                // y_p += V_pi x_p + (dV t - V_sp x_s) u, with the H and the S integrals
+                const double2* q = reinterpret_cast<const double2*>(skr + 12 * (size_t)en.blk);
+                const double2 u01 = __ldg(q), u2_ = __ldg(q + 1);
+                const double2 a01 = __ldg(q + 2), a23 = __ldg(q + 3), b01 = __ldg(q + 4), b23 = __ldg(q + 5);
+                const double t = fma(u2_.x, x23.y, fma(u01.y, x23.x, u01.x * x01.y));
+                h0 = fma(a01.y, t, fma(a01.x, x01.x, h0));
+                const double ah = fma(a23.y, t, -a01.y * x01.x);
+                h1 = fma(ah, u01.x, fma(a23.x, x01.y, h1));
+                h2 = fma(ah, u01.y, fma(a23.x, x23.x, h2));
+                h3 = fma(ah, u2_.x, fma(a23.x, x23.y, h3));
+                s0 = fma(b01.y, t, fma(b01.x, x01.x, s0));
+                const double as = fma(b23.y, t, -b01.y * x01.x);
+                s1 = fma(as, u01.x, fma(b23.x, x01.y, s1));
+                s2 = fma(as, u01.y, fma(b23.x, x23.x, s2));
+                s3 = fma(as, u2_.x, fma(b23.x, x23.y, s3));
+            } else {
+                const double2* bh = reinterpret_cast<const double2*>(Hv + 16 * (size_t)en.blk);
+                const double2* bs = reinterpret_cast<const double2*>(Sv + 16 * (size_t)en.blk);
+                double2 c0 = __ldg(bh + 0), c1 = __ldg(bh + 1), c2 = __ldg(bh + 2), c3 = __ldg(bh + 3);
+                double2 c4 = __ldg(bh + 4), c5 = __ldg(bh + 5), c6 = __ldg(bh + 6), c7 = __ldg(bh + 7);
+                h0 = fma(c0.x, x01.x, fma(c0.y, x01.y, fma(c1.x, x23.x, fma(c1.y, x23.y, h0))));
+                h1 = fma(c2.x, x01.x, fma(c2.y, x01.y, fma(c3.x, x23.x, fma(c3.y, x23.y, h1))));
+                h2 = fma(c4.x, x01.x, fma(c4.y, x01.y, fma(c5.x, x23.x, fma(c5.y, x23.y, h2))));
+                h3 = fma(c6.x, x01.x, fma(c6.y, x01.y, fma(c7.x, x23.x, fma(c7.y, x23.y, h3))));
+                c0 = __ldg(bs + 0); c1 = __ldg(bs + 1); c2 = __ldg(bs + 2); c3 = __ldg(bs + 3);
+                c4 = __ldg(bs + 4); c5 = __ldg(bs + 5); c6 = __ldg(bs + 6); c7 = __ldg(bs + 7);
+                s0 = fma(c0.x, x01.x, fma(c0.y, x01.y, fma(c1.x, x23.x, fma(c1.y, x23.y, s0))));
+                s1 = fma(c2.x, x01.x, fma(c2.y, x01.y, fma(c3.x, x23.x, fma(c3.y, x23.y, s1))));
+                s2 = fma(c4.x, x01.x, fma(c4.y, x01.y, fma(c5.x, x23.x, fma(c5.y, x23.y, s2))));
+                s3 = fma(c6.x, x01.x, fma(c6.y, x01.y, fma(c7.x, x23.x, fma(c7.y, x23.y, s3))));
+            }
+        }
+    }
+    if (cur >= 0) {
+        const int po = 4 * (cur * W + lane);
+        st4(yH + po, make_double2(h0, h1), make_double2(h2, h3));
+        st4(yS + po, make_double2(s0, s1), make_double2(s2, s3));
+    }
+}
+
 // Sum of 16 values held by every lane over the 32 lanes (recursive halving on lane bits 3..0,
 // then one exchange across bit 4): lanes l and l + 16 end with the sum of value l & 15.
 __device__ __forceinline__ double warp_sum16(double (&v)[16]) {
@@ -304,8 +395,10 @@ __device__ __forceinline__ bool cluster_view(const KrylovArgs& a, int J, int NA,
 // (packed upper) and row j of U, SU, HU of the column. With kAdj it also keeps HU in HUw and the
 // Gram-Schmidt coefficients in hess[n][k] (row stride nu_max): SU_k . HU_n for k <= n (the
 // first pass) and beta_n at k = n + 1, which the adjoint needs. A and B are the warp's two
-// shared vectors, h its coefficient buffer. Returns nu_eff (nu_out: the column's nu), or 0 for
-// bad input (flagged).
+// shared vectors (u_1, then by turns H u_n -> w and the products H w of the next vector), h its
+// coefficient buffer. The H and S products of each new vector are formed together from w
+// (spmv_hs_w) and scaled by 1 / beta with it. Returns nu_eff (nu_out: the column's nu), or 0
+// for bad input (flagged).
 template <bool kAdj>
 __device__ __forceinline__ int column_forward(const KrylovArgs& a, const ClusterView& v, int J, int alpha,
                                               double* A, double* B, double* h, double* Uw, double* SUw,
@@ -340,7 +433,8 @@ __device__ __forceinline__ int column_forward(const KrylovArgs& a, const Cluster
     __syncwarp();
     if (lane == 0) A[jp] = 1.0 / sqrt(sjj);
     __syncwarp();
-    spmv(a.S, a.skr, 1, ell, kmax, NS, A, SUw, lane, onsite, nullptr, eself);   // S u_1 -> SU[0]
+    // H u_1 -> B, S u_1 -> SU[0]; u_1 -> U[0]
+    spmv_hs_w<32>(a.H, a.S, a.skr, ell, kmax, NS, A, B, SUw, lane, onsite, eself);
     for (int sl = 0; sl < NS; ++sl) {
         const int p = sl * 32 + lane;
         double2 x0, x1;
@@ -349,23 +443,24 @@ __device__ __forceinline__ int column_forward(const KrylovArgs& a, const Cluster
     }
     __syncwarp();
 
+    // P holds H u_n at the top of step n (then w); the products of the next basis vector go to Q
+    double* P = B;
+    double* Q = A;
     int nu_eff = nu;
     for (int n = 0; n < nu; ++n) {
         double* SUn = SUw + (size_t)n * vs;
-        spmv(a.H, a.skr, 0, ell, kmax, NS, A, B, lane, onsite, a.H, eself);
-        __syncwarp();
         if constexpr (kAdj) {
             for (int sl = 0; sl < NS; ++sl) {
                 const int p = sl * 32 + lane;
                 double2 x0, x1;
-                ld4(B + 4 * p, x0, x1);
+                ld4(P + 4 * p, x0, x1);
                 st4(HUw + (size_t)n * vs + 4 * p, x0, x1);
             }
         }
         if (lane == 0) {
-            a.urow[(size_t)col * a.nu_max + n] = A[jp];
+            a.urow[(size_t)col * a.nu_max + n] = Uw[(size_t)n * vs + jp];
             a.surow[(size_t)col * a.nu_max + n] = SUn[jp];
-            a.hurow[(size_t)col * a.nu_max + n] = B[jp];
+            a.hurow[(size_t)col * a.nu_max + n] = P[jp];
         }
         // pass A: H'[k][n], S'[k][n] and the first CGS coefficients, k <= n, five k at a time
         double hh = 0.0;
@@ -376,7 +471,7 @@ __device__ __forceinline__ int column_forward(const KrylovArgs& a, const Cluster
             for (int sl = 0; sl < NS; ++sl) {
                 const int p = sl * 32 + lane;
                 double2 hu0, hu1, su0, su1;
-                ld4(B + 4 * p, hu0, hu1);
+                ld4(P + 4 * p, hu0, hu1);
                 ld4(SUn + 4 * p, su0, su1);
                 if (k0 == 0) acc[15] = fma4(hu0, hu1, hu0, hu1, acc[15]);
 #pragma unroll
@@ -416,10 +511,10 @@ __device__ __forceinline__ int column_forward(const KrylovArgs& a, const Cluster
             for (int sl = 0; sl < NS; ++sl) {
                 const int p = sl * 32 + lane;
                 double2 w0, w1;
-                ld4(B + 4 * p, w0, w1);
+                ld4(P + 4 * p, w0, w1);
                 if (k0 == 0) {
                     sub_basis(Uw, NP, p, h, n, w0, w1);
-                    st4(B + 4 * p, w0, w1);
+                    st4(P + 4 * p, w0, w1);
                 }
 #pragma unroll
                 for (int kk = 0; kk < 16; ++kk) {
@@ -441,19 +536,19 @@ __device__ __forceinline__ int column_forward(const KrylovArgs& a, const Cluster
         for (int sl = 0; sl < NS; ++sl) {
             const int p = sl * 32 + lane;
             double2 w0, w1;
-            ld4(B + 4 * p, w0, w1);
+            ld4(P + 4 * p, w0, w1);
             sub_basis(Uw, NP, p, h, n, w0, w1);
-            st4(B + 4 * p, w0, w1);
+            st4(P + 4 * p, w0, w1);
         }
         __syncwarp();
-        // Sw (into the next SU slot) and beta
+        // H w -> Q and S w -> the next SU slot in one pass, then beta
         double* SUn1 = SUw + (size_t)(n + 1) * vs;
-        spmv(a.S, a.skr, 1, ell, kmax, NS, B, SUn1, lane, onsite, nullptr, eself);
+        spmv_hs_w<32>(a.H, a.S, a.skr, ell, kmax, NS, P, Q, SUn1, lane, onsite, eself);
         double part = 0.0;
         for (int sl = 0; sl < NS; ++sl) {
             const int p = sl * 32 + lane;
             double2 w0, w1, v0, v1;
-            ld4(B + 4 * p, w0, w1);
+            ld4(P + 4 * p, w0, w1);
             ld4(SUn1 + 4 * p, v0, v1);
             part = fma4(w0, w1, v0, v1, part);
         }
@@ -476,18 +571,24 @@ __device__ __forceinline__ int column_forward(const KrylovArgs& a, const Cluster
         if constexpr (kAdj) {
             if (lane == 0) hess[(size_t)n * a.nu_max + n + 1] = beta;
         }
+        // u_{n+1} = w / beta, S u_{n+1} = S w / beta, H u_{n+1} = H w / beta (by linearity)
         const double inv = 1.0 / beta;
         for (int sl = 0; sl < NS; ++sl) {
             const int p = sl * 32 + lane;
-            double2 w0, w1, v0, v1;
-            ld4(B + 4 * p, w0, w1);
+            double2 w0, w1, v0, v1, g0, g1;
+            ld4(P + 4 * p, w0, w1);
             ld4(SUn1 + 4 * p, v0, v1);
+            ld4(Q + 4 * p, g0, g1);
             w0.x *= inv; w0.y *= inv; w1.x *= inv; w1.y *= inv;
             v0.x *= inv; v0.y *= inv; v1.x *= inv; v1.y *= inv;
-            st4(A + 4 * p, w0, w1);
+            g0.x *= inv; g0.y *= inv; g1.x *= inv; g1.y *= inv;
             st4(Uw + (size_t)(n + 1) * vs + 4 * p, w0, w1);
             st4(SUn1 + 4 * p, v0, v1);
+            st4(Q + 4 * p, g0, g1);
         }
+        double* t = P;
+        P = Q;
+        Q = t;
         __syncwarp();
     }
     return nu_eff;
@@ -722,8 +823,10 @@ __device__ __forceinline__ bool cluster_view_w(const KrylovArgs& a, int J, int N
 // (packed upper) and row j of U, SU, HU of the column. With kAdj it also keeps HU in HUw and the
 // Gram-Schmidt coefficients in hess[n][k] (row stride nu_max): SU_k . HU_n for k <= n (the
 // first pass) and beta_n at k = n + 1, which the adjoint needs. A and B are the warp's two
-// shared vectors, h its coefficient buffer. Returns nu_eff (nu_out: the column's nu), or 0 for
-// bad input (flagged).
+// shared vectors (u_1, then by turns H u_n -> w and the products H w of the next vector), h its
+// coefficient buffer. The H and S products of each new vector are formed together from w
+// (spmv_hs_w) and scaled by 1 / beta with it. Returns nu_eff (nu_out: the column's nu), or 0
+// for bad input (flagged).
 template <bool kAdj, int W>
 __device__ __forceinline__ int column_forward_w(const KrylovArgs& a, const ClusterView& v, int J, int alpha,
                                               double* A, double* B, double* h, double* Uw, double* SUw,
@@ -759,7 +862,8 @@ __device__ __forceinline__ int column_forward_w(const KrylovArgs& a, const Clust
     __syncwarp(gm);
     if (lane == 0) A[jp] = 1.0 / sqrt(sjj);
     __syncwarp(gm);
-    spmv_w<W>(a.S, a.skr, 1, ell, kmax, NS, A, SUw, lane, onsite, nullptr, eself);   // S u_1 -> SU[0]
+    // H u_1 -> B, S u_1 -> SU[0]; u_1 -> U[0]
+    spmv_hs_w<W>(a.H, a.S, a.skr, ell, kmax, NS, A, B, SUw, lane, onsite, eself);
     for (int sl = 0; sl < NS; ++sl) {
         const int p = sl * W + lane;
         double2 x0, x1;
@@ -768,23 +872,24 @@ __device__ __forceinline__ int column_forward_w(const KrylovArgs& a, const Clust
     }
     __syncwarp(gm);
 
+    // P holds H u_n at the top of step n (then w); the products of the next basis vector go to Q
+    double* P = B;
+    double* Q = A;
     int nu_eff = nu;
     for (int n = 0; n < nu; ++n) {
         double* SUn = SUw + (size_t)n * vs;
-        spmv_w<W>(a.H, a.skr, 0, ell, kmax, NS, A, B, lane, onsite, a.H, eself);
-        __syncwarp(gm);
         if constexpr (kAdj) {
             for (int sl = 0; sl < NS; ++sl) {
                 const int p = sl * W + lane;
                 double2 x0, x1;
-                ld4(B + 4 * p, x0, x1);
+                ld4(P + 4 * p, x0, x1);
                 st4(HUw + (size_t)n * vs + 4 * p, x0, x1);
             }
         }
         if (lane == 0) {
-            a.urow[(size_t)col * a.nu_max + n] = A[jp];
+            a.urow[(size_t)col * a.nu_max + n] = Uw[(size_t)n * vs + jp];
             a.surow[(size_t)col * a.nu_max + n] = SUn[jp];
-            a.hurow[(size_t)col * a.nu_max + n] = B[jp];
+            a.hurow[(size_t)col * a.nu_max + n] = P[jp];
         }
         // pass A: H'[k][n], S'[k][n] and the first CGS coefficients, k <= n, five k at a time
         double hh = 0.0;
@@ -795,7 +900,7 @@ __device__ __forceinline__ int column_forward_w(const KrylovArgs& a, const Clust
             for (int sl = 0; sl < NS; ++sl) {
                 const int p = sl * W + lane;
                 double2 hu0, hu1, su0, su1;
-                ld4(B + 4 * p, hu0, hu1);
+                ld4(P + 4 * p, hu0, hu1);
                 ld4(SUn + 4 * p, su0, su1);
                 if (k0 == 0) acc[15] = fma4(hu0, hu1, hu0, hu1, acc[15]);
 #pragma unroll
@@ -835,10 +940,10 @@ __device__ __forceinline__ int column_forward_w(const KrylovArgs& a, const Clust
             for (int sl = 0; sl < NS; ++sl) {
                 const int p = sl * W + lane;
                 double2 w0, w1;
-                ld4(B + 4 * p, w0, w1);
+                ld4(P + 4 * p, w0, w1);
                 if (k0 == 0) {
                     sub_basis(Uw, NP, p, h, n, w0, w1);
-                    st4(B + 4 * p, w0, w1);
+                    st4(P + 4 * p, w0, w1);
                 }
 #pragma unroll
                 for (int kk = 0; kk < 16; ++kk) {
@@ -860,19 +965,19 @@ __device__ __forceinline__ int column_forward_w(const KrylovArgs& a, const Clust
         for (int sl = 0; sl < NS; ++sl) {
             const int p = sl * W + lane;
             double2 w0, w1;
-            ld4(B + 4 * p, w0, w1);
+            ld4(P + 4 * p, w0, w1);
             sub_basis(Uw, NP, p, h, n, w0, w1);
-            st4(B + 4 * p, w0, w1);
+            st4(P + 4 * p, w0, w1);
         }
         __syncwarp(gm);
-        // Sw (into the next SU slot) and beta
+        // H w -> Q and S w -> the next SU slot in one pass, then beta
         double* SUn1 = SUw + (size_t)(n + 1) * vs;
-        spmv_w<W>(a.S, a.skr, 1, ell, kmax, NS, B, SUn1, lane, onsite, nullptr, eself);
+        spmv_hs_w<W>(a.H, a.S, a.skr, ell, kmax, NS, P, Q, SUn1, lane, onsite, eself);
         double part = 0.0;
         for (int sl = 0; sl < NS; ++sl) {
             const int p = sl * W + lane;
             double2 w0, w1, v0, v1;
-            ld4(B + 4 * p, w0, w1);
+            ld4(P + 4 * p, w0, w1);
             ld4(SUn1 + 4 * p, v0, v1);
             part = fma4(w0, w1, v0, v1, part);
         }
@@ -895,18 +1000,24 @@ __device__ __forceinline__ int column_forward_w(const KrylovArgs& a, const Clust
         if constexpr (kAdj) {
             if (lane == 0) hess[(size_t)n * a.nu_max + n + 1] = beta;
         }
+        // u_{n+1} = w / beta, S u_{n+1} = S w / beta, H u_{n+1} = H w / beta (by linearity)
         const double inv = 1.0 / beta;
         for (int sl = 0; sl < NS; ++sl) {
             const int p = sl * W + lane;
-            double2 w0, w1, v0, v1;
-            ld4(B + 4 * p, w0, w1);
+            double2 w0, w1, v0, v1, g0, g1;
+            ld4(P + 4 * p, w0, w1);
             ld4(SUn1 + 4 * p, v0, v1);
+            ld4(Q + 4 * p, g0, g1);
             w0.x *= inv; w0.y *= inv; w1.x *= inv; w1.y *= inv;
             v0.x *= inv; v0.y *= inv; v1.x *= inv; v1.y *= inv;
-            st4(A + 4 * p, w0, w1);
+            g0.x *= inv; g0.y *= inv; g1.x *= inv; g1.y *= inv;
             st4(Uw + (size_t)(n + 1) * vs + 4 * p, w0, w1);
             st4(SUn1 + 4 * p, v0, v1);
+            st4(Q + 4 * p, g0, g1);
         }
+        double* t = P;
+        P = Q;
+        Q = t;
         __syncwarp(gm);
     }
     return nu_eff;

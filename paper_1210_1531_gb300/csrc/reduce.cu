@@ -2,8 +2,8 @@
 //
 // With the poles e_k and weights of every column, the electron count is
 //     N(mu) = Tr(rho S) = sum_j sum_k 2 f(e_k - mu) d_k c_k,   f(x) = 1 / (1 + exp(x / kT)),
-// and mu is found "in the bisection method" after the first calculation of G (Eq. 3 and the
-// text after it). Reading: bracket [min e - 40 kT, max e + 40 kT]; each step replaces lo by mid
+// and mu is found by bisection on N(mu) = N_e once G has been computed the first time (Eq. 3
+// and the text after it). Reading: bracket [min e - 40 kT, max e + 40 kT]; each step replaces lo by mid
 // when N(mid) < N_e, else hi; stop when hi - lo < tol or after max_iter steps; mu = (lo+hi)/2.
 // E_band = sum 2 f g c = Tr(rho H) (Eq. 6); Omega = sum d c w(e), w = -2 kT ln(1 + e^{-(e-mu)/kT}).
 //
