@@ -157,9 +157,20 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
                          const double* box_host, const elses_sk* sk,
                          const elses_params* params, void* stream);
 
-/* Replace H and S by user values on the system's own pattern (double[nnzb][4][4] device).
- * Forces need the Slater-Koster derivatives and are unavailable afterwards (ERR_STATE). */
-int elses_set_hs(elses_system sys, const double* H_dev, const double* S_dev, void* stream);
+/* Replace H and S by caller values (double[nnzb][4][4] device each, [e][a][b] = X_(I,a),(J,b) for
+ * block e = (I, J)), on the system's own pattern (row_ptr_dev = col_idx_dev = NULL; nnzb is then
+ * ignored) or on the caller's block pattern: row_ptr_dev int32[N+1], col_idx_dev int32[nnzb]
+ * (device), rows strictly ascending, every diagonal block present, the pattern symmetric (block
+ * (J, I) present with (I, J)) and no row longer than max_neighbors. The caller's pattern replaces
+ * the neighbour pattern until the next elses_build_clusters: it is the pattern of the sparse
+ * products inside each column's cluster (the clusters stay those of r_cluster around the
+ * positions), of rho and rhoE (elses_density_matrix), of G and of the ICOHP. The on-site blocks
+ * are applied as full blocks. The pattern is checked on the host before anything changes
+ * (ELSES_ERR_ARG, or ELSES_ERR_CAPACITY for a row over max_neighbors). Forces need the
+ * Slater-Koster H and S and are unavailable afterwards (ERR_STATE). Synchronises `stream` when a
+ * pattern is given. Passage: Eq. 1 (H and S sparse, real symmetric, S positive definite). */
+int elses_set_hs(elses_system sys, int nnzb, const int* row_ptr_dev, const int* col_idx_dev,
+                 const double* H_dev, const double* S_dev, void* stream);
 
 /* Autotuner of the Krylov kernel's launch shape (a3, a4). For each cluster size class of the
  * system (clusters up to its capacity in atoms; one CTA per atom, persistent), run = 1 times

@@ -54,6 +54,21 @@ def bsr_to_dense(row_ptr, col_idx, vals):
     return A
 
 
+def bsr_submatrix(row_ptr, col_idx, vals, atoms):
+    """Principal submatrix of a block-sparse matrix on the orbitals of `atoms` (sorted list),
+    rows/columns ordered by (atom position in `atoms`, orbital); blocks outside the pattern are 0."""
+    atoms = np.asarray(atoms)
+    n = len(atoms)
+    A = np.zeros((n, 4, n, 4))
+    for a, I in enumerate(atoms):
+        row = col_idx[row_ptr[I]:row_ptr[I + 1]]
+        hit = np.searchsorted(atoms, row)
+        ok = (hit < n) & (atoms[np.minimum(hit, n - 1)] == row)
+        for k in np.nonzero(ok)[0]:
+            A[a, :, hit[k], :] = vals[row_ptr[I] + k]
+    return A.reshape(4 * n, 4 * n)
+
+
 def cluster_matrices(pos, box, sk, atoms):
     """Principal submatrices H_C, S_C of H and S on the orbitals of `atoms` (sorted list).
 

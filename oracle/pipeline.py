@@ -62,6 +62,21 @@ def solve_column(pos, box, sk, r_cluster, nu, j, nu_rule=None):
                   kc.Hp, kc.Sp)
 
 
+def solve_column_matrices(Hc, Sc, atoms, pattern, j, nu):
+    """The same per-column path on given cluster matrices (caller values on a caller pattern):
+    Hc, Sc are the principal submatrices of H and S on the orbitals of `atoms` (sorted), and the
+    pattern rows P(j) are the atoms `pattern` (the caller pattern's row J), inside the cluster."""
+    J, alpha = divmod(int(j), 4)
+    atoms = np.asarray(atoms)
+    jl = 4 * int(np.searchsorted(atoms, J)) + alpha
+    kc = krylov.arnoldi_column(Hc, Sc, jl, nu)
+    eps, V = krylov.projected_eig(kc.Hp, kc.Sp)
+    c, d, g = krylov.spectra(kc, V, jl)
+    pattern = np.asarray(pattern)
+    rows = (4 * np.searchsorted(atoms, pattern)[:, None] + np.arange(4)[None, :]).ravel()
+    return Column(int(j), atoms, pattern, kc.nu_eff, eps, c, d, g, kc.U[rows, :], V, kc.Hp, kc.Sp)
+
+
 def columns(workload, cols=None):
     """Per-column results for the given basis indices (default: all 4N)."""
     M = 4 * workload.n_atoms

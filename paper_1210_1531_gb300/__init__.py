@@ -88,7 +88,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     pI, pD, pLL = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)
     sig = {
         "elses_build_clusters": [ctypes.POINTER(P), I, P, pD, ctypes.POINTER(SK), ctypes.POINTER(Params), V],
-        "elses_set_hs": [P, P, P, V],
+        "elses_set_hs": [P, I, P, P, P, P, V],
         "elses_green_columns": [P, I, I, I, pD, P, P, V],
         "elses_find_mu": [P, pD, pD, V],
         "elses_density_matrix": [P, D, P, P, V],
@@ -323,8 +323,20 @@ class System:
         _check(self._L.elses_get_hs(self._h, _ptr(H), _ptr(S), _stream(stream)))
         return H, S
 
-    def set_hs(self, H, S, stream=None):
-        _check(self._L.elses_set_hs(self._h, _ptr(H.contiguous()), _ptr(S.contiguous()), _stream(stream)))
+    def set_hs(self, H, S, row_ptr=None, col_idx=None, stream=None):
+        """elses_set_hs: caller H and S (CUDA float64 [nnzb, 4, 4]) on the system's own pattern,
+        or on the caller's block pattern (CUDA int32 row_ptr [N+1] and col_idx [nnzb])."""
+        if (row_ptr is None) != (col_idx is None):
+            raise ValueError("row_ptr and col_idx go together")
+        nnzb = 0
+        if row_ptr is not None:
+            row_ptr = row_ptr.to(torch.int32).contiguous()
+            col_idx = col_idx.to(torch.int32).contiguous()
+            nnzb = int(col_idx.numel())
+        _check(self._L.elses_set_hs(self._h, nnzb, _ptr(row_ptr), _ptr(col_idx), _ptr(H.contiguous()),
+                                    _ptr(S.contiguous()), _stream(stream)))
+        if row_ptr is not None:
+            self.nnzb = nnzb
 
     def clusters(self, stream=None):
         total, mx = ctypes.c_longlong(0), ctypes.c_int(0)

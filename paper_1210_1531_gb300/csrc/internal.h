@@ -24,6 +24,9 @@ void count_lists(const double* pos, int n, const CellGrid& g, const int* cell_of
 void fill_lists(const double* pos, int n, const CellGrid& g, const int* cell_of,
                 const int* cell_start, const int* cell_atoms, double r, const int* ptr, int* idx,
                 int cap, int* status, cudaStream_t st);
+// count += the pattern pairs (I, J), I in row J, with I outside the cluster of J
+void pattern_outside_clusters(int n, const int* row_ptr, const int* col_idx, const int* cl_ptr,
+                              const int* cl_idx, int* count, cudaStream_t st);
 
 // Sets the thread-local message returned by elses_last_error and returns `code`.
 int report_error(int code, const char* fmt, ...);

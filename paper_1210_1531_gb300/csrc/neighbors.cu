@@ -290,4 +290,33 @@ void fill_lists(const double* pos, int n, const CellGrid& g, const int* cell_of,
                                                          ptr, idx, cap, status);
 }
 
+// Counts the pattern pairs (I, J), I in row J's list, whose atom I lies outside the cluster of J
+// (clusters as sorted lists cl_idx[cl_ptr[J] ..]); the pattern is already known to be well formed.
+__global__ void k_pattern_outside(int n, const int* __restrict__ row_ptr, const int* __restrict__ col_idx,
+                                  const int* __restrict__ cl_ptr, const int* __restrict__ cl_idx,
+                                  int* __restrict__ count) {
+    const int J = blockIdx.x * blockDim.x + threadIdx.x;
+    if (J >= n) return;
+    const int a = cl_ptr[J], b = cl_ptr[J + 1];
+    int missing = 0;
+    for (int e = row_ptr[J]; e < row_ptr[J + 1]; ++e) {
+        const int I = col_idx[e];
+        int lo = a, hi = b - 1;
+        bool found = false;
+        while (lo <= hi && !found) {
+            const int mid = (lo + hi) >> 1, v = cl_idx[mid];
+            found = v == I;
+            if (v < I) lo = mid + 1; else hi = mid - 1;
+        }
+        missing += found ? 0 : 1;
+    }
+    if (missing) atomicAdd(count, missing);
+}
+
+void pattern_outside_clusters(int n, const int* row_ptr, const int* col_idx, const int* cl_ptr,
+                              const int* cl_idx, int* count, cudaStream_t st) {
+    const int T = 256;
+    k_pattern_outside<<<(n + T - 1) / T, T, 0, st>>>(n, row_ptr, col_idx, cl_ptr, cl_idx, count);
+}
+
 }  // namespace elses

@@ -844,13 +844,84 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
     return ELSES_OK;
 }
 
-int elses_set_hs(elses_system s, const double* H_dev, const double* S_dev, void* stream) {
+// A caller's block pattern: checked on the host (rows ascending, inside [0, N), the diagonal
+// present, symmetric, rows within max_neighbors), then row map and transpose map, and the
+// column buffers sized for it.
+static int adopt_pattern(elses_system s, int nnzb, const int* row_ptr_dev, const int* col_idx_dev, cudaStream_t st) {
+    const int n = s->n;
+    std::vector<int> rp(n + 1), ci((size_t)nnzb);
+    CUDA_TRY(cudaMemcpyAsync(rp.data(), row_ptr_dev, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(ci.data(), col_idx_dev, sizeof(int) * (size_t)nnzb, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (rp[0] != 0 || rp[n] != nnzb) return fail(ELSES_ERR_ARG, "row_ptr must run from 0 to nnzb");
+    int max_row = 0;
+    for (int i = 0; i < n; ++i) {
+        const int a = rp[i], b = rp[i + 1];
+        if (b < a) return fail(ELSES_ERR_ARG, "row_ptr must not decrease (row %d)", i);
+        max_row = std::max(max_row, b - a);
+        bool diag = false;
+        for (int e = a; e < b; ++e) {
+            if (ci[e] < 0 || ci[e] >= n) return fail(ELSES_ERR_ARG, "col_idx out of range (row %d)", i);
+            if (e > a && ci[e] <= ci[e - 1]) return fail(ELSES_ERR_ARG, "row %d is not strictly ascending", i);
+            diag |= ci[e] == i;
+        }
+        if (!diag) return fail(ELSES_ERR_ARG, "row %d has no diagonal block", i);
+    }
+    if (max_row > s->p.max_neighbors)
+        return fail(ELSES_ERR_CAPACITY, "a row has %d blocks (max_neighbors %d)", max_row, s->p.max_neighbors);
+    if (s->p.r_cluster > 0) {   // each column's pattern rows must lie in its cluster
+        int* cnt = s->counters.p + 3;
+        CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int), st));
+        pattern_outside_clusters(n, row_ptr_dev, col_idx_dev, s->cl_ptr.p, s->cl_idx.p, cnt, st);
+        s->stats.launches++;
+        int outside = 0;
+        CUDA_TRY(cudaMemcpyAsync(&outside, cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        if (outside) return fail(ELSES_ERR_ARG, "%d pattern blocks join atoms farther apart than r_cluster", outside);
+    }
+    std::vector<int> row_of((size_t)nnzb), tmap((size_t)nnzb);
+    for (int i = 0; i < n; ++i)
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+            row_of[e] = i;
+            const int J = ci[e];
+            const auto first = ci.begin() + rp[J], last = ci.begin() + rp[J + 1];
+            const auto it = std::lower_bound(first, last, i);
+            if (it == last || *it != i) return fail(ELSES_ERR_ARG, "the pattern is not symmetric (%d, %d)", i, J);
+            tmap[e] = (int)(it - ci.begin());
+        }
+    TRY(s->col_idx.ensure(nnzb));
+    TRY(s->row_of.ensure(nnzb));
+    TRY(s->tmap.ensure(nnzb));
+    TRY(s->H.ensure((size_t)nnzb * 16));
+    TRY(s->S.ensure((size_t)nnzb * 16));
+    CUDA_TRY(cudaMemcpyAsync(s->row_ptr.p, rp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(s->col_idx.p, ci.data(), sizeof(int) * (size_t)nnzb, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(s->row_of.p, row_of.data(), sizeof(int) * (size_t)nnzb, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(s->tmap.p, tmap.data(), sizeof(int) * (size_t)nnzb, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));   // the host vectors are released on return
+    s->h_row_ptr = rp;
+    s->nnzb = nnzb;
+    s->max_nb = max_row;
+    return 0;
+}
+
+int elses_set_hs(elses_system s, int nnzb, const int* row_ptr_dev, const int* col_idx_dev, const double* H_dev,
+                 const double* S_dev, void* stream) {
     TRY(check_built(s));
     if (!H_dev || !S_dev) return fail(ELSES_ERR_ARG, "null H or S");
+    if ((row_ptr_dev == nullptr) != (col_idx_dev == nullptr))
+        return fail(ELSES_ERR_ARG, "row_ptr and col_idx go together");
     cudaStream_t st = (cudaStream_t)stream;
+    if (row_ptr_dev) {
+        if (nnzb < s->n) return fail(ELSES_ERR_ARG, "nnzb must cover at least the diagonal blocks");
+        TRY(adopt_pattern(s, nnzb, row_ptr_dev, col_idx_dev, st));   // checks before it changes anything
+        s->user_hs = true;
+        s->drop_graph();
+        TRY(prepare_columns(s));
+    }
+    s->user_hs = true;
     CUDA_TRY(cudaMemcpyAsync(s->H.p, H_dev, sizeof(double) * 16 * s->nnzb, cudaMemcpyDeviceToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(s->S.p, S_dev, sizeof(double) * 16 * s->nnzb, cudaMemcpyDeviceToDevice, st));
-    s->user_hs = true;
     s->have_rho = false;
     s->v_lazy = false;   // every column is recomputed before V is used again
     s->atom_done.assign(s->n, 0);

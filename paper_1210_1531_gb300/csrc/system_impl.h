@@ -202,7 +202,8 @@ struct elses_system_s {
 };
 
 enum { T_KRYLOV = 0, T_EIG = 1, T_BISECT = 2, T_DENSITY = 3, T_FORCE = 4, T_ADJOINT = 5 };
-// device counters: [0] max neighbours, [1] max cluster, [2] status, [3] unused, [8..] the work
+// device counters: [0] max neighbours, [1] max cluster, [2] status, [3] a caller pattern's blocks
+// outside the clusters (elses_set_hs), [8..] the work
 // queues of the class launches of a batch (one each, so that they can run at the same time)
 constexpr int kQueue0 = 8;
 constexpr int kCounters = 24;

@@ -139,6 +139,36 @@ def test_indefinite_overlap_is_reported_not_truncated(diamond64):
         assert krylov.arnoldi_column(H, S, j, 30).nu_eff == 30
 
 
+def test_column_from_given_matrices_equals_the_slater_koster_path(diamond64):
+    """The caller-matrix form of the column path (pipeline.solve_column_matrices), given the
+    dense Slater-Koster H and S and the r_cut pattern, is the Slater-Koster path itself, and the
+    whole-system cluster with the whole system as pattern gives the exact density matrix at
+    full subspace (nu = M)."""
+    w = diamond64
+    rp, ci = structure.neighbor_csr(w.pos, w.box, w.sk.r_cut)
+    Hb, Sb = hamiltonian.bsr_values(w.pos, w.box, w.sk, rp, ci)
+    atoms = np.arange(w.n_atoms)
+    Hc, Sc = hamiltonian.bsr_submatrix(rp, ci, Hb, atoms), hamiltonian.bsr_submatrix(rp, ci, Sb, atoms)
+    H, S = hamiltonian.dense(w.pos, w.box, w.sk)
+    assert np.array_equal(Hc, H) and np.array_equal(Sc, S)
+    for j in (0, 37, 254):
+        pat = structure.within(w.pos, w.box, j // 4, w.sk.r_cut)
+        a = pipeline.solve_column(w.pos, w.box, w.sk, 0.0, 30, j)
+        b = pipeline.solve_column_matrices(Hc, Sc, atoms, pat, j, 30)
+        assert np.array_equal(a.pattern, b.pattern) and a.nu_eff == b.nu_eff
+        ra, rb = pipeline.rho_column(a, 0.5, w.kT), pipeline.rho_column(b, 0.5, w.kT)
+        assert np.abs(ra[0] - rb[0]).max() < 1e-13
+    frag = _fragment()
+    Hf, Sf = hamiltonian.dense(frag.pos, frag.box, frag.sk)
+    ref = pipeline.dense_reference(frag)
+    M = 4 * frag.n_atoms
+    everything = np.arange(frag.n_atoms)
+    for j in (3, 30):
+        col = pipeline.solve_column_matrices(Hf, Sf, everything, everything, j, M)
+        r, _ = pipeline.rho_column(col, ref["mu"], frag.kT)
+        assert np.abs(r.ravel() - ref["rho"][:, j]).max() < 1e-8
+
+
 # ----------------------------------------------------------------------------- exact path
 def test_exact_matches_library_generalized_eigh(diamond64):
     H, S = hamiltonian.dense(diamond64.pos, diamond64.box, diamond64.sk)
