@@ -10,22 +10,38 @@ namespace elses {
 
 // The autotuner: per size class (at the first batch that has it), the Krylov kernel timed at every resident
 // CTA count that fits, on the class's first atoms in launch order (up to two full waves at the
-// largest count); the fastest per atom is kept in tuned_bps. With the work queue, the whole
-// class is then timed in both orders of its atoms -- decreasing cluster size (short tail) and
-// atom order (neighbouring clusters in flight together share H and S in L2) -- and the faster
-// is kept in tuned_order. The launches are planned again.
+// largest count); the fastest per atom is kept in tuned_bps. A class of an odd number of 16-atom
+// slots is timed in both column forms, half-warp (capacity 16 ns) and whole-warp (16 (ns + 1)),
+// whatever the occupancy heuristic would have planned, and the faster kept in tuned_half. With
+// the work queue, the whole class is then timed in both orders of its atoms -- decreasing
+// cluster size (short tail) and atom order (neighbouring clusters in flight together share H
+// and S in L2) -- and the faster is kept in tuned_order. The launches are planned again.
 int autotune_impl(elses_system s, cudaStream_t st) {
     const int nm = s->nu_max;
     const int kdeg = s->user_hs ? s->max_nb : s->deg_cap;
     s->tuned_bps.assign(s->na_max / 16 + 1, 0);
     s->tuned_order.assign(s->na_max / 16 + 1, 0);
     s->tuned_half.assign(s->na_max / 16 + 1, 0);
+    const bool half_ok = s->p.k3_lanes != 32 && s->p.force_mode == 0 && !s->p.krylov_block;
+    // odd classes (an odd number of 16-atom slots) that the occupancy heuristic merged into the
+    // next even class are planned on their own for the comparison below, so that half-warp and
+    // whole-warp columns are timed for every odd class that has atoms
+    if (half_ok) {
+        bool split = false;
+        for (int a = 0; a < s->n; ++a) {
+            const int k = (s->h_clsize[a] + 15) / 16;
+            if ((k & 1) && k < (int)s->tuned_half.size() && !s->tuned_half[k]) {
+                s->tuned_half[k] = 1;
+                split = true;
+            }
+        }
+        if (split) TRY(prepare_columns(s));
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
     int rc = 0;
     const auto launches = s->k3_launches;
-    const bool half_ok = s->p.k3_lanes != 32 && s->p.force_mode == 0 && !s->p.krylov_block;
     std::vector<char> seen(s->na_max / 16 + 1, 0);
     for (const auto& L : launches) {
         if (rc || seen[L.key]) continue;   // each class once, at its first batch
