@@ -57,7 +57,7 @@ int autotune_impl(elses_system s, cudaStream_t st) {
         for (auto& f : forms) {
             f.maxb = s->p.krylov_block ? block_krylov_blocks_per_sm(f.na, kdeg)
                      : f.half          ? krylov_half_blocks_per_sm(f.na, kdeg)
-                                       : krylov_blocks_per_sm(f.na, kdeg);
+                                       : krylov_blocks_per_sm_max(f.na, kdeg);
             maxb_all = std::max(maxb_all, f.maxb);
             const size_t per_cta = s->p.krylov_block ? block_krylov_scratch_doubles(nm, f.na)
                                                      : (size_t)kWarpsPerAtom * 2 * nm * f.na * 4;
@@ -88,7 +88,7 @@ int autotune_impl(elses_system s, cudaStream_t st) {
                 }
                 cudaEventRecord(e0, st);
                 if (s->p.krylov_block) block_krylov_columns(ka, grid, st);
-                else krylov_columns(ka, grid, st);
+                else krylov_columns(ka, grid, b, st);
                 cudaEventRecord(e1, st);
                 s->stats.launches++;
             }
@@ -130,7 +130,7 @@ int autotune_impl(elses_system s, cudaStream_t st) {
                 cudaMemsetAsync(ka.queue, 0, sizeof(int), st);
                 cudaEventRecord(e0, st);
                 if (s->p.krylov_block) block_krylov_columns(ka, grid, st);
-                else krylov_columns(ka, grid, st);
+                else krylov_columns(ka, grid, best_b, st);
                 cudaEventRecord(e1, st);
                 s->stats.launches++;
             }

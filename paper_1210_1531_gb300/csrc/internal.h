@@ -112,7 +112,8 @@ struct AdjointArgs {
     size_t bstride, bvec;   // then the forward recursion is recomputed
 };
 size_t krylov_smem_bytes(int na_max, int deg_max);
-int krylov_blocks_per_sm(int na_max, int deg_max);
+int krylov_blocks_per_sm(int na_max, int deg_max);       // resident CTAs at the 3-CTA register budget
+int krylov_blocks_per_sm_max(int na_max, int deg_max);   // with the 4-CTA form where shared memory allows
 int krylov_half_blocks_per_sm(int na_max, int deg_max);
 size_t block_krylov_scratch_doubles(int nu_max, int na_max);
 int block_krylov_blocks_per_sm(int na_max, int deg_max);
@@ -123,7 +124,7 @@ void adjoint_columns(const KrylovArgs& a, const AdjointArgs& g, int grid, cudaSt
 // gH = value of acc[0], gS = s_scale * value of acc[1] as doubles ([nnzb * 16] each)
 void adjoint_finish(const unsigned long long* acc, size_t n, double s_scale, double* gH, double* gS,
                     cudaStream_t st);
-void krylov_columns(const KrylovArgs& a, int grid, cudaStream_t st);
+void krylov_columns(const KrylovArgs& a, int grid, int ctas_per_sm, cudaStream_t st);
 
 // ---------------------------------------------------------------- a5, a6 (proj_eig.cu)
 struct EigArgs {

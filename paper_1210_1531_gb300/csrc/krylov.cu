@@ -22,6 +22,8 @@
 // reduced by recursive halving (one addition per value). The bases U and SU stay in per-CTA
 // global scratch in [k][position][orbital] order (coalesced 32-byte rows per lane). FP64
 // everywhere; no tensor cores (the work is sparse and FP64).
+#include <algorithm>
+
 #include "krylov.cuh"
 
 namespace elses {
@@ -36,8 +38,11 @@ size_t krylov_smem_bytes(int na_max, int deg_max) {
 
 // kStore: the bases of every column are kept in a.bstore (with HU, the Gram-Schmidt
 // coefficients and H') for the exact-gradient kernel, instead of the per-CTA scratch.
-template <bool kStore>
-__global__ void __launch_bounds__(kThreads, 3) k_krylov(const KrylovArgs a) {
+// kMinB: resident CTAs per SM the register budget is set for -- 3 (168 registers), or 4 (128
+// registers, a few hundred bytes of spills to L1-cached local memory) for size classes whose
+// shared memory leaves room for a fourth CTA; the autotuner times both.
+template <bool kStore, int kMinB>
+__global__ void __launch_bounds__(kThreads, kMinB) k_krylov(const KrylovArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int NA = a.na_max;
     double* vec = reinterpret_cast<double*>(smem_raw);
@@ -215,23 +220,34 @@ int krylov_half_blocks_per_sm(int na_max, int deg_max) {
 
 int krylov_blocks_per_sm(int na_max, int deg_max) {
     const size_t smem = krylov_smem_bytes(na_max, deg_max);
-    smem_at_least(k_krylov<false>, smem);
+    smem_at_least(k_krylov<false, 3>, smem);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_krylov<false>, kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_krylov<false, 3>, kThreads, smem);
     return nb;
 }
 
-void krylov_columns(const KrylovArgs& a, int grid, cudaStream_t st) {
+int krylov_blocks_per_sm_max(int na_max, int deg_max) {
+    const size_t smem = krylov_smem_bytes(na_max, deg_max);
+    smem_at_least(k_krylov<false, 4>, smem);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_krylov<false, 4>, kThreads, smem);
+    return std::max(nb, krylov_blocks_per_sm(na_max, deg_max));
+}
+
+void krylov_columns(const KrylovArgs& a, int grid, int ctas_per_sm, cudaStream_t st) {
     const size_t smem = krylov_smem_bytes(a.na_max, a.deg_max);
     if (a.half && !a.bstore) {
         smem_at_least(k_krylov_half, smem);
         k_krylov_half<<<grid, kHalfThreads, smem, st>>>(a);
     } else if (a.bstore) {
-        smem_at_least(k_krylov<true>, smem);
-        k_krylov<true><<<grid, kThreads, smem, st>>>(a);
+        smem_at_least(k_krylov<true, 3>, smem);
+        k_krylov<true, 3><<<grid, kThreads, smem, st>>>(a);
+    } else if (ctas_per_sm >= 4) {
+        smem_at_least(k_krylov<false, 4>, smem);
+        k_krylov<false, 4><<<grid, kThreads, smem, st>>>(a);
     } else {
-        smem_at_least(k_krylov<false>, smem);
-        k_krylov<false><<<grid, kThreads, smem, st>>>(a);
+        smem_at_least(k_krylov<false, 3>, smem);
+        k_krylov<false, 3><<<grid, kThreads, smem, st>>>(a);
     }
 }
 

@@ -150,8 +150,10 @@ int prepare_columns(elses_system s) {
                       : half             ? krylov_half_blocks_per_sm(na, kdeg)
                                          : krylov_blocks_per_sm(na, kdeg);
             if (bps < 1) return fail(ELSES_ERR_CAPACITY, "Krylov kernel cannot be resident (%d-atom class)", na);
-            if (s->p.k3_ctas_per_sm > 0) bps = std::min(bps, s->p.k3_ctas_per_sm);
-            else if (key < (int)s->tuned_bps.size() && s->tuned_bps[key] > 0) bps = std::min(bps, s->tuned_bps[key]);
+            // a count fixed by the caller or chosen by the autotuner may use the 4-CTA form
+            const int bps_max = (s->p.krylov_block || half) ? bps : krylov_blocks_per_sm_max(na, kdeg);
+            if (s->p.k3_ctas_per_sm > 0) bps = std::min(bps_max, s->p.k3_ctas_per_sm);
+            else if (key < (int)s->tuned_bps.size() && s->tuned_bps[key] > 0) bps = std::min(bps_max, s->tuned_bps[key]);
             const int grid = std::min(count, s->num_sms * bps);
             s->k3_launches.push_back({b, e, begin, count, na, grid, bps, half ? 1 : 0, key, batch_off});
             batch_off += s->p.krylov_block ? (size_t)grid * block_krylov_scratch_doubles(nm, na)
@@ -374,7 +376,7 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
             ka.queue = q;
         }
         if (s->p.krylov_block) block_krylov_columns(ka, L.grid, lst);
-        else krylov_columns(ka, L.grid, lst);
+        else krylov_columns(ka, L.grid, L.bps, lst);
         s->stats.launches++;
         s->stats.krylov_launches++;
     }
