@@ -131,15 +131,25 @@ __device__ __forceinline__ void st4(double* p, const double2 a, const double2 b)
     q[1] = b;
 }
 
+// Hint that the 32-byte row at p be brought into L2 (no register, no wait; in-bounds addresses
+// only), so that a later load finds it there instead of in DRAM.
+__device__ __forceinline__ void prefetch_l2(const double* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // w -= sum_{k <= n} U[:, k] h_k on the lane's rows of slot position p; the basis rows are
-// fetched eight at a time before they are used, so their latency overlaps.
+// fetched six at a time before they are used, so their latency overlaps, and the rows of the
+// next position pn (pn < 0: none) are prefetched into L2 beside them.
 __device__ __forceinline__ void sub_basis(const double* Ub, int NP, int p, const double* h, int n,
-                                          double2& w0, double2& w1) {
+                                          double2& w0, double2& w1, int pn = -1) {
     for (int k0 = 0; k0 <= n; k0 += 6) {
         double2 ua[6], ub[6];
 #pragma unroll
         for (int kk = 0; kk < 6; ++kk)
-            if (k0 + kk <= n) ld4(Ub + 4 * ((size_t)(k0 + kk) * NP + p), ua[kk], ub[kk]);
+            if (k0 + kk <= n) {
+                ld4(Ub + 4 * ((size_t)(k0 + kk) * NP + p), ua[kk], ub[kk]);
+                if (pn >= 0) prefetch_l2(Ub + 4 * ((size_t)(k0 + kk) * NP + pn));
+            }
 #pragma unroll
         for (int kk = 0; kk < 6; ++kk) {
             if (k0 + kk <= n) {
@@ -470,6 +480,9 @@ __device__ __forceinline__ int column_forward(const KrylovArgs& a, const Cluster
             for (int q = 0; q < 16; ++q) acc[q] = 0.0;
             for (int sl = 0; sl < NS; ++sl) {
                 const int p = sl * 32 + lane;
+                // the rows this chunk reads next: the next position, else the next chunk's first
+                const int pn = sl + 1 < NS ? p + 32 : lane;
+                const int kn = sl + 1 < NS ? k0 : k0 + 5;
                 double2 hu0, hu1, su0, su1;
                 ld4(P + 4 * p, hu0, hu1);
                 ld4(SUn + 4 * p, su0, su1);
@@ -477,6 +490,10 @@ __device__ __forceinline__ int column_forward(const KrylovArgs& a, const Cluster
 #pragma unroll
                 for (int kk = 0; kk < 5; ++kk) {
                     const int k = k0 + kk;
+                    if (kn + kk <= n) {
+                        prefetch_l2(Uw + (size_t)(kn + kk) * vs + 4 * pn);
+                        prefetch_l2(SUw + (size_t)(kn + kk) * vs + 4 * pn);
+                    }
                     if (k <= n) {
                         double2 u0, u1, v0, v1;
                         ld4(Uw + (size_t)k * vs + 4 * p, u0, u1);
@@ -513,13 +530,14 @@ __device__ __forceinline__ int column_forward(const KrylovArgs& a, const Cluster
                 double2 w0, w1;
                 ld4(P + 4 * p, w0, w1);
                 if (k0 == 0) {
-                    sub_basis(Uw, NP, p, h, n, w0, w1);
+                    sub_basis(Uw, NP, p, h, n, w0, w1, sl + 1 < NS ? p + NP / NS : -1);
                     st4(P + 4 * p, w0, w1);
                 }
 #pragma unroll
                 for (int kk = 0; kk < 16; ++kk) {
                     if (k0 + kk <= n) {
                         double2 v0, v1;
+                        if (sl + 1 < NS) prefetch_l2(SUw + (size_t)(k0 + kk) * vs + 4 * (p + 32));
                         ld4(SUw + (size_t)(k0 + kk) * vs + 4 * p, v0, v1);
                         acc2[kk] = fma4(v0, v1, w0, w1, acc2[kk]);
                     }
@@ -537,7 +555,7 @@ __device__ __forceinline__ int column_forward(const KrylovArgs& a, const Cluster
             const int p = sl * 32 + lane;
             double2 w0, w1;
             ld4(P + 4 * p, w0, w1);
-            sub_basis(Uw, NP, p, h, n, w0, w1);
+            sub_basis(Uw, NP, p, h, n, w0, w1, sl + 1 < NS ? p + NP / NS : -1);
             st4(P + 4 * p, w0, w1);
         }
         __syncwarp();
