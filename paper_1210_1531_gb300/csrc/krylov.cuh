@@ -138,20 +138,22 @@ __device__ __forceinline__ void prefetch_l2(const double* p) {
 }
 
 // w -= sum_{k <= n} U[:, k] h_k on the lane's rows of slot position p; the basis rows are
-// fetched six at a time before they are used, so their latency overlaps, and the rows of the
-// next position pn (pn < 0: none) are prefetched into L2 beside them.
+// fetched four at a time before they are used, so their latency overlaps, and the rows of the
+// next position pn (pn < 0: none) are prefetched into L2 beside them. (Four at a time: 87.4 ms
+// for the 4096-atom Krylov phase, against 89.7 with six and 93.4 with eight, whose registers
+// spill; two and three do as well as four.)
 __device__ __forceinline__ void sub_basis(const double* Ub, int NP, int p, const double* h, int n,
                                           double2& w0, double2& w1, int pn = -1) {
-    for (int k0 = 0; k0 <= n; k0 += 6) {
-        double2 ua[6], ub[6];
+    for (int k0 = 0; k0 <= n; k0 += 4) {
+        double2 ua[4], ub[4];
 #pragma unroll
-        for (int kk = 0; kk < 6; ++kk)
+        for (int kk = 0; kk < 4; ++kk)
             if (k0 + kk <= n) {
                 ld4(Ub + 4 * ((size_t)(k0 + kk) * NP + p), ua[kk], ub[kk]);
                 if (pn >= 0) prefetch_l2(Ub + 4 * ((size_t)(k0 + kk) * NP + pn));
             }
 #pragma unroll
-        for (int kk = 0; kk < 6; ++kk) {
+        for (int kk = 0; kk < 4; ++kk) {
             if (k0 + kk <= n) {
                 const double hk = h[k0 + kk];
                 w0.x = fma(-ua[kk].x, hk, w0.x);
