@@ -919,6 +919,9 @@ __device__ __forceinline__ int column_forward_w(const KrylovArgs& a, const Clust
             for (int q = 0; q < 16; ++q) acc[q] = 0.0;
             for (int sl = 0; sl < NS; ++sl) {
                 const int p = sl * W + lane;
+                // the rows this chunk reads next: the next position, else the next chunk's first
+                const int pn = sl + 1 < NS ? p + W : lane;
+                const int kn = sl + 1 < NS ? k0 : k0 + 5;
                 double2 hu0, hu1, su0, su1;
                 ld4(P + 4 * p, hu0, hu1);
                 ld4(SUn + 4 * p, su0, su1);
@@ -926,6 +929,10 @@ __device__ __forceinline__ int column_forward_w(const KrylovArgs& a, const Clust
 #pragma unroll
                 for (int kk = 0; kk < 5; ++kk) {
                     const int k = k0 + kk;
+                    if (kn + kk <= n) {
+                        prefetch_l2(Uw + (size_t)(kn + kk) * vs + 4 * pn);
+                        prefetch_l2(SUw + (size_t)(kn + kk) * vs + 4 * pn);
+                    }
                     if (k <= n) {
                         double2 u0, u1, v0, v1;
                         ld4(Uw + (size_t)k * vs + 4 * p, u0, u1);
@@ -962,13 +969,14 @@ __device__ __forceinline__ int column_forward_w(const KrylovArgs& a, const Clust
                 double2 w0, w1;
                 ld4(P + 4 * p, w0, w1);
                 if (k0 == 0) {
-                    sub_basis(Uw, NP, p, h, n, w0, w1);
+                    sub_basis(Uw, NP, p, h, n, w0, w1, sl + 1 < NS ? p + W : -1);
                     st4(P + 4 * p, w0, w1);
                 }
 #pragma unroll
                 for (int kk = 0; kk < 16; ++kk) {
                     if (k0 + kk <= n) {
                         double2 v0, v1;
+                        if (sl + 1 < NS) prefetch_l2(SUw + (size_t)(k0 + kk) * vs + 4 * (p + W));
                         ld4(SUw + (size_t)(k0 + kk) * vs + 4 * p, v0, v1);
                         acc2[kk] = fma4(v0, v1, w0, w1, acc2[kk]);
                     }
@@ -986,7 +994,7 @@ __device__ __forceinline__ int column_forward_w(const KrylovArgs& a, const Clust
             const int p = sl * W + lane;
             double2 w0, w1;
             ld4(P + 4 * p, w0, w1);
-            sub_basis(Uw, NP, p, h, n, w0, w1);
+            sub_basis(Uw, NP, p, h, n, w0, w1, sl + 1 < NS ? p + W : -1);
             st4(P + 4 * p, w0, w1);
         }
         __syncwarp(gm);
