@@ -46,7 +46,7 @@ RHO_GATE = 1e-10                             # |delta rho_ij| against the same-a
 # DRAM bytes (read + write) of the k_krylov launches of one 4096-atom step from one ncu capture,
 # valid for the Krylov source whose sha256 prefix (krylov.cu + krylov.cuh) is given; reported
 # per launch, and null once that source changes
-KRYLOV_TRAFFIC = {"krylov_sha256_prefix": "6a1b8bbf40fae333", "bytes_per_step": 183.48e9,
+KRYLOV_TRAFFIC = {"krylov_sha256_prefix": "ffcb50a4b37d1792", "bytes_per_step": 195.57e9,
                   "launches_per_step": 2}
 # further systems timed after the main one: (steps, warm-up steps, plain-form steps, plain-form
 # warm-up steps, sampled columns checked against the oracle)
