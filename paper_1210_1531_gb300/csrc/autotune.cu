@@ -157,6 +157,7 @@ int autotune_impl(elses_system s, cudaStream_t st) {
 extern "C" {
 
 int elses_autotune(elses_system s, int run, int max_classes, int* classes_out, int* n_host, void* stream) {
+    NvtxRange nvtx_range("elses_autotune");
     TRY(check_built(s));
     if (max_classes < 0 || (max_classes > 0 && !classes_out)) return fail(ELSES_ERR_ARG, "bad class output");
     if (run) {

@@ -627,6 +627,7 @@ int energy_force_eager(elses_system s, double* mu_host, double* e_band_host, dou
 extern "C" {
 
 int elses_density_matrix(elses_system s, double mu, double* rho_dev, double* rhoE_dev, void* stream) {
+    NvtxRange nvtx_range("elses_density_matrix");
     TRY(check_built(s));
     if (!rho_dev) return fail(ELSES_ERR_ARG, "null rho");
     cudaStream_t st = (cudaStream_t)stream;
@@ -636,6 +637,7 @@ int elses_density_matrix(elses_system s, double mu, double* rho_dev, double* rho
 
 int elses_energies(elses_system s, double mu, double* n_host, double* e_band_host, double* omega_host,
                    double* f_free_host, void* stream) {
+    NvtxRange nvtx_range("elses_energies");
     TRY(check_built(s));
     cudaStream_t st = (cudaStream_t)stream;
     if (s->atoms_done != s->n) return fail(ELSES_ERR_STATE, "energies need every column");
@@ -675,6 +677,7 @@ void elses_system_destroy(elses_system s) {
 int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
                          const double* box_host, const elses_sk* sk, const elses_params* params,
                          void* stream) {
+    NvtxRange nvtx_range("elses_build_clusters");
     cudaStream_t st = (cudaStream_t)stream;
     if (!sys || !pos_dev || !box_host || !sk || !params) return fail(ELSES_ERR_ARG, "null argument");
     if (n_atoms <= 0) return fail(ELSES_ERR_ARG, "n_atoms must be positive");
@@ -909,6 +912,7 @@ static int adopt_pattern(elses_system s, int nnzb, const int* row_ptr_dev, const
 
 int elses_set_hs(elses_system s, int nnzb, const int* row_ptr_dev, const int* col_idx_dev, const double* H_dev,
                  const double* S_dev, void* stream) {
+    NvtxRange nvtx_range("elses_set_hs");
     TRY(check_built(s));
     if (!H_dev || !S_dev) return fail(ELSES_ERR_ARG, "null H or S");
     if ((row_ptr_dev == nullptr) != (col_idx_dev == nullptr))
@@ -934,6 +938,7 @@ int elses_set_hs(elses_system s, int nnzb, const int* row_ptr_dev, const int* co
 
 int elses_green_columns(elses_system s, int col_begin, int col_end, int n_z, const double* z_host,
                         double* G_dev, int* nu_eff_dev, void* stream) {
+    NvtxRange nvtx_range("elses_green_columns");
     TRY(check_built(s));
     cudaStream_t st = (cudaStream_t)stream;
     if (col_begin < 0 || col_end > s->M || col_begin > col_end || col_begin % 4 || col_end % 4)
@@ -979,6 +984,7 @@ int elses_green_columns(elses_system s, int col_begin, int col_end, int n_z, con
 }
 
 int elses_find_mu(elses_system s, double* mu_host, double* n_at_mu_host, void* stream) {
+    NvtxRange nvtx_range("elses_find_mu");
     TRY(check_built(s));
     cudaStream_t st = (cudaStream_t)stream;
     if (s->atoms_done != s->n) return fail(ELSES_ERR_STATE, "find_mu needs every column (call green_columns first)");
@@ -1016,6 +1022,7 @@ int elses_find_mu(elses_system s, double* mu_host, double* n_at_mu_host, void* s
 
 int elses_energy_force(elses_system s, double* mu_host, double* e_band_host, double* f_free_host,
                        double* forces_dev, void* stream) {
+    NvtxRange nvtx_range("elses_energy_force");
     TRY(check_built(s));
     cudaStream_t st = (cudaStream_t)stream;
     if (forces_dev && s->user_hs) return fail(ELSES_ERR_STATE, "forces need the Slater-Koster H, S");
@@ -1025,6 +1032,7 @@ int elses_energy_force(elses_system s, double* mu_host, double* e_band_host, dou
 
 int elses_cohp_spectrum(elses_system s, int n_z, const double* z_host, double* C_dev, double* Csig_dev,
                         double* Cpi_dev, double* dos_host, void* stream) {
+    NvtxRange nvtx_range("elses_cohp_spectrum");
     TRY(check_built(s));
     if (n_z <= 0 || !z_host) return fail(ELSES_ERR_ARG, "need n_z > 0 energies");
     if (!C_dev && !Csig_dev && !Cpi_dev && !dos_host) return fail(ELSES_ERR_ARG, "no output requested");
@@ -1090,6 +1098,7 @@ int elses_cohp_spectrum(elses_system s, int n_z, const double* z_host, double* C
 
 int elses_omega_gradient(elses_system s, double mu, int atom_begin, int atom_end, double* dH_dev,
                          double* dS_dev, void* stream) {
+    NvtxRange nvtx_range("elses_omega_gradient");
     TRY(check_built(s));
     if (!dH_dev || !dS_dev) return fail(ELSES_ERR_ARG, "null gradient outputs");
     if (atom_begin < 0 || atom_end > s->n || atom_begin > atom_end)
@@ -1106,6 +1115,7 @@ int elses_omega_gradient(elses_system s, double mu, int atom_begin, int atom_end
 }
 
 int elses_forces(elses_system s, double* forces_dev, void* stream) {
+    NvtxRange nvtx_range("elses_forces");
     TRY(check_built(s));
     if (!forces_dev) return fail(ELSES_ERR_ARG, "null forces");
     if (s->user_hs) return fail(ELSES_ERR_STATE, "forces need the Slater-Koster H, S");
@@ -1131,6 +1141,7 @@ int elses_forces(elses_system s, double* forces_dev, void* stream) {
 
 int elses_icohp(elses_system s, const double* rho_dev, double* B_dev, double* Bsig_dev, double* Bpi_dev,
                 void* stream) {
+    NvtxRange nvtx_range("elses_icohp");
     TRY(check_built(s));
     if (!rho_dev || !B_dev) return fail(ELSES_ERR_ARG, "null rho or B");
     if ((Bsig_dev || Bpi_dev) && s->user_hs)

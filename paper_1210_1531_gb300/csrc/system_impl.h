@@ -10,12 +10,23 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 
 namespace elses {
 // Records the message of the last error (elses_last_error) and returns code.
 int fail(int code, const char* fmt, ...);
+
+// An NVTX range over one library call, named after the call (shown by Nsight Systems and other
+// NVTX tools; header-only NVTX 3, a no-op when no tool is attached). Closed on every return.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 }  // namespace elses
 
 #define CUDA_TRY(x)                                                                        \
