@@ -130,6 +130,26 @@ def test_two_pass_equals_stored(eg, d64):
     assert np.array_equal(gu.to_np(rho), d64["rho"]) and np.array_equal(gu.to_np(F), d64["F"])
 
 
+def test_two_pass_equals_stored_in_batches(eg):
+    """The same workflow invariance with the columns streamed in batches (the 4096-atom system in
+    four batches of 1024 atoms, the form the 10^6-atom system runs in). The stored workflow
+    forms V per batch and takes the spectra as Q^T z; the memory-saving one keeps only the
+    spectra in its first calculation of G (the rotation replay) and recomputes each batch for the
+    density. So they agree to rounding, not bit for bit: mu to the bisection's resolution,
+    energies and rho to 1e-12 relative."""
+    w = wl.make("diamond_4096")
+    a = eg.system_for(w, batch_atoms=1024)
+    b = eg.system_for(w, batch_atoms=1024, two_pass=True)
+    ra, rb = a.energy_force(), b.energy_force()
+    assert abs(ra[0] - rb[0]) <= 3e-13
+    assert abs(ra[1] - rb[1]) <= 1e-12 * abs(ra[1]) and abs(ra[2] - rb[2]) <= 1e-12 * abs(ra[2])
+    Fa, Fb = gu.to_np(ra[3]), gu.to_np(rb[3])
+    assert np.abs(Fa - Fb).max() <= 1e-10 * np.abs(Fa).max()
+    for x, y in zip(a.density_matrix(ra[0]), b.density_matrix(ra[0])):
+        x, y = gu.to_np(x), gu.to_np(y)
+        assert np.abs(x - y).max() <= 1e-12 * np.abs(x).max()
+
+
 def test_factor_density_equals_formed_V(eg, d64):
     """One batch of every atom leaves V unformed: the spectra come from the rotation replay and
     t = V w from the eigen-factors (rotations, reflectors, L^-T). Several batches form V, with
