@@ -38,15 +38,16 @@ sys.path.insert(0, ROOT)
 METRIC = "Green's-fn columns/sec & energy+force steps/sec at |drho|<=1e-10, batched vs plain"
 WORKLOAD = "diamond_4096"
 DESCRIPTION = {"diamond_4096": "disordered diamond (8x8x8 cells, sigma 0.1 A)",
+               "diamond_512": "disordered diamond (4x4x4 cells, sigma 0.1 A)",
                "composite_32768": "graphite with diamond grains (sp2-sp3 composite)",
                "amorphous_1m": "dense disordered carbon (3.0 g/cm3, sigma 0.3 A)",
                "diamond_64": "disordered diamond (2x2x2 cells, sigma 0.05 A)"}
 FP64_NOMINAL_GFLOPS = 152 * 2 * 2 * 2.07     # SMs x FP64 FMA/clk/SM x 2 flops x GHz
-RHO_GATE = 1e-10                             # |delta rho_ij| against the same-algorithm oracle
+RHO_GATE = 1e-10                             # |delta rho_ij| against the oracle
 # DRAM bytes (read + write) of the k_krylov launches of one 4096-atom step from one ncu capture,
-# valid for the Krylov source whose sha256 prefix (krylov.cu + krylov.cuh) is given; reported
-# per launch, and null once that source changes
-KRYLOV_TRAFFIC = {"krylov_sha256_prefix": "ffcb50a4b37d1792", "bytes_per_step": 195.57e9,
+# valid for the Krylov source whose sha256 prefix (krylov.cu + krylov.cuh) and Gram-Schmidt
+# setting (reorth) are given; reported per launch, and null once either changes
+KRYLOV_TRAFFIC = {"krylov_sha256_prefix": "859d093f58184039", "reorth": 1, "bytes_per_step": 115.01e9,
                   "launches_per_step": 2}
 # further systems timed after the main one: (steps, warm-up steps, plain-form steps, plain-form
 # warm-up steps, sampled columns checked against the oracle)
@@ -66,6 +67,9 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the composite and 10^6-atom systems reported beside the main one")
     ap.add_argument("--k3-ctas", type=int, default=0, help="Krylov CTAs per SM (0: as many as fit)")
+    ap.add_argument("--reorth", type=int, default=1, choices=[0, 1],
+                    help="second Gram-Schmidt pass: 0 a second classical pass (CGS2), 1 its "
+                         "coefficients from the projected overlap S' (one sweep of the basis)")
     ap.add_argument("--no-exact", action="store_true",
                     help="skip the energy + exact-force step (gradient through the truncated Krylov build)")
     return ap.parse_args()
@@ -232,13 +236,13 @@ def aggregate(ms_local, units_local, world, dist=None, device=None):
     return ms, float(u.item()) / (ms * 1e-3)
 
 
-def krylov_traffic():
+def krylov_traffic(reorth):
     import hashlib
     h = hashlib.sha256()
     for name in ("krylov.cu", "krylov.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1210_1531_gb300", "csrc", name), "rb").read())
     h = h.hexdigest()[:16]
-    if h != KRYLOV_TRAFFIC["krylov_sha256_prefix"]:
+    if h != KRYLOV_TRAFFIC["krylov_sha256_prefix"] or reorth != KRYLOV_TRAFFIC["reorth"]:
         return None
     return KRYLOV_TRAFFIC["bytes_per_step"] / KRYLOV_TRAFFIC["launches_per_step"]
 
@@ -248,13 +252,19 @@ STAT_KEYS = ("launches", "krylov_launches", "t_krylov_ms", "t_eig_ms", "t_bisect
 PHASES = ("t_krylov_ms", "t_eig_ms", "t_bisect_ms", "t_density_ms", "t_force_ms")
 
 
+GRAM_SCHMIDT = {0: "two classical passes in the S inner product (CGS2)",
+                1: "first pass classical; the second pass's coefficients from the projected "
+                   "overlap S' (-(S' - I) h), both subtracted in one sweep of the basis"}
+
+
 class Runner:
     """One workload on the current device: Systems of it, and their timed energy + force steps
     (each step: rebuild at the resident positions, then elses_energy_force)."""
 
-    def __init__(self, eg, w, k3_ctas, stream, flush):
+    def __init__(self, eg, w, k3_ctas, stream, flush, reorth=0):
         import torch
         self.eg, self.w, self.k3_ctas, self.stream, self.flush = eg, w, k3_ctas, stream, flush
+        self.reorth = reorth
         self.pos_dev = torch.tensor(w.pos, dtype=torch.float64, device="cuda")
         self.forces = torch.empty((w.n_atoms, 3), dtype=torch.float64, device="cuda")
 
@@ -263,7 +273,8 @@ class Runner:
         return self.eg.System(self.pos_dev, w.box, w.sk, w.r_cluster, w.nu, w.kT, w.n_electrons,
                               nu_classes=w.nu_classes, schedule=schedule, timing=True,
                               k3_ctas_per_sm=self.k3_ctas, exact_forces=exact_forces,
-                              autotune=autotune and self.k3_ctas == 0, graph=graph)
+                              autotune=autotune and self.k3_ctas == 0, graph=graph,
+                              reorth=self.reorth)
 
     def step(self, s):
         s.rebuild(self.pos_dev)
@@ -319,14 +330,14 @@ def shapes(tuned):
     return {f"{k}-atom clusters": f"{b} CTAs/SM, queue by {o}" for k, (b, o) in tuned.items()}
 
 
-def extra_record(eg, wl, name, k3_ctas, stream, flush, peak_probe, check):
+def extra_record(eg, wl, name, k3_ctas, stream, flush, peak_probe, check, reorth=0):
     """A further system in the production form against the plain form, with the Krylov roofline
     and the library's rho on seeded columns checked against the oracle (cpu_baseline leg)."""
     import numpy as np
     steps, warm, p_steps, p_warm, n_check = EXTRA[name]
     w = wl.make(name)
     M = 4 * w.n_atoms
-    r = Runner(eg, w, k3_ctas, stream, flush)
+    r = Runner(eg, w, k3_ctas, stream, flush, reorth)
     batched = r.make(1, autotune=True, graph=True)
     tuned = batched.autotune_shapes()
     times, stats, out = r.timed(batched, steps, warm)
@@ -381,7 +392,7 @@ def run_ours(args):
     M = 4 * w.n_atoms
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    r = Runner(eg, w, args.k3_ctas, stream, flush)
+    r = Runner(eg, w, args.k3_ctas, stream, flush, args.reorth)
 
     # the production form: launch shape tuned at build (before timing), the step replayed as a
     # CUDA graph (captured during the warm-up steps)
@@ -448,7 +459,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_extra:
         for name in EXTRA:
             extra[name] = extra_record(eg, wl, name, args.k3_ctas, stream, flush, peak_probe,
-                                       not args.no_cpu_baseline)
+                                       not args.no_cpu_baseline, args.reorth)
 
     if world > 1:
         dist.destroy_process_group()
@@ -463,13 +474,14 @@ def run_ours(args):
         "plain": {"ms_per_step": plain_ms, "value": M / (plain_ms * 1e-3), "unit": "columns/s"},
         "exact_forces": exact,
         "autotuned_shapes": shapes(tuned),
+        "gram_schmidt": GRAM_SCHMIDT[args.reorth],
         "phases_ms_per_step": {k: stats[k] / args.steps for k in PHASES},
         "e2e": {"value": e2e_value, "unit": "columns/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(pos_host.numel() * 8),
                 "d2h_bytes_per_step": int(f_host.numel() * 8 + 3 * 8)},
         "gpu_launches": int(stats["launches"]),
         "roofline": dict(roofline(stats, peak_probe,
-                                  krylov_traffic() if args.workload == WORKLOAD else None),
+                                  krylov_traffic(args.reorth) if args.workload == WORKLOAD else None),
                          ctas_per_sm=batched_stats["k3_ctas_per_sm"],
                          launches_per_step=stats["krylov_launches"] / args.steps),
         "clocks": clk.summary(),

@@ -109,6 +109,16 @@ typedef struct elses_params {
                                32 = one warp per column always                                   */
     int    max_qr_sweeps;   /* cap on the implicit-shift QR sweeps of one projected eigenproblem
                                (0: 30 nu); a column that needs more sets ELSES_ERR_TIMEOUT       */
+    int    reorth;          /* second Gram-Schmidt pass of the per-column spaces: 0 = a second
+                               classical pass, h2 = SU^T w (CGS2); 1 = its coefficients from the
+                               projected overlap already formed, h2 = -(S' - I) h1 (equal to
+                               SU^T (w - U h1) in exact arithmetic), so that both passes
+                               subtract U (h1 + h2) in one sweep of the basis. The two spaces
+                               agree to rounding; the results follow S' and H' formed from the
+                               basis itself, so they agree to rounding too, and so does the
+                               exact gradient (it differentiates the recursion in exact
+                               arithmetic, where the second pass vanishes). Block spaces
+                               (krylov_block) always use 0.                                    */
 } elses_params;
 
 /* Counters and event timings of the calls since the last build (timing = 1 for the times). */
@@ -130,7 +140,8 @@ typedef struct elses_stats {
                                shared by the H and the S block, 19 each -- 64 for two dense 4x4
                                blocks; on-site H diagonal 4 per atom, on-site S = I none) plus
                                CGS2 and projection sum_{n<nu}(6(n+1)+2) n_c
-                               + sum_{n<nu-1}(6(n+1)+4) n_c, n_c = 4 |cluster|               */
+                               + sum_{n<nu-1}(6(n+1)+4) n_c, n_c = 4 |cluster|; with reorth = 1
+                               the second sum is sum_{n<nu-1}((2(n+1)+4) n_c + 2(n+1)^2)     */
     double t_adjoint_ms;    /* exact-gradient kernels (elses_omega_gradient)                  */
     double adjoint_flops;   /* algorithmic FP64 flops of the exact-gradient kernels: per column
                                (nu = nu_eff, n_c, b_off in-cluster blocks applied from the

@@ -495,12 +495,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_adjoint(const KrylovArgs a, con
             const unsigned long long blocks = nent + (onsite ? nat : 0ull);
             unsigned long long f = 8ull * vv * vv * nc + 6ull * vv * vv * vv + 64ull * vv * blocks;
             f += (vv - 1) * (8ull * nc + per * nent + (onsite ? 4ull * nat : 0ull)) + 5ull * nc * vv * (vv - 1);
-            if (!g.bstore) {   // the forward recursion recomputed: the Krylov kernel's count
-                const unsigned long long pair = a.skr ? 43ull : 64ull;   // H and S products of a block
-                const unsigned long long spm = onsite ? vv * (pair * nent + 4ull * nat) : vv * pair * nent;
-                const unsigned long long tri = vv * (vv + 1) / 2, trim = (vv - 1) * vv / 2;
-                f += spm + nc * (6 * tri + 2 * vv) + nc * (6 * trim + 4 * (vv - 1));
-            }
+            if (!g.bstore)   // the forward recursion recomputed: the Krylov kernel's count
+                f += column_flops(a, v.n_at, v.nent, nv, a.reorth != 0);
             atomicAdd(g.flops, f);
         }
         if (lane == 0) {

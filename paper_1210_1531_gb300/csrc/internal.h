@@ -67,6 +67,7 @@ struct KrylovArgs {
     int class_max_atoms[4];
     int class_nu[4];
     double breakdown_tol;
+    int reorth;             // 1: second-pass coefficients from S' (elses_params.reorth)
     int onsite_diag;        // 1: on-site S blocks are I and on-site H blocks diagonal
     int na_max;             // cluster capacity: a multiple of 32 (of 16 with half)
     int half;               // 1: two columns per warp, one per half-warp (k_krylov_half)

@@ -11,7 +11,10 @@
 // Hw and Sw formed in one pass over the cluster; the oracle forms S u_{n+1} and H u_{n+1} by
 // products, which agree to rounding). H'[k][n] = u_k . HU_n and S'[k][n] = u_k . SU_n are formed
 // for k <= n as the columns appear (the oracle symmetrises full products; same values to
-// rounding).
+// rounding). With KrylovArgs::reorth = 1 the second pass takes its coefficients from S'
+// instead of a second product with SU (second_pass_from_overlap, krylov.cuh) and one sweep of
+// the basis subtracts both passes: the same space to rounding, with a third fewer basis reads
+// and dense flops.
 //
 // GB300 layout: one CTA of 4 warps per atom J, one warp per orbital column alpha; the CTA
 // builds an ELL view of the cluster sub-matrix (atoms sorted by in-cluster degree and assigned
@@ -101,22 +104,7 @@ __global__ void __launch_bounds__(kThreads, kMinB) k_krylov(const KrylovArgs a) 
             if (lane == 0) {
                 a.nu_eff[j] = nu_eff;
                 if (nu_eff < nu) flag(a.status, DEV_BREAKDOWN);
-                if (a.flops) {
-                    // sparse products: nu_eff of H and S together, per off-site block 43 flops
-                    // in the two-centre form (the projection t = u.x_p, 5 flops, shared by the two
-                    // blocks of 19) or 64 as two dense blocks, on-site H diagonal 4 per atom,
-                    // on-site S = I none; dense CGS2 +
-                    // projection: sum_{n<nu}(6(n+1)+2) n_c + sum_{n<nu-1}(6(n+1)+4) n_c
-                    const bool onsite = a.onsite_diag != 0;
-                    const unsigned long long nent = (unsigned long long)v.nent;
-                    const unsigned long long nc = 4ull * n_at, vv = (unsigned long long)nu_eff;
-                    const unsigned long long pair = a.skr ? 43ull : 64ull;   // flops per block pair (H, S)
-                    const unsigned long long spm = onsite ? vv * (pair * nent + 4ull * n_at) : vv * pair * nent;
-                    const unsigned long long tri = vv * (vv + 1) / 2;          // sum_{n<v} (n+1)
-                    const unsigned long long trim = vv > 0 ? (vv - 1) * vv / 2 : 0;  // sum_{n<v-1} (n+1)
-                    const unsigned long long dense = nc * (6 * tri + 2 * vv) + (vv > 0 ? nc * (6 * trim + 4 * (vv - 1)) : 0);
-                    atomicAdd(a.flops, spm + dense);
-                }
+                if (a.flops) atomicAdd(a.flops, column_flops(a, n_at, v.nent, nu_eff, a.reorth != 0));
             }
             __syncwarp();
             // pattern rows of U for rho / G: blocks e = (J, I) of row J, orbital r of atom I
@@ -182,17 +170,7 @@ __global__ void __launch_bounds__(kHalfThreads, 6) k_krylov_half(const KrylovArg
             if (lane == 0) {
                 a.nu_eff[j] = nu_eff;
                 if (nu_eff < nu) flag(a.status, DEV_BREAKDOWN);
-                if (a.flops) {   // the same algorithmic count as k_krylov
-                    const bool onsite = a.onsite_diag != 0;
-                    const unsigned long long nent = (unsigned long long)v.nent;
-                    const unsigned long long nc = 4ull * n_at, vv = (unsigned long long)nu_eff;
-                    const unsigned long long pair = a.skr ? 43ull : 64ull;
-                    const unsigned long long spm = onsite ? vv * (pair * nent + 4ull * n_at) : vv * pair * nent;
-                    const unsigned long long tri = vv * (vv + 1) / 2;
-                    const unsigned long long trim = vv > 0 ? (vv - 1) * vv / 2 : 0;
-                    const unsigned long long dense = nc * (6 * tri + 2 * vv) + (vv > 0 ? nc * (6 * trim + 4 * (vv - 1)) : 0);
-                    atomicAdd(a.flops, spm + dense);
-                }
+                if (a.flops) atomicAdd(a.flops, column_flops(a, n_at, v.nent, nu_eff, a.reorth != 0));
             }
             __syncwarp(gm);
             if (a.UP) {

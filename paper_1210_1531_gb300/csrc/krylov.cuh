@@ -402,6 +402,62 @@ __device__ __forceinline__ bool cluster_view(const KrylovArgs& a, int J, int NA,
     return true;
 }
 
+// Algorithmic FP64 flops of one column. Sparse products: nu_eff of H and S together, per
+// off-site block 43 flops in the two-centre form (the projection t = u . x_p, 5 flops, shared by
+// the two blocks of 19) or 64 as two dense blocks, the on-site H diagonal 4 per atom, the
+// on-site S = I none. Dense work over the n_c = 4 n_at rows: per step n < nu_eff, pass A's three
+// products and ||H u_n||^2, (6 (n+1) + 2) n_c; per step n < nu_eff - 1, the Gram-Schmidt
+// updates and second-pass products, 6 (n+1) n_c with two classical passes or 2 (n+1) n_c +
+// 2 (n+1)^2 with the second pass from S', then w^T S w and the scaling of u and S u, 4 n_c.
+__device__ __forceinline__ unsigned long long column_flops(const KrylovArgs& a, int n_at, int nent, int nu_eff,
+                                                           bool from_overlap) {
+    const unsigned long long ne = (unsigned long long)nent, na = (unsigned long long)n_at;
+    const unsigned long long nc = 4ull * na, vv = (unsigned long long)nu_eff;
+    const unsigned long long pair = a.skr ? 43ull : 64ull;   // flops per block pair (H, S)
+    const unsigned long long spm = a.onsite_diag ? vv * (pair * ne + 4ull * na) : vv * pair * ne;
+    const unsigned long long tri = vv * (vv + 1) / 2;                 // sum_{n<v} (n+1)
+    const unsigned long long trim = vv > 0 ? (vv - 1) * vv / 2 : 0;   // sum_{n<v-1} (n+1)
+    const unsigned long long sq = vv > 0 ? (vv - 1) * vv * (2 * vv - 1) / 6 : 0;   // sum_{n<v-1} (n+1)^2
+    unsigned long long dense = nc * (6 * tri + 2 * vv);
+    if (vv > 0) dense += from_overlap ? nc * (2 * trim + 4 * (vv - 1)) + 2 * sq : nc * (6 * trim + 4 * (vv - 1));
+    return spm + dense;
+}
+
+// The second Gram-Schmidt pass from the projected overlap (KrylovArgs::reorth = 1). With
+// E = S' - I over k, q <= n (S' packed upper at sp, this step's column already written), the
+// second pass's coefficients SU^T (w - U h) equal -E h in exact arithmetic, since SU^T U = S'.
+// So h becomes h - E h, the coefficients of both passes together, and one sweep of the basis
+// subtracts them. S'_kk - 1 is exact (S'_kk is within rounding of 1). Lane l of the group of
+// W lanes (mask m) forms the values k = l, l + W, ...; every lane must call.
+template <int W>
+__device__ __forceinline__ void second_pass_from_overlap(const double* __restrict__ sp, double* h, int n,
+                                                        int lane, unsigned m) {
+    constexpr int KR = kMaxNu / W;
+    double g[KR];
+#pragma unroll
+    for (int r = 0; r < KR; ++r) {
+        const int k = lane + r * W;
+        g[r] = 0.0;
+        if (k <= n) {
+            double eh = 0.0;
+            for (int q = 0; q <= n; ++q) {
+                const int lo = min(k, q), hi = max(k, q);
+                double e = sp[lo + hi * (hi + 1) / 2];
+                if (q == k) e -= 1.0;
+                eh = fma(e, h[q], eh);
+            }
+            g[r] = h[k] - eh;
+        }
+    }
+    __syncwarp(m);
+#pragma unroll
+    for (int r = 0; r < KR; ++r) {
+        const int k = lane + r * W;
+        if (k <= n) h[k] = g[r];
+    }
+    __syncwarp(m);
+}
+
 // Forward Krylov recursion of column j = 4 J + alpha by one warp (the reading of the module
 // header of krylov.cu): leaves U and SU in Uw, SUw ([k][position][orbital]) and writes H', S'
 // (packed upper) and row j of U, SU, HU of the column. With kAdj it also keeps HU in HUw and the
@@ -521,9 +577,12 @@ __device__ __forceinline__ int column_forward(const KrylovArgs& a, const Cluster
         }
         if (n == nu - 1) break;
         __syncwarp();
+        const bool from_overlap = a.reorth != 0;
+        if (from_overlap) second_pass_from_overlap<32>(a.Sp + (size_t)col * PK, h, n, lane, 0xffffffffu);
         // sweep B: w = hu - U h (first pass) and the second-pass coefficients SU^T w,
-        // sixteen k at a time (the first sixteen in the same sweep as the update)
-        for (int k0 = 0; k0 <= n; k0 += 16) {
+        // sixteen k at a time (the first sixteen in the same sweep as the update); with the
+        // second pass from S', sweep C alone subtracts both passes
+        for (int k0 = 0; k0 <= (from_overlap ? -1 : n); k0 += 16) {
             double acc2[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) acc2[q] = 0.0;
@@ -958,9 +1017,12 @@ __device__ __forceinline__ int column_forward_w(const KrylovArgs& a, const Clust
         }
         if (n == nu - 1) break;
         __syncwarp(gm);
+        const bool from_overlap = a.reorth != 0;
+        if (from_overlap) second_pass_from_overlap<W>(a.Sp + (size_t)col * PK, h, n, lane, gm);
         // sweep B: w = hu - U h (first pass) and the second-pass coefficients SU^T w,
-        // sixteen k at a time (the first sixteen in the same sweep as the update)
-        for (int k0 = 0; k0 <= n; k0 += 16) {
+        // sixteen k at a time (the first sixteen in the same sweep as the update); with the
+        // second pass from S', sweep C alone subtracts both passes
+        for (int k0 = 0; k0 <= (from_overlap ? -1 : n); k0 += 16) {
             double acc2[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) acc2[q] = 0.0;

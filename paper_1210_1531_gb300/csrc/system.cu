@@ -270,6 +270,7 @@ KrylovArgs krylov_args(elses_system s, int b, int e) {
         ka.class_nu[c] = s->p.class_nu[c];
     }
     ka.breakdown_tol = s->p.breakdown_tol;
+    ka.reorth = s->p.krylov_block ? 0 : s->p.reorth;   // the block build has its own passes
     ka.onsite_diag = s->user_hs ? 0 : 1;   // Slater-Koster on-site blocks: S = I, H diagonal
     ka.deg_max = s->user_hs ? s->max_nb : s->deg_cap;
     ka.scratch = s->kscratch.p;
@@ -697,6 +698,7 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
     if (p.batch_atoms < 0) return fail(ELSES_ERR_ARG, "batch_atoms must be >= 0");
     if (p.k3_lanes != 0 && p.k3_lanes != 32) return fail(ELSES_ERR_ARG, "k3_lanes must be 0 or 32");
     if (p.max_qr_sweeps < 0) return fail(ELSES_ERR_ARG, "max_qr_sweeps must be >= 0");
+    if (p.reorth != 0 && p.reorth != 1) return fail(ELSES_ERR_ARG, "reorth must be 0 or 1");
     if (p.krylov_block) {
         if (p.nu < 4) return fail(ELSES_ERR_ARG, "a block space needs nu >= 4");
         for (int c = 0; c < p.n_classes; ++c)

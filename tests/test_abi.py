@@ -52,3 +52,32 @@ def test_loads_without_gpu_and_reports_version(libpath):
     # argument checks happen before any device call
     L.elses_build_clusters.restype = ctypes.c_int
     assert L.elses_build_clusters(None, 0, None, None, None, None, None) == -1
+
+
+def _header_fields(struct):
+    """(name, C type, array length) of the members of `struct` in include/elses.h, in order."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (struct, struct), text, re.S).group(1)
+    out = []
+    for decl in filter(None, (d.strip() for d in body.split(";"))):
+        m = re.match(r"(long long|double|int)\s+(.*)$", decl, re.S)
+        assert m, decl
+        for item in m.group(2).split(","):
+            a = re.match(r"\s*(\w+)\s*(?:\[(\d+)\])?\s*$", item)
+            out.append((a.group(1), m.group(1), int(a.group(2)) if a.group(2) else 0))
+    return out
+
+
+@pytest.mark.parametrize("struct, cls", [("elses_sk", "SK"), ("elses_params", "Params"),
+                                         ("elses_stats", "Stats")])
+def test_binding_structs_match_the_header(struct, cls):
+    """The ctypes mirrors of the header's structs have the same members, types and order."""
+    import paper_1210_1531_gb300 as eg
+    ctype = {"double": ctypes.c_double, "int": ctypes.c_int, "long long": ctypes.c_longlong}
+    want = []
+    for name, t, n in _header_fields(struct):
+        want.append((name, ctype[t] * n if n else ctype[t]))
+    got = getattr(eg, cls)._fields_
+    assert [n for n, _ in got] == [n for n, _ in want]
+    for (n, a), (_, b) in zip(got, want):
+        assert ctypes.sizeof(a) == ctypes.sizeof(b) and getattr(a, "_type_", a) == getattr(b, "_type_", b), n

@@ -271,6 +271,8 @@ def make(name: str) -> Workload:
     """The named synthetic workloads.
 
     diamond_64       64-atom diamond (2x2x2 cells), sigma 0.05 A, cluster = whole system, nu 30
+    diamond_512      512-atom diamond (4x4x4 cells), sigma 0.1 A, cluster radius 6 A, nu 30: the
+                     per-column work of diamond_4096 at an eighth of the columns (profiling size)
     diamond_4096     4096-atom diamond (8x8x8 cells), sigma 0.1 A, cluster radius 6 A, nu 30
     composite_32768  32768-atom graphite + diamond grains, cluster radius 6 A, nu 20/30/40 by size
                      (<= 100 cluster atoms: graphite interior; <= 140: grain boundaries; larger:
@@ -281,6 +283,9 @@ def make(name: str) -> Workload:
     if name == "diamond_64":
         pos, box = diamond((2, 2, 2), sigma=0.05)
         return Workload(name, pos, box, sk, r_cluster=0.0, nu=30)
+    if name == "diamond_512":
+        pos, box = diamond((4, 4, 4), sigma=0.1)
+        return Workload(name, pos, box, sk, r_cluster=6.0, nu=30)
     if name == "diamond_4096":
         pos, box = diamond((8, 8, 8), sigma=0.1)
         return Workload(name, pos, box, sk, r_cluster=6.0, nu=30)
