@@ -267,12 +267,15 @@ __global__ void __launch_bounds__(kChaseThreads) k_eig_chase(const EigArgs a) {
     const double eps = 2.220446049250313e-16;
     int hi = nu - 1, sweeps = 0;
     const int max_sweeps = a.max_sweeps > 0 ? a.max_sweeps : 30 * nu;
-    while (hi > 0 && ok) {
-        if (fabs(E[hi - 1]) <= eps * (fabs(D[hi - 1]) + fabs(D[hi]))) {
+    // each pass deflates every negligible trailing off-diagonal entry, then makes one sweep:
+    // the columns of a warp then reach their sweeps together (a column that deflated would
+    // otherwise sit out the other lanes' sweep), in the same order of operations per column
+    while (ok) {
+        while (hi > 0 && fabs(E[hi - 1]) <= eps * (fabs(D[hi - 1]) + fabs(D[hi]))) {
             E[hi - 1] = 0.0;
             --hi;
-            continue;
         }
+        if (hi == 0) break;
         int lo = hi - 1;
         while (lo > 0 && fabs(E[lo - 1]) > eps * (fabs(D[lo - 1]) + fabs(D[lo]))) --lo;
         if (lo > 0) E[lo - 1] = 0.0;
