@@ -18,7 +18,7 @@
 //
 // GB300 layout: one CTA of 4 warps per atom J, one warp per orbital column alpha; the CTA
 // builds an ELL view of the cluster sub-matrix (atoms sorted by in-cluster degree and assigned
-// to lanes in snake order, so that lane work is balanced) in shared memory once for the 4
+// to lanes so that their list lengths balance) in shared memory once for the 4
 // columns. Each lane owns whole atoms (4 rows); the sparse products gather the source vector
 // from shared memory and stream the 4x4 FP64 blocks (the 4 warps of a CTA read the same blocks,
 // which L1 serves). The S-inner products of CGS2 and the projection are per-lane partial sums

@@ -3,7 +3,7 @@
 // helpers and the forward Krylov recursion of one column.
 //
 // Layout (one CTA of 4 warps per atom J, one warp per orbital column alpha): the cluster's atoms
-// are sorted by in-cluster degree and assigned to lanes in snake order over slots of 32, so that
+// are sorted by in-cluster degree and dealt to the lanes with the shortest lists, so that
 // lane work is balanced; each lane owns whole atoms (4 rows). A vector of the cluster is held
 // in "position" order: position p = slot * 32 + lane, orbital r at 4 p + r. The bases live in
 // global scratch as [k][position][orbital] (coalesced 32-byte rows per lane). The forms ending in
@@ -280,7 +280,7 @@ struct ClusterView {
     int* cl;              // cluster atoms, ascending
     int* deg;             // in-cluster list length of each cluster atom
     int* pos_of;          // position of each cluster atom
-    int* atom_of_rank;    // cluster atom of each degree rank (empty positions: -1 - position)
+    int* atom_at;         // cluster atom at each position (-1: empty)
     int* eoff;            // first list entry of each position
     int* eself;           // on-site block of each position (-1: none)
     int n_at, NS, kmax, nent;
@@ -295,9 +295,51 @@ __device__ __forceinline__ void carve_view(unsigned char* base, int NA, int deg_
     v.cl = reinterpret_cast<int*>(v.ell + (size_t)NA * deg_max);
     v.deg = v.cl + NA;
     v.pos_of = v.deg + NA;
-    v.atom_of_rank = v.pos_of + NA;
-    v.eoff = v.atom_of_rank + NA;
+    v.atom_at = v.pos_of + NA;
+    v.eoff = v.atom_at + NA;
     v.eself = v.eoff + NA;
+}
+
+// Positions of the cluster atoms (W lanes, NS slots each; every thread of the CTA's T calls).
+// The atoms go in decreasing in-cluster degree (ties by index) one at a time to the lane whose
+// list is shortest so far among the lanes with a free slot (ties to the lowest lane), into its
+// next slot: the lanes' list lengths, which set the trip count of the sparse products, then
+// differ by about one atom's degree at most (a snake order over degree-sorted atoms left the
+// longest list 7% above the mean on 6 A diamond clusters). `atom_at` serves as scratch for the
+// atoms in rank order, then holds the atom at each position (-1: empty).
+template <int W, int T>
+__device__ __forceinline__ void balanced_positions(int n_at, int NS, const int* deg, int* pos_of, int* atom_at) {
+    const int tid = threadIdx.x;
+    for (int q = tid; q < n_at; q += T) {
+        const int dq = deg[q];
+        int rank = 0;
+        for (int b = 0; b < n_at; ++b) {
+            const int db = deg[b];
+            rank += (db > dq) || (db == dq && b < q);
+        }
+        atom_at[rank] = q;
+    }
+    __syncthreads();
+    if (tid < W) {
+        const unsigned m = W == 32 ? 0xffffffffu : 0xffffu;
+        int tot = 0, cnt = 0;
+        for (int r = 0; r < n_at; ++r) {
+            const int q = atom_at[r];
+            int key = cnt < NS ? tot * W + tid : 0x7fffffff;
+#pragma unroll
+            for (int o = W / 2; o > 0; o >>= 1) key = min(key, __shfl_xor_sync(m, key, o));
+            if (key % W == tid) {
+                pos_of[q] = cnt * W + tid;
+                ++cnt;
+                tot += deg[q];
+            }
+        }
+    }
+    __syncthreads();
+    for (int p = tid; p < NS * W; p += T) atom_at[p] = -1;
+    __syncthreads();
+    for (int q = tid; q < n_at; q += T) atom_at[pos_of[q]] = q;
+    __syncthreads();
 }
 
 // Builds the view of atom J's cluster (every thread of the CTA calls it). Returns false, the
@@ -310,7 +352,7 @@ __device__ __forceinline__ bool cluster_view(const KrylovArgs& a, int J, int NA,
     int* cl = v.cl;
     int* deg = v.deg;
     int* pos_of = v.pos_of;
-    int* atom_of_rank = v.atom_of_rank;
+    int* atom_at = v.atom_at;
     int* eoff = v.eoff;
     int* eself = v.eself;
     int n_at, cbase = 0;
@@ -330,31 +372,13 @@ __device__ __forceinline__ bool cluster_view(const KrylovArgs& a, int J, int NA,
     }
     __syncthreads();
     const int NS = (n_at + 31) >> 5;
-    for (int q = tid; q < NS * 32; q += kThreads) {
-        int rank = q;   // ranks >= n_at are empty positions
-        if (q < n_at) {
-            const int dq = deg[q];
-            rank = 0;
-            for (int b = 0; b < n_at; ++b) {
-                const int db = deg[b];
-                rank += (db > dq) || (db == dq && b < q);
-            }
-        }
-        const int s = rank >> 5;
-        int l = rank & 31;
-        if (s & 1) l = 31 - l;
-        if (q < n_at) pos_of[q] = s * 32 + l;
-        atom_of_rank[rank] = q < n_at ? q : -1 - (s * 32 + l);   // empty: encode its position
-    }
-    __syncthreads();
+    balanced_positions<32, kThreads>(n_at, NS, deg, pos_of, atom_at);
     // per-lane lists: the entries of the lane's rows in slot order
     if (tid < 32) {
         int off = 0;
         for (int sl = 0; sl < NS; ++sl) {
             const int pp = sl * 32 + tid;
-            // rank of position pp (inverse of the snake map)
-            const int l = (sl & 1) ? 31 - tid : tid;
-            const int q = atom_of_rank[sl * 32 + l];
+            const int q = atom_at[pp];
             eoff[pp] = off;
             off += q >= 0 ? deg[q] : 0;
         }
@@ -374,9 +398,8 @@ __device__ __forceinline__ bool cluster_view(const KrylovArgs& a, int J, int NA,
     const int kmax = sh_kmax;
     for (int q = tid; q < kmax * 32; q += kThreads) ell[q] = Ent{0, -1};
     __syncthreads();
-    for (int rank = tid; rank < NS * 32; rank += kThreads) {
-        const int q = atom_of_rank[rank];
-        const int p = q >= 0 ? pos_of[q] : -1 - q;
+    for (int p = tid; p < NS * 32; p += kThreads) {
+        const int q = atom_at[p];
         const int sl = p >> 5, l = p & 31;
         int k = eoff[p];
         int es = -1;
@@ -427,8 +450,10 @@ __device__ __forceinline__ unsigned long long column_flops(const KrylovArgs& a, 
 // E = S' - I over k, q <= n (S' packed upper at sp, this step's column already written), the
 // second pass's coefficients SU^T (w - U h) equal -E h in exact arithmetic, since SU^T U = S'.
 // So h becomes h - E h, the coefficients of both passes together, and one sweep of the basis
-// subtracts them. S'_kk - 1 is exact (S'_kk is within rounding of 1). Lane l of the group of
-// W lanes (mask m) forms the values k = l, l + W, ...; every lane must call.
+// subtracts them. S'_kk - 1 is exact (S'_kk is within rounding of 1); the off-diagonal terms
+// are summed first (the diagonal one selected away, no FP64 instruction) and the diagonal term
+// added last. Lane l of the group of W lanes (mask m) forms the values k = l, l + W, ...; every
+// lane must call.
 template <int W>
 __device__ __forceinline__ void second_pass_from_overlap(const double* __restrict__ sp, double* h, int n,
                                                         int lane, unsigned m) {
@@ -442,10 +467,10 @@ __device__ __forceinline__ void second_pass_from_overlap(const double* __restric
             double eh = 0.0;
             for (int q = 0; q <= n; ++q) {
                 const int lo = min(k, q), hi = max(k, q);
-                double e = sp[lo + hi * (hi + 1) / 2];
-                if (q == k) e -= 1.0;
+                const double e = q == k ? 0.0 : sp[lo + hi * (hi + 1) / 2];
                 eh = fma(e, h[q], eh);
             }
+            eh = fma(sp[k + k * (k + 1) / 2] - 1.0, h[k], eh);
             g[r] = h[k] - eh;
         }
     }
@@ -804,7 +829,7 @@ __device__ __forceinline__ bool cluster_view_w(const KrylovArgs& a, int J, int N
     int* cl = v.cl;
     int* deg = v.deg;
     int* pos_of = v.pos_of;
-    int* atom_of_rank = v.atom_of_rank;
+    int* atom_at = v.atom_at;
     int* eoff = v.eoff;
     int* eself = v.eself;
     int n_at, cbase = 0;
@@ -824,32 +849,14 @@ __device__ __forceinline__ bool cluster_view_w(const KrylovArgs& a, int J, int N
     }
     __syncthreads();
     const int NS = (n_at + W - 1) / W;
-    for (int q = tid; q < NS * W; q += T) {
-        int rank = q;   // ranks >= n_at are empty positions
-        if (q < n_at) {
-            const int dq = deg[q];
-            rank = 0;
-            for (int b = 0; b < n_at; ++b) {
-                const int db = deg[b];
-                rank += (db > dq) || (db == dq && b < q);
-            }
-        }
-        const int s = rank / W;
-        int l = rank % W;
-        if (s & 1) l = W - 1 - l;
-        if (q < n_at) pos_of[q] = s * W + l;
-        atom_of_rank[rank] = q < n_at ? q : -1 - (s * W + l);   // empty: encode its position
-    }
-    __syncthreads();
+    balanced_positions<W, T>(n_at, NS, deg, pos_of, atom_at);
     // per-lane lists: the entries of the lane's rows in slot order
     if (tid < W) {
         const unsigned m = W == 32 ? 0xffffffffu : 0xffffu;
         int off = 0;
         for (int sl = 0; sl < NS; ++sl) {
             const int pp = sl * W + tid;
-            // rank of position pp (inverse of the snake map)
-            const int l = (sl & 1) ? W - 1 - tid : tid;
-            const int q = atom_of_rank[sl * W + l];
+            const int q = atom_at[pp];
             eoff[pp] = off;
             off += q >= 0 ? deg[q] : 0;
         }
@@ -869,9 +876,8 @@ __device__ __forceinline__ bool cluster_view_w(const KrylovArgs& a, int J, int N
     const int kmax = sh_kmax;
     for (int q = tid; q < kmax * W; q += T) ell[q] = Ent{0, -1};
     __syncthreads();
-    for (int rank = tid; rank < NS * W; rank += T) {
-        const int q = atom_of_rank[rank];
-        const int p = q >= 0 ? pos_of[q] : -1 - q;
+    for (int p = tid; p < NS * W; p += T) {
+        const int q = atom_at[p];
         const int sl = p / W, l = p % W;
         int k = eoff[p];
         int es = -1;

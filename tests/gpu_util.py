@@ -15,6 +15,17 @@ E_TOL_PER_ATOM = 1e-9    # |delta E| / atom (eV)
 RHOE_TOL = 10.0 * RHO_TOL
 
 
+def mu_tolerance(system, mu, dn=1e-10, h=1e-4):
+    """Bound on the distance between two bisection results whose N(mu) differ by rounding: the
+    crossing of N_e moves by delta N / N'(mu), so a difference of up to `dn` electrons (far above
+    the rounding of N over every pole of these systems, about 1e-11) allows dn / N'(mu), with
+    N' from a central difference of the system's own N; plus twice the bisection's resolution
+    (each result lies within half a 1e-13 bracket of its crossing). In a gap N is nearly flat
+    and the bound widens accordingly; where N is steep it stays near the resolution."""
+    slope = (system.energies(mu + h)["N"] - system.energies(mu - h)["N"]) / (2.0 * h)
+    return 2e-13 + dn / max(slope, 1e-300)
+
+
 def library():
     from paper_1210_1531_gb300 import build
     build.build()

@@ -42,7 +42,7 @@ def test_autotuned_shape_keeps_results(eg, name, r_cluster):
     if _half_classes(shapes) == _half_classes(before):
         assert mu2 == mu and e_band2 == e_band and np.array_equal(gu.to_np(F2), F)
     else:
-        assert abs(mu2 - mu) <= 3e-13 and abs(e_band2 - e_band) <= 1e-12 * abs(e_band)
+        assert abs(mu2 - mu) <= gu.mu_tolerance(s, mu2) and abs(e_band2 - e_band) <= 1e-12 * abs(e_band)
         assert np.abs(gu.to_np(F2) - F).max() <= 1e-10 * np.abs(F).max()
 
 

@@ -62,7 +62,7 @@ def test_diamond4096_all_columns(eg):
     r = _sampled_parity(s, w, np.arange(4 * w.n_atoms))   # replayed
     b = eg.system_for(w, schedule=1)
     mu_b, e_b, _, F_b = b.energy_force()
-    assert abs(r["mu"] - mu_b) <= 3e-13
+    assert abs(r["mu"] - mu_b) <= gu.mu_tolerance(b, mu_b)
     rho_a, _ = s.density_matrix(r["mu"])
     rho_b, _ = b.density_matrix(r["mu"])
     assert np.abs(gu.to_np(rho_a) - gu.to_np(rho_b)).max() <= 1e-12

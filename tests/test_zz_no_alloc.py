@@ -23,6 +23,7 @@ def test_find_mu_static_matches_find_mu_on_two_calls(name):
     s.green_columns()
     mu_ref, n_ref = s.find_mu()
     e_ref = s.energies(mu_ref)["E_band"]
+    mu_tol = gu.mu_tolerance(s, mu_ref)
     sp = s.spectra()
     torch.cuda.synchronize()
     side = torch.cuda.Stream()
@@ -36,7 +37,7 @@ def test_find_mu_static_matches_find_mu_on_two_calls(name):
         # two bisections with mu_tol = 1e-13 end within half a bracket of their own crossing
         # of N_e; the crossings differ by the rounding of two summation orders (the static
         # entry sums every pole, the system keeps the poles near mu once the bracket is narrow)
-        assert abs(mu - mu_ref) <= 3e-13
+        assert abs(mu - mu_ref) <= mu_tol
         assert abs(n - n_ref) <= 1e-8
         assert abs(e - e_ref) / w.n_atoms <= gu.E_TOL_PER_ATOM
         results.append((mu, n, e))
