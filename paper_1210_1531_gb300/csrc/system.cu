@@ -650,6 +650,7 @@ int elses_energies(elses_system s, double mu, double* n_host, double* e_band_hos
     BisectState h{};
     CUDA_TRY(cudaMemcpyAsync(&h, s->bstate.p, sizeof h, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY(cudaGetLastError());   // a failed launch is reported before the timings are read
     s->collect();
     if (n_host) *n_host = h.n_at;
     if (e_band_host) *e_band_host = h.e_band;
@@ -1000,6 +1001,7 @@ int elses_find_mu(elses_system s, double* mu_host, double* n_at_mu_host, void* s
     BisectState h{};
     CUDA_TRY(cudaMemcpyAsync(&h, s->bstate.p, sizeof h, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY(cudaGetLastError());
     s->collect();
     s->stats.bisect_steps = h.iter;
     if (h.status & DEV_NONFINITE) return fail(ELSES_ERR_NONFINITE, "non-finite poles");
@@ -1016,6 +1018,7 @@ int elses_find_mu(elses_system s, double* mu_host, double* n_at_mu_host, void* s
         s->stats.launches++;
         CUDA_TRY(cudaMemcpyAsync(&h, s->bstate.p, sizeof h, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
+        CUDA_TRY(cudaGetLastError());
         s->collect();
         *n_at_mu_host = h.n_at;
     }

@@ -195,7 +195,9 @@ struct elses_system_s {
         for (auto& q : graph_ev) { pool.push_back(q.a); pool.push_back(q.b); }
         graph_ev.clear();
     }
-    void collect() {   // after a synchronisation of the stream
+    // after a synchronisation of the stream and a check of cudaGetLastError (it clears the error
+    // that an unrecorded timing event leaves)
+    void collect() {
         for (auto& q : pending) {
             add_time(q);
             pool.push_back(q.a);
