@@ -144,6 +144,8 @@ __device__ __forceinline__ void axis_range(int c, int reach, int nc, int& first,
 // FILL = false: counts[i] = number of atoms within r of atom i (and max into *max_count).
 // FILL = true : writes the sorted list into idx[ptr[i] ..), using a per-warp shared buffer of
 //               `cap` entries (overflow sets DEV_CAPACITY and skips the row).
+constexpr int kListWarps = 8;   // warps (atoms) per CTA of k_lists
+
 template <bool FILL>
 __global__ void k_lists(const double* __restrict__ pos, int n, CellGrid g,
                         const int* __restrict__ cell_of, const int* __restrict__ cell_start,
@@ -172,7 +174,30 @@ __global__ void k_lists(const double* __restrict__ pos, int n, CellGrid g,
     int first[3], count[3];
     bool absol[3];
     for (int d = 0; d < 3; ++d) axis_range(ci[d], reach[d], g.nc[d], first[d], count[d], absol[d]);
+    // candidates that pass the FP32 prefilter wait in a per-warp buffer and take the exact FP64
+    // test 32 at a time with every lane busy (the FP64 pipe charges a warp instruction whatever
+    // its active lanes, and few candidates of each 32 pass the prefilter)
+    __shared__ int cand_buf[kListWarps][64];
+    int* cb = cand_buf[wib];
+    int nb = 0;
     int found = 0;
+    auto exact_chunk = [&](int cnt) {
+        bool hit = false;
+        int j = -1;
+        if (lane < cnt) {
+            j = cb[lane];
+            const double dx = min_image(__dsub_rn(pos[3 * j], xi), g.L[0]);
+            const double dy = min_image(__dsub_rn(pos[3 * j + 1], yi), g.L[1]);
+            const double dz = min_image(__dsub_rn(pos[3 * j + 2], zi), g.L[2]);
+            hit = dist2_exact(dx, dy, dz) <= r2;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (FILL && hit) {
+            const int slot = found + __popc(m & ((1u << lane) - 1u));
+            if (slot < cap) buf[slot] = j;
+        }
+        found += __popc(m);
+    };
     for (int a = 0; a < count[0]; ++a) {
         int cx = first[0] + a;
         if (!absol[0]) cx = (cx % g.nc[0] + g.nc[0]) % g.nc[0];
@@ -199,34 +224,37 @@ __global__ void k_lists(const double* __restrict__ pos, int n, CellGrid g,
                 const int s0 = cell_start[row + zlo[run]], s1 = cell_start[row + zhi[run]];
                 for (int base = s0; base < s1; base += 32) {
                     const int q = base + lane;
-                    bool hit = false;
+                    bool pass = false;
                     int j = -1;
                     if (q < s1) {
                         j = cell_atoms[q];
                         // FP32 prefilter (error < 1e-3 A^2 for boxes of a few hundred A): only
-                        // candidates near the sphere take the exact FP64 test below
+                        // candidates near the sphere take the exact FP64 test
                         const float fx = (float)pos[3 * j] - fxi, fy = (float)pos[3 * j + 1] - fyi,
                                     fz = (float)pos[3 * j + 2] - fzi;
                         const float gx = fx - fL[0] * rintf(fx * fiL[0]);
                         const float gy = fy - fL[1] * rintf(fy * fiL[1]);
                         const float gz = fz - fL[2] * rintf(fz * fiL[2]);
-                        if (gx * gx + gy * gy + gz * gz <= r2_pre) {
-                            const double dx = min_image(__dsub_rn(pos[3 * j], xi), g.L[0]);
-                            const double dy = min_image(__dsub_rn(pos[3 * j + 1], yi), g.L[1]);
-                            const double dz = min_image(__dsub_rn(pos[3 * j + 2], zi), g.L[2]);
-                            hit = dist2_exact(dx, dy, dz) <= r2;
-                        }
+                        pass = gx * gx + gy * gy + gz * gz <= r2_pre;
                     }
-                    const unsigned m = __ballot_sync(0xffffffffu, hit);
-                    if (FILL && hit) {
-                        const int slot = found + __popc(m & ((1u << lane) - 1u));
-                        if (slot < cap) buf[slot] = j;
+                    const unsigned m = __ballot_sync(0xffffffffu, pass);
+                    if (pass) cb[nb + __popc(m & ((1u << lane) - 1u))] = j;
+                    nb += __popc(m);
+                    __syncwarp();
+                    if (nb >= 32) {          // a full chunk: test it, keep the rest (< 32)
+                        exact_chunk(32);
+                        const int rest = nb - 32;
+                        const int v = lane < rest ? cb[32 + lane] : 0;
+                        __syncwarp();
+                        if (lane < rest) cb[lane] = v;
+                        nb = rest;
+                        __syncwarp();
                     }
-                    found += __popc(m);
                 }
             }
         }
     }
+    if (nb > 0) exact_chunk(nb);
     if (!FILL) {
         if (lane == 0) {
             counts[i] = found;
@@ -270,7 +298,7 @@ void count_lists(const double* pos, int n, const CellGrid& g, const int* cell_of
                  int* max_count, cudaStream_t st) {
     int reach[3];
     for (int d = 0; d < 3; ++d) reach[d] = (int)ceil(r / g.len[d]);
-    const int W = 8;
+    const int W = kListWarps;
     k_lists<false><<<(n + W - 1) / W, 32 * W, 0, st>>>(pos, n, g, cell_of, cell_start, cell_atoms, r,
                                                        reach[0], reach[1], reach[2], counts, max_count,
                                                        nullptr, nullptr, 0, nullptr);
@@ -281,7 +309,7 @@ void fill_lists(const double* pos, int n, const CellGrid& g, const int* cell_of,
                 int cap, int* status, cudaStream_t st) {
     int reach[3];
     for (int d = 0; d < 3; ++d) reach[d] = (int)ceil(r / g.len[d]);
-    const int W = 8;
+    const int W = kListWarps;
     const size_t smem = sizeof(int) * (size_t)cap * W;
     if (smem > 48 * 1024)
         smem_at_least(k_lists<true>, smem);
