@@ -184,18 +184,36 @@ __global__ void __launch_bounds__(kRedThreads) k_count(const ReduceArgs a, int m
     } else {
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         __shared__ int wcount[kRedThreads / 32];
+        // the poles within 50 kT of x need exponentials; they wait in a per-warp buffer and are
+        // evaluated 32 at a time with every lane busy (the FP64 pipe charges a warp instruction
+        // whatever its active lanes), the others add their limits at once
+        __shared__ double qt[kRedThreads / 32][64], qdc[kRedThreads / 32][64], qe[kRedThreads / 32][64],
+            qg[kRedThreads / 32][64], qc[kRedThreads / 32][64];
+        int nq = 0;
+        auto evaluate = [&](int cnt) {
+            if (lane < cnt) {
+                const double t = qt[wid][lane], dc = qdc[wid][lane];
+                const double f2 = 2.0 * fermi(t);
+                v[0] = fma(f2, dc, v[0]);
+                if (mode == 3) {
+                    v[1] = fma(f2 * qg[wid][lane], qc[wid][lane], v[1]);
+                    v[2] = fma(dc, omega_w(qe[wid][lane], x, a.kT), v[2]);
+                }
+            }
+        };
         double below = 0.0;
         int kept = 0;
         for (size_t t0 = b0; t0 < b1; t0 += blockDim.x) {
             const size_t p = t0 + threadIdx.x;
-            bool in_window = false;
-            double Ek = 0.0, dcw = 0.0;
+            bool in_window = false, near = false;
+            double Ek = 0.0, dcw = 0.0, t = 0.0, dc = 0.0, e = 0.0, cc = 0.0;
             if (p < b1) {
                 const int j = (int)(p / a.nu_max), k = (int)(p - (size_t)j * a.nu_max);
                 if (k < __ldg(a.nu_eff + j)) {
-                    const double e = a.eps[p], cc = a.c[p];
-                    const double t = (e - x) * inv_kT;
-                    const double dc = a.d[p] * cc;
+                    e = a.eps[p];
+                    cc = a.c[p];
+                    t = (e - x) * inv_kT;
+                    dc = a.d[p] * cc;
                     if (keep) {
                         if (fabs(t) <= 60.0) {
                             in_window = true;
@@ -205,19 +223,56 @@ __global__ void __launch_bounds__(kRedThreads) k_count(const ReduceArgs a, int m
                             below = fma(2.0, dc, below);
                         }
                     }
-                    double f2 = 0.0, om = 0.0;
-                    if (t < -50.0) {
-                        f2 = 2.0;
-                        if (mode == 3) om = 2.0 * (e - x);
+                    if (t < -50.0) {          // f = 1, w = 2 (e - x) to e^-50 of the weight
+                        v[0] = fma(2.0, dc, v[0]);
+                        if (mode == 3) {
+                            v[1] = fma(2.0 * a.g[p], cc, v[1]);
+                            v[2] = fma(dc, 2.0 * (e - x), v[2]);
+                        }
                     } else if (t <= 50.0) {
-                        f2 = 2.0 * fermi(t);
-                        if (mode == 3) om = omega_w(e, x, a.kT);
+                        near = true;
                     }
-                    v[0] = fma(f2, dc, v[0]);
+                }
+            }
+            {   // buffer this tile's near poles; evaluate a full buffer
+                const unsigned m = __ballot_sync(0xffffffffu, near);
+                if (near) {
+                    const int q = nq + __popc(m & ((1u << lane) - 1u));
+                    qt[wid][q] = t;
+                    qdc[wid][q] = dc;
                     if (mode == 3) {
-                        v[1] = fma(f2 * a.g[p], cc, v[1]);
-                        v[2] = fma(dc, om, v[2]);
+                        qe[wid][q] = e;
+                        qg[wid][q] = a.g[p];
+                        qc[wid][q] = cc;
                     }
+                }
+                nq += __popc(m);
+                __syncwarp();
+                if (nq >= 32) {
+                    evaluate(32);
+                    const int rest = nq - 32;
+                    double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0, r4 = 0.0;
+                    if (lane < rest) {
+                        r0 = qt[wid][32 + lane];
+                        r1 = qdc[wid][32 + lane];
+                        if (mode == 3) {
+                            r2 = qe[wid][32 + lane];
+                            r3 = qg[wid][32 + lane];
+                            r4 = qc[wid][32 + lane];
+                        }
+                    }
+                    __syncwarp();
+                    if (lane < rest) {
+                        qt[wid][lane] = r0;
+                        qdc[wid][lane] = r1;
+                        if (mode == 3) {
+                            qe[wid][lane] = r2;
+                            qg[wid][lane] = r3;
+                            qc[wid][lane] = r4;
+                        }
+                    }
+                    nq = rest;
+                    __syncwarp();
                 }
             }
             if (keep) {   // this tile's kept poles, appended in pole order
@@ -234,6 +289,7 @@ __global__ void __launch_bounds__(kRedThreads) k_count(const ReduceArgs a, int m
                 kept = tot;
             }
         }
+        if (nq > 0) evaluate(nq);
         if (keep) {
             double bl[1] = {below};
             block_reduce_store<1>(bl, a.act_below, 1);
