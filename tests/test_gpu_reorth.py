@@ -161,6 +161,43 @@ def test_exact_forces_4096_sampled_atoms(eg):
     assert np.abs(gu.to_np(F) - Fb).max() <= 1e-10 * np.abs(Fb).max()
 
 
+def test_dimer_breakdown(eg):
+    """A z-dimer with nu = 8: the s and pz columns span 4 dimensions, the px and py columns 2, so
+    every column breaks down, in the half-warp form with the two columns of a warp stopping at
+    different steps; each space is exact on its invariant subspace (rho against the oracle and
+    the exact diagonalisation)."""
+    pos, box = wl.dimer(wl.sk_params().r0)
+    w = wl.Workload("dimer", pos, box, wl.sk_params(), r_cluster=0.0, nu=8)
+    s = eg.system_for(w, reorth=1)
+    mu, e_band, _, _ = s.energy_force()
+    nu = gu.to_np(s.spectra()["nu_eff"])
+    assert list(nu[:4]) == [4, 2, 2, 4] and list(nu[4:]) == [4, 2, 2, 4]
+    res = pipeline.run(w, mu=mu)
+    rho, rhoE = s.density_matrix(mu)
+    assert np.abs(gu.to_np(rho) - res["rho"]).max() < gu.RHO_TOL
+    assert np.abs(gu.to_np(rhoE) - res["rhoE"]).max() < gu.RHO_TOL
+    ref = pipeline.dense_reference(w)
+    rp, ci = (gu.to_np(t) for t in s.pattern())
+    assert np.abs(hamiltonian.bsr_to_dense(rp, ci, gu.to_np(rho)) - ref["rho"]).max() < 1e-8
+
+
+def test_indefinite_overlap_is_not_spd(eg):
+    """The off-site overlap scaled by 3 makes S indefinite; the one-sweep form meets w^T S w < 0
+    and reports ELSES_ERR_NOT_SPD as the two-pass form does."""
+    import torch
+    w = wl.make("diamond_64")
+    s = eg.system_for(w, reorth=1)
+    H, S = s.hs()
+    rp, ci = (gu.to_np(t) for t in s.pattern())
+    onsite = torch.tensor(np.repeat(np.arange(w.n_atoms), np.diff(rp)) == ci, device="cuda")
+    s.set_hs(H, torch.where(onsite[:, None, None], S, 3.0 * S))
+    with pytest.raises(eg.ElsesError) as err:
+        s.green_columns()
+    assert err.value.code == -2
+    s.set_hs(H, S)
+    assert s.green_columns() == 0
+
+
 def test_bad_setting_is_rejected(eg):
     with pytest.raises(eg.ElsesError) as err:
         eg.system_for(wl.make("diamond_64"), reorth=2)
