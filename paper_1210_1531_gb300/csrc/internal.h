@@ -158,6 +158,7 @@ __host__ __device__ size_t eig_fac_doubles(int nm);
 __host__ __device__ size_t eig_rot_cap(int nm);
 // reduce, chase, spectra (eps, c, d, g); V too when form_v
 void projected_eig(const EigArgs& a, cudaStream_t st, bool form_v);
+size_t eig_smem_max(int nm);   // largest dynamic shared memory of the eigensolver kernels
 // V of the columns whose factors (fac, rotations, perm) are those of the last projected_eig
 void eig_vectors(const EigArgs& a, cudaStream_t st);
 // T[batch col][2 nu_max]: t = V w and t_E = V w_E for the density weights at mu, from the factors

@@ -22,6 +22,8 @@
 //                  spectra c, d, g = Q^T z too (instead of k_eig_spectra).
 //   k_eig_weights  one thread per (column, vector): the density needs V only applied to two
 //                  vectors, t = V w = L^-T Q_H (R_1^T .. R_n^T w), taken from the factors.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace elses {
@@ -562,11 +564,19 @@ __global__ void __launch_bounds__(kWtThreads) k_eig_weights(const EigArgs a, dou
     }
 }
 
+// The largest dynamic shared memory any eigensolver kernel asks for at capacity nm (checked
+// against the device before the columns are planned).
+size_t eig_smem_max(int nm);
+
 size_t eig_smem_reduce(int nm) {
     return sizeof(double) * 2 * ((2 * (size_t)nm + 3) * (nm + 1) + 2 * (size_t)nm + 3);
 }
 size_t eig_smem_vectors(int nm) { return sizeof(double) * (3 * (size_t)nm * (nm + 1) + 4 * (size_t)nm); }
 size_t eig_smem_threads(int nm, int arrays) { return sizeof(double) * arrays * (size_t)nm * kChaseThreads; }
+size_t eig_smem_max(int nm) {
+    const size_t spec = sizeof(double) * (size_t)nm * kSpecThreads, wt = sizeof(double) * (size_t)nm * kWtThreads;
+    return std::max({eig_smem_reduce(nm), eig_smem_vectors(nm), eig_smem_threads(nm, 2), spec, wt});
+}
 int eig_thread_grid(int ncols) { return (ncols + kChaseThreads - 1) / kChaseThreads; }
 
 void projected_eig(const EigArgs& a, cudaStream_t st, bool form_v) {

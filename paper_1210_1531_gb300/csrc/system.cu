@@ -90,6 +90,9 @@ int prepare_columns(elses_system s) {
     if ((int)krylov_smem_bytes(s->na_max, kdeg) > smem_optin)
         return fail(ELSES_ERR_CAPACITY, "cluster of %d atoms needs %zu B of shared memory (max %d)",
                     s->max_cl, krylov_smem_bytes(s->na_max, kdeg), smem_optin);
+    if ((long long)eig_smem_max(nm) > smem_optin)
+        return fail(ELSES_ERR_CAPACITY, "Krylov dimension %d needs %zu B of shared memory in the eigensolver (max %d)",
+                    nm, eig_smem_max(nm), smem_optin);
     // batch of atoms for the Krylov -> eigensolver hand-off
     {
         const size_t PK0 = (size_t)nm * (nm + 1) / 2;
