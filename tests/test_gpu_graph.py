@@ -25,8 +25,10 @@ def _same(ra, rb):
 
 
 @pytest.mark.parametrize("kw", [{}, {"two_pass": True}, {"exact_forces": True}, {"schedule": 1},
-                                {"krylov_block": True}, {"batch_atoms": 16}],
-                         ids=["stored", "two_pass", "exact_forces", "batched", "block", "batches"])
+                                {"krylov_block": True}, {"batch_atoms": 16},
+                                {"reorth": 1, "schedule": 1}, {"reorth": 1, "exact_forces": True}],
+                         ids=["stored", "two_pass", "exact_forces", "batched", "block", "batches",
+                              "one_sweep", "one_sweep_exact"])
 def test_replay_equals_eager(eg, kw):
     w = wl.make("diamond_64")
     a = eg.system_for(w, **kw)

@@ -198,6 +198,35 @@ def test_indefinite_overlap_is_not_spd(eg):
     assert s.green_columns() == 0
 
 
+def test_block_spaces_keep_two_passes(eg):
+    """Block-start spaces have their own build with two classical passes: the setting leaves
+    their results unchanged, bit for bit."""
+    w = wl.make("diamond_64")
+    a = eg.system_for(w, krylov_block=True)
+    b = eg.system_for(w, krylov_block=True, reorth=1)
+    ra, rb = a.energy_force(), b.energy_force()
+    assert ra[0] == rb[0] and ra[1] == rb[1] and np.array_equal(gu.to_np(ra[3]), gu.to_np(rb[3]))
+
+
+def test_caller_pattern_dense_blocks(eg):
+    """Caller H and S on a wider pattern (every pair within 3.2 A, seeded couplings beyond the
+    Slater-Koster cutoff): the dense 4 x 4 block products with the one-sweep form, sampled columns
+    of the 4096-atom system against the oracle on the same matrices."""
+    import torch
+    from oracle import structure
+    from tests.test_gpu_user_pattern import R_WIDE, _compare, _oracle_rho, _wide_values
+    w = wl.make("diamond_4096")
+    rp, ci = structure.neighbor_csr(w.pos, w.box, R_WIDE)
+    H, S = _wide_values(w, rp, ci)
+    s = eg.system_for(w, reorth=1)
+    s.set_hs(torch.tensor(H, device="cuda"), torch.tensor(S, device="cuda"),
+             torch.tensor(rp, device="cuda"), torch.tensor(ci, device="cuda"))
+    s.green_columns()
+    mu, _ = s.find_mu()
+    oc = _oracle_rho(w, rp, ci, H, S, wl.sample_columns(4 * w.n_atoms, 24), mu, w.r_cluster)
+    _compare(eg, s, w, rp, ci, oc, mu)
+
+
 def test_bad_setting_is_rejected(eg):
     with pytest.raises(eg.ElsesError) as err:
         eg.system_for(wl.make("diamond_64"), reorth=2)
