@@ -58,3 +58,17 @@ def test_every_column_against_the_oracle(eg, case):
     nu_g = gu.to_np(s.spectra()["nu_eff"])
     assert np.array_equal(nu_g, np.array([c.nu_eff for c in cols]))
     assert np.abs(gu.to_np(F).sum(axis=0)).max() < 1e-9
+
+
+@pytest.mark.parametrize("reorth", [0, 1])
+def test_exact_gradient_against_the_oracle(eg, reorth):
+    """The exact gradient of the truncated method (dOmega/dH, dOmega/dS on the pattern) on a
+    random 64-atom system with nu = 12, every column, against the oracle's autodiff."""
+    from oracle import adjoint
+    w = _system((2, 2, 2), 3.0, 0.25, 14, 0.0, 12, ())
+    s = eg.system_for(w, reorth=reorth)
+    mu, _, _, _ = s.energy_force()
+    dH, dS = (gu.to_np(t) for t in s.omega_gradient(mu))
+    _, _, oH, oS, _ = adjoint.pattern_gradient(w, mu)
+    assert np.abs(dH - oH).max() <= 1e-9 * np.abs(oH).max()
+    assert np.abs(dS - oS).max() <= 1e-9 * np.abs(oS).max()
