@@ -120,3 +120,38 @@ def test_qr_sweep_cap_reports_timeout(eg):
     assert err.value.code == -5
     s.close()
     assert eg.system_for(w).green_columns() == 0
+
+
+def test_cluster_capacity(eg):
+    """max_cluster bounds the cluster lists: a system whose largest cluster has exactly that many
+    atoms runs (results equal the default capacity's bit for bit), one atom fewer is
+    ELSES_ERR_CAPACITY at build time, before any column is solved."""
+    w = wl.make("diamond_512")
+    a = eg.system_for(w)
+    cp, _, mx = a.clusters()
+    largest = int(np.diff(gu.to_np(cp)).max())
+    assert largest == mx
+    ra = a.energy_force()
+    b = eg.system_for(w, max_cluster=largest)
+    rb = b.energy_force()
+    assert ra[0] == rb[0] and ra[1] == rb[1] and np.array_equal(gu.to_np(ra[3]), gu.to_np(rb[3]))
+    with pytest.raises(eg.ElsesError) as err:
+        eg.system_for(w, max_cluster=largest - 1)
+    assert err.value.code == -10
+
+
+@pytest.mark.parametrize("nu", [1, 2, 3])
+def test_smallest_krylov_dimensions(eg, nu):
+    """nu = 1, 2, 3 (no Householder step, no QR sweep or a single 2 x 2 one): every column of the
+    64-atom diamond against the oracle, at the GPU's mu."""
+    import dataclasses
+    w = dataclasses.replace(wl.make("diamond_64"), nu=nu)
+    s = eg.system_for(w)
+    mu, e_band, _, _ = s.energy_force()
+    cols = pipeline.columns(w)
+    assert abs(pipeline.scalars(cols, mu, w.kT, w.n_electrons)["N"] - w.n_electrons) < 1e-8
+    rho, rhoE = s.density_matrix(mu)
+    _, _, rho_o, rhoE_o = pipeline.assemble(w, cols, mu)
+    assert np.abs(gu.to_np(rho) - rho_o).max() <= gu.RHO_TOL
+    assert np.abs(gu.to_np(rhoE) - rhoE_o).max() <= gu.RHOE_TOL
+    assert np.array_equal(gu.to_np(s.spectra()["nu_eff"]), np.full(4 * w.n_atoms, nu))
