@@ -48,7 +48,9 @@ extern "C" {
 #define ELSES_ERR_OOM            -7   /* device allocation failed                        */
 #define ELSES_ERR_NOT_IMPLEMENTED -8
 #define ELSES_ERR_STATE          -9   /* call out of order (e.g. density before columns) */
-#define ELSES_ERR_CAPACITY      -10   /* a neighbour or cluster list exceeded its bound  */
+#define ELSES_ERR_CAPACITY      -10   /* a neighbour or cluster list exceeded its bound,
+                                         or a kernel would need more shared memory than
+                                         the device has (cluster size, Krylov dimension) */
 
 /* Two-centre s/p Slater-Koster model (reading of the paper's TB-form Hamiltonian):
  * integral x in (ss-sigma, sp-sigma, pp-sigma, pp-pi),
