@@ -543,7 +543,8 @@ __device__ __forceinline__ void second_pass_from_overlap(const double* __restric
 // first pass) and beta_n at k = n + 1, which the adjoint needs. A and B are the warp's two
 // shared vectors (u_1, then by turns H u_n -> w and the products H w of the next vector), h its
 // coefficient buffer. The H and S products of each new vector are formed together from w
-// (spmv_hs_w) and scaled by 1 / beta with it. Returns nu_eff (nu_out: the column's nu), or 0
+// (spmv_hs_w); the S product is scaled by 1 / beta with w, the H product is kept unscaled and its
+// scale carried as a scalar (pscale). Returns nu_eff (nu_out: the column's nu), or 0
 // for bad input (flagged).
 template <bool kAdj>
 __device__ __forceinline__ int column_forward(const KrylovArgs& a, const ClusterView& v, int J, int alpha,
@@ -592,6 +593,9 @@ __device__ __forceinline__ int column_forward(const KrylovArgs& a, const Cluster
     // P holds H u_n at the top of step n (then w); the products of the next basis vector go to Q
     double* P = B;
     double* Q = A;
+    // H u_n = pscale P: the H product of each new vector stays unscaled in P, and the values
+    // formed from it (H', the first-pass coefficients) are scaled once as scalars
+    double pscale = 1.0;
     int nu_eff = nu;
     for (int n = 0; n < nu; ++n) {
         double* SUn = SUw + (size_t)n * vs;
@@ -600,13 +604,14 @@ __device__ __forceinline__ int column_forward(const KrylovArgs& a, const Cluster
                 const int p = sl * 32 + lane;
                 double2 x0, x1;
                 ld4(P + 4 * p, x0, x1);
+                x0.x *= pscale; x0.y *= pscale; x1.x *= pscale; x1.y *= pscale;
                 st4(HUw + (size_t)n * vs + 4 * p, x0, x1);
             }
         }
         if (lane == 0) {
             a.urow[(size_t)col * a.nu_max + n] = Uw[(size_t)n * vs + jp];
             a.surow[(size_t)col * a.nu_max + n] = SUn[jp];
-            a.hurow[(size_t)col * a.nu_max + n] = P[jp];
+            a.hurow[(size_t)col * a.nu_max + n] = P[jp] * pscale;
         }
         // pass A: H'[k][n], S'[k][n] and the first CGS coefficients, k <= n, five k at a time
         double hh = 0.0;
@@ -644,11 +649,11 @@ __device__ __forceinline__ int column_forward(const KrylovArgs& a, const Cluster
             const int kk = lane % 5, kind = lane / 5, k = k0 + kk;
             if (lane < 15 && k <= n) {
                 const size_t pk = (size_t)col * PK + k + (size_t)n * (n + 1) / 2;
-                if (kind == 0) a.Hp[pk] = r;
+                if (kind == 0) a.Hp[pk] = r * pscale;
                 else if (kind == 1) a.Sp[pk] = r;
                 else {
-                    h[k] = r;
-                    if constexpr (kAdj) hess[(size_t)n * a.nu_max + k] = r;
+                    h[k] = r;                // the coefficients of the unscaled P
+                    if constexpr (kAdj) hess[(size_t)n * a.nu_max + k] = r * pscale;
                 }
             }
             if (k0 == 0) hh = __shfl_sync(0xffffffffu, r, 15);
@@ -726,23 +731,25 @@ __device__ __forceinline__ int column_forward(const KrylovArgs& a, const Cluster
             break;
         }
         if constexpr (kAdj) {
-            if (lane == 0) hess[(size_t)n * a.nu_max + n + 1] = beta;
+            if (lane == 0) hess[(size_t)n * a.nu_max + n + 1] = beta * pscale;
         }
-        // u_{n+1} = w / beta, S u_{n+1} = S w / beta, H u_{n+1} = H w / beta (by linearity)
+        // u_{n+1} = w / beta, S u_{n+1} = S w / beta; H w stays in Q unscaled, with
+        // H u_{n+1} = (H w) / beta by linearity (the next step's pscale). w here is the true
+        // residual divided by the previous pscale (it was formed from the unscaled P), which
+        // the normalisation cancels: beta, the breakdown and S-norm tests and u_{n+1} all take
+        // the same factor or none.
         const double inv = 1.0 / beta;
         for (int sl = 0; sl < NS; ++sl) {
             const int p = sl * 32 + lane;
-            double2 w0, w1, v0, v1, g0, g1;
+            double2 w0, w1, v0, v1;
             ld4(P + 4 * p, w0, w1);
             ld4(SUn1 + 4 * p, v0, v1);
-            ld4(Q + 4 * p, g0, g1);
             w0.x *= inv; w0.y *= inv; w1.x *= inv; w1.y *= inv;
             v0.x *= inv; v0.y *= inv; v1.x *= inv; v1.y *= inv;
-            g0.x *= inv; g0.y *= inv; g1.x *= inv; g1.y *= inv;
             st4(Uw + (size_t)(n + 1) * vs + 4 * p, w0, w1);
             st4(SUn1 + 4 * p, v0, v1);
-            st4(Q + 4 * p, g0, g1);
         }
+        pscale = inv;
         double* t = P;
         P = Q;
         Q = t;
@@ -963,7 +970,8 @@ __device__ __forceinline__ bool cluster_view_w(const KrylovArgs& a, int J, int N
 // first pass) and beta_n at k = n + 1, which the adjoint needs. A and B are the warp's two
 // shared vectors (u_1, then by turns H u_n -> w and the products H w of the next vector), h its
 // coefficient buffer. The H and S products of each new vector are formed together from w
-// (spmv_hs_w) and scaled by 1 / beta with it. Returns nu_eff (nu_out: the column's nu), or 0
+// (spmv_hs_w); the S product is scaled by 1 / beta with w, the H product is kept unscaled and its
+// scale carried as a scalar (pscale). Returns nu_eff (nu_out: the column's nu), or 0
 // for bad input (flagged).
 template <bool kAdj, int W>
 __device__ __forceinline__ int column_forward_w(const KrylovArgs& a, const ClusterView& v, int J, int alpha,
@@ -1013,6 +1021,9 @@ __device__ __forceinline__ int column_forward_w(const KrylovArgs& a, const Clust
     // P holds H u_n at the top of step n (then w); the products of the next basis vector go to Q
     double* P = B;
     double* Q = A;
+    // H u_n = pscale P: the H product of each new vector stays unscaled in P, and the values
+    // formed from it (H', the first-pass coefficients) are scaled once as scalars
+    double pscale = 1.0;
     int nu_eff = nu;
     for (int n = 0; n < nu; ++n) {
         double* SUn = SUw + (size_t)n * vs;
@@ -1021,13 +1032,14 @@ __device__ __forceinline__ int column_forward_w(const KrylovArgs& a, const Clust
                 const int p = sl * W + lane;
                 double2 x0, x1;
                 ld4(P + 4 * p, x0, x1);
+                x0.x *= pscale; x0.y *= pscale; x1.x *= pscale; x1.y *= pscale;
                 st4(HUw + (size_t)n * vs + 4 * p, x0, x1);
             }
         }
         if (lane == 0) {
             a.urow[(size_t)col * a.nu_max + n] = Uw[(size_t)n * vs + jp];
             a.surow[(size_t)col * a.nu_max + n] = SUn[jp];
-            a.hurow[(size_t)col * a.nu_max + n] = P[jp];
+            a.hurow[(size_t)col * a.nu_max + n] = P[jp] * pscale;
         }
         // pass A: H'[k][n], S'[k][n] and the first CGS coefficients, k <= n, five k at a time
         double hh = 0.0;
@@ -1065,11 +1077,11 @@ __device__ __forceinline__ int column_forward_w(const KrylovArgs& a, const Clust
             const int kk = lane % 5, kind = lane / 5, k = k0 + kk;
             if (lane < 15 && k <= n) {
                 const size_t pk = (size_t)col * PK + k + (size_t)n * (n + 1) / 2;
-                if (kind == 0) a.Hp[pk] = r;
+                if (kind == 0) a.Hp[pk] = r * pscale;
                 else if (kind == 1) a.Sp[pk] = r;
                 else {
-                    h[k] = r;
-                    if constexpr (kAdj) hess[(size_t)n * a.nu_max + k] = r;
+                    h[k] = r;                // the coefficients of the unscaled P
+                    if constexpr (kAdj) hess[(size_t)n * a.nu_max + k] = r * pscale;
                 }
             }
             if (k0 == 0) hh = __shfl_sync(gm, r, ((threadIdx.x & 31) & ~(W - 1)) + 15);
@@ -1147,23 +1159,25 @@ __device__ __forceinline__ int column_forward_w(const KrylovArgs& a, const Clust
             break;
         }
         if constexpr (kAdj) {
-            if (lane == 0) hess[(size_t)n * a.nu_max + n + 1] = beta;
+            if (lane == 0) hess[(size_t)n * a.nu_max + n + 1] = beta * pscale;
         }
-        // u_{n+1} = w / beta, S u_{n+1} = S w / beta, H u_{n+1} = H w / beta (by linearity)
+        // u_{n+1} = w / beta, S u_{n+1} = S w / beta; H w stays in Q unscaled, with
+        // H u_{n+1} = (H w) / beta by linearity (the next step's pscale). w here is the true
+        // residual divided by the previous pscale (it was formed from the unscaled P), which
+        // the normalisation cancels: beta, the breakdown and S-norm tests and u_{n+1} all take
+        // the same factor or none.
         const double inv = 1.0 / beta;
         for (int sl = 0; sl < NS; ++sl) {
             const int p = sl * W + lane;
-            double2 w0, w1, v0, v1, g0, g1;
+            double2 w0, w1, v0, v1;
             ld4(P + 4 * p, w0, w1);
             ld4(SUn1 + 4 * p, v0, v1);
-            ld4(Q + 4 * p, g0, g1);
             w0.x *= inv; w0.y *= inv; w1.x *= inv; w1.y *= inv;
             v0.x *= inv; v0.y *= inv; v1.x *= inv; v1.y *= inv;
-            g0.x *= inv; g0.y *= inv; g1.x *= inv; g1.y *= inv;
             st4(Uw + (size_t)(n + 1) * vs + 4 * p, w0, w1);
             st4(SUn1 + 4 * p, v0, v1);
-            st4(Q + 4 * p, g0, g1);
         }
+        pscale = inv;
         double* t = P;
         P = Q;
         Q = t;
