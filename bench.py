@@ -47,7 +47,7 @@ RHO_GATE = 1e-10                             # |delta rho_ij| against the oracle
 # DRAM bytes (read + write) of the k_krylov launches of one 4096-atom step from one ncu capture,
 # valid for the Krylov source whose sha256 prefix (krylov.cu + krylov.cuh) and Gram-Schmidt
 # setting (reorth) are given; reported per launch, and null once either changes
-KRYLOV_TRAFFIC = {"krylov_sha256_prefix": "426f3b87507b4ae0", "reorth": 1, "bytes_per_step": 114.89e9,
+KRYLOV_TRAFFIC = {"krylov_sha256_prefix": "51a5e4c8a9c32334", "reorth": 1, "bytes_per_step": 115.03e9,
                   "launches_per_step": 2}
 # further systems timed after the main one: (steps, warm-up steps, plain-form steps, plain-form
 # warm-up steps, sampled columns checked against the oracle)
