@@ -274,7 +274,7 @@ class Runner:
                               nu_classes=w.nu_classes, schedule=schedule, timing=True,
                               k3_ctas_per_sm=self.k3_ctas, exact_forces=exact_forces,
                               autotune=autotune and self.k3_ctas == 0, graph=graph,
-                              reorth=self.reorth)
+                              reorth=self.reorth, keep_factors=1)
 
     def step(self, s):
         s.rebuild(self.pos_dev)
@@ -345,6 +345,7 @@ def extra_record(eg, wl, name, k3_ctas, stream, flush, peak_probe, check, reorth
     batched = r.make(1, autotune=True, graph=True)
     tuned = batched.autotune_shapes()
     times, stats, out = r.timed(batched, steps, warm)
+    last = batched.stats()
     ms = sum(times) / len(times)
     mu = out[0]
     cols = np.asarray(wl.sample_columns(M, n_check)) if check else None
@@ -359,6 +360,12 @@ def extra_record(eg, wl, name, k3_ctas, stream, flush, peak_probe, check, reorth
            "plain": {"ms_per_step": plain_ms, "value": M / (plain_ms * 1e-3), "steps": p_steps,
                      "warmup": p_warm},
            "autotuned_shapes": shapes(tuned),
+           "batches": last["batches"],
+           "eigen_factors": ({"kept": "every column's (reflectors, L, rotation pool), V not formed",
+                              "kept_rotations": last["kept_rotations"],
+                              "v_formed_columns": last["v_formed_columns"]}
+                             if last["keep_factors"] else "V formed per batch" if last["batches"] > 1
+                             else "kept in the batch buffers (one batch)"),
            "phases_ms_per_step": {k: stats[k] / steps for k in PHASES},
            "gpu_launches_per_step": stats["launches"] / steps,
            "roofline": roofline(stats, peak_probe),
@@ -408,12 +415,6 @@ def run_ours(args):
     mu, e_band, f_free, _ = out
     peak_probe = eg.probe_fp64()
 
-    # plain schedule, same step, fewer repetitions (reported beside the batched form)
-    plain = r.make(0)
-    pt, _, _ = r.timed(plain, max(3, args.steps // 2), 1)
-    plain_ms = sum(pt) / len(pt)
-    plain.close()
-
     # end to end through the public API from pinned host memory
     pos_host = torch.tensor(w.pos, dtype=torch.float64).pin_memory()
     f_host = torch.empty((w.n_atoms, 3), dtype=torch.float64).pin_memory()
@@ -437,6 +438,14 @@ def run_ours(args):
     n_check = M if world == 1 and args.cpu_sample <= 0 else min(M, args.cpu_sample or 2048)
     cols = np.arange(M) if n_check == M else np.asarray(wl.sample_columns(M, n_check))
     gpu_rho = gpu_rho_columns(batched, mu, cols) if check else None
+    batched_stats = batched.stats()
+    batched.close()                       # one system on the device at a time
+
+    # plain schedule, same step, fewer repetitions (reported beside the batched form)
+    plain = r.make(0)
+    pt, _, _ = r.timed(plain, max(3, args.steps // 2), 1)
+    plain_ms = sum(pt) / len(pt)
+    plain.close()
 
     # the same step with exact forces (the gradient through the truncated Krylov build)
     exact = None
@@ -456,8 +465,6 @@ def run_ours(args):
                  "note": "forces = exact gradient of Omega through the truncated Krylov build "
                          "(finite-difference gated at 1e-5); 2 timed steps after 1 warm-up"}
         ex.close()
-    batched_stats = batched.stats()
-    batched.close()
 
     extra = {}
     if rank == 0 and world == 1 and not args.no_extra:

@@ -121,6 +121,21 @@ typedef struct elses_params {
                                exact gradient (it differentiates the recursion in exact
                                arithmetic, where the second pass vanishes). Block spaces
                                (krylov_block) always use 0.                                    */
+    int    keep_factors;    /* several batches (batch_atoms < N) in the stored workflow: where the
+                               density (or G(z), the spectra on the pattern, the exact gradient)
+                               later needs V of every column, keep each batch's eigen-factors --
+                               the Householder reflectors and L packed (nu_max (nu_max + 1)
+                               doubles per column), the recorded Givens rotations in a pool
+                               shared by all columns (17 bytes each, about nu^2 per column) --
+                               instead of forming V per batch: 0 = never (V per batch), 1 = a
+                               pool of at most 60% of the free device memory at the build (V per
+                               batch when that holds fewer than nu_max^2 / 2 rotations per
+                               column), n >= 2 = a pool of n rotations per column. A column
+                               whose rotations do not fit gets V formed instead. Results equal
+                               those of V formed per batch to rounding, and those of one batch
+                               exactly. A pass over every column starts the pool afresh. The
+                               pool is memory the build takes for the system's lifetime: about
+                               3x that of V at nu = 30 (the 10^6-atom system: 100 GB for 31 GB). */
 } elses_params;
 
 /* Counters and event timings of the calls since the last build (timing = 1 for the times). */
@@ -156,6 +171,10 @@ typedef struct elses_stats {
                                reverse Gram-Schmidt sweep with its H products)
                                + 64 nu (b_off + n_at) (the sampled dH and dS blocks, H and S);
                                plus the krylov_flops formula when the bases are recomputed      */
+    long long kept_rotations;   /* rotations in the pool of kept eigen-factors (keep_factors)     */
+    long long v_formed_columns; /* columns of the last pass whose V was formed as the pool was full */
+    int batches;            /* Krylov -> eigensolver batches of a pass over every column         */
+    int keep_factors;       /* 1 when the eigen-factors of every column are kept across batches  */
 } elses_stats;
 
 typedef struct elses_system_s* elses_system;

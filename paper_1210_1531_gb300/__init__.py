@@ -51,7 +51,7 @@ class Params(ctypes.Structure):
                 ("force_mode", ctypes.c_int), ("krylov_block", ctypes.c_int),
                 ("batch_atoms", ctypes.c_int), ("autotune", ctypes.c_int), ("graph", ctypes.c_int),
                 ("k3_lanes", ctypes.c_int), ("max_qr_sweeps", ctypes.c_int),
-                ("reorth", ctypes.c_int)]
+                ("reorth", ctypes.c_int), ("keep_factors", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -61,7 +61,9 @@ class Stats(ctypes.Structure):
                 ("t_eig_ms", ctypes.c_double), ("t_bisect_ms", ctypes.c_double),
                 ("t_density_ms", ctypes.c_double), ("t_force_ms", ctypes.c_double),
                 ("krylov_flops", ctypes.c_double), ("t_adjoint_ms", ctypes.c_double),
-                ("adjoint_flops", ctypes.c_double)]
+                ("adjoint_flops", ctypes.c_double), ("kept_rotations", ctypes.c_longlong),
+                ("v_formed_columns", ctypes.c_longlong), ("batches", ctypes.c_int),
+                ("keep_factors", ctypes.c_int)]
 
 
 EXPORTS = (
@@ -153,7 +155,7 @@ def make_params(r_cluster, nu, kT, n_electrons, two_pass=False, nu_classes=(), s
                 max_neighbors=0, max_cluster=0, breakdown_tol=0.0, mu_tol=0.0,
                 max_bisect=0, timing=False, k3_ctas_per_sm=0, exact_forces=False,
                 krylov_block=False, batch_atoms=0, autotune=False, graph=False, k3_lanes=0,
-                max_qr_sweeps=0, reorth=0) -> Params:
+                max_qr_sweeps=0, reorth=0, keep_factors=0) -> Params:
     p = Params()
     p.r_cluster, p.kT, p.n_electrons = float(r_cluster), float(kT), float(n_electrons)
     p.breakdown_tol, p.mu_tol = float(breakdown_tol), float(mu_tol)
@@ -173,6 +175,7 @@ def make_params(r_cluster, nu, kT, n_electrons, two_pass=False, nu_classes=(), s
     p.k3_lanes = int(k3_lanes)
     p.max_qr_sweeps = int(max_qr_sweeps)
     p.reorth = int(reorth)
+    p.keep_factors = int(keep_factors)
     return p
 
 
@@ -186,13 +189,17 @@ class System:
     the forces (exact_forces: the gradient of the truncated method), block-start Krylov spaces
     (krylov_block), the batch size (batch_atoms), the QR sweep cap of the projected eigenproblem
     (max_qr_sweeps, 0: 30 nu), the second Gram-Schmidt pass (reorth: 0 a second classical pass,
-    1 its coefficients from the projected overlap S') and per-call event timings (timing).
+    1 its coefficients from the projected overlap S'), the eigen-factors kept across batches
+    (keep_factors: 0 never, 1 a pool sized from the free memory, n >= 2 a pool of n rotations
+    per column) and per-call
+    event timings (timing).
     """
 
     def __init__(self, pos, box, sk, r_cluster, nu, kT, n_electrons, two_pass=False,
                  nu_classes=(), schedule=0, max_neighbors=0, max_cluster=0, timing=False,
                  k3_ctas_per_sm=0, exact_forces=False, krylov_block=False, batch_atoms=0,
-                 autotune=False, graph=False, k3_lanes=0, max_qr_sweeps=0, reorth=0, stream=None):
+                 autotune=False, graph=False, k3_lanes=0, max_qr_sweeps=0, reorth=0, keep_factors=0,
+                 stream=None):
         self._L = load_library()
         self._h = ctypes.c_void_p(None)
         self.n = int(pos.shape[0])
@@ -203,7 +210,7 @@ class System:
                                   k3_ctas_per_sm=k3_ctas_per_sm, exact_forces=exact_forces,
                                   krylov_block=krylov_block, batch_atoms=batch_atoms,
                                   autotune=autotune, graph=graph, k3_lanes=k3_lanes,
-                                  max_qr_sweeps=max_qr_sweeps, reorth=reorth)
+                                  max_qr_sweeps=max_qr_sweeps, reorth=reorth, keep_factors=keep_factors)
         self.box = (ctypes.c_double * 3)(*[float(b) for b in box])
         self.rebuild(pos, stream)
 

@@ -37,17 +37,19 @@ inline void smem_at_least(Kernel kernel, size_t bytes) {
 }
 
 // For kernels that stream per-thread data through L1 (one thread per column reading its own
-// lists): the shared memory of the CTAs a grid of `grid` CTAs puts on an SM, the rest of the
-// unified L1 / shared storage left to L1. By default the driver sizes shared memory for the
-// kernel's maximum occupancy, which leaves L1 too small for these streams.
+// lists): the shared memory of the CTAs a grid of `grid` CTAs puts on an SM, at most
+// `max_ctas` of them where it is set, the rest of the unified L1 / shared storage left to L1.
+// By default the driver sizes shared memory for the kernel's maximum occupancy, which leaves L1
+// too small for these streams; a grid of many waves would do the same without the cap.
 template <typename Kernel>
-inline void carveout_for(Kernel kernel, size_t bytes, int grid) {
+inline void carveout_for(Kernel kernel, size_t bytes, int grid, int max_ctas = 0) {
     int dev = 0, sms = 1, smem_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (smem_sm <= 0 || sms <= 0) return;
-    const size_t ctas = (size_t)(grid + sms - 1) / sms;
+    size_t ctas = (size_t)(grid + sms - 1) / sms;
+    if (max_ctas > 0) ctas = std::min<size_t>(ctas, (size_t)max_ctas);
     const size_t need = ctas * (bytes + 1024);   // + the per-CTA reservation
     const int pct = (int)std::min<size_t>(100, (need * 100 + smem_sm - 1) / (size_t)smem_sm);
     cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);

@@ -17,6 +17,7 @@ namespace elses {
 int enqueue_step(elses_system s, double* forces_dev, cudaStream_t st) {
     TRY(clear_status(s, st));
     const bool stored = !s->p.two_pass;
+    if (stored && s->arch) TRY(reset_archive(s, st));
     for (int b = 0; b < s->n; b += s->batch_atoms) {
         const int e = std::min(s->n, b + s->batch_atoms);
         double *V = nullptr, *UP = nullptr;
@@ -90,6 +91,7 @@ int capture_step(elses_system s, double* forces_dev) {
     int rc = enqueue_step(s, forces_dev, s->gstream);
     s->capturing = false;
     s->graph_v_lazy = s->v_lazy;
+    s->graph_v_arch = s->v_arch;
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(s->gstream, &g);
     s->graph_launches = s->stats.launches - l0;
@@ -131,6 +133,7 @@ int energy_force_graph(elses_system s, double* mu_host, double* e_band_host, dou
     s->atom_done.assign(s->n, 1);
     s->atoms_done = s->n;
     s->v_lazy = s->graph_v_lazy;
+    s->v_arch = s->graph_v_arch;
     s->have_rho = true;
     BisectState h{};
     CUDA_TRY(cudaMemcpyAsync(&h, s->bstate.p, sizeof h, cudaMemcpyDeviceToHost, st));

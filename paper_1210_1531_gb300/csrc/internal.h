@@ -128,6 +128,26 @@ void adjoint_finish(const unsigned long long* acc, size_t n, double s_scale, dou
 void krylov_columns(const KrylovArgs& a, int grid, int ctas_per_sm, cudaStream_t st);
 
 // ---------------------------------------------------------------- a5, a6 (proj_eig.cu)
+// The eigen-factors of every column kept across batches (several batches, stored workflow), so
+// that V need not be formed per batch: per global column j the reflectors with tau_k (packed
+// upper triangle, row k from entry k) then L (packed lower triangle), nu_max (nu_max + 1)
+// doubles; the ascending order of the eigenvalues; and the recorded rotations in a pool shared by
+// all columns, each column's run at off[j]. A column whose rotations do not fit in the pool gets
+// n[j] = -1 and its V formed instead.
+struct FactorArchive {
+    double* fac;                 // [M][nu_max (nu_max + 1)]
+    int* perm;                   // [M][nu_max]
+    int* n;                      // [M]: rotations kept, or -1 (V formed)
+    unsigned long long* off;     // [M]: first rotation in the pool
+    double* rot_c;               // [cap]
+    double* rot_s;
+    unsigned char* rot_k;
+    unsigned long long cap;      // pool capacity (rotations)
+    unsigned long long* cnt;     // device counters: [0] pool use, [1] columns with V formed, [2] this batch's list length
+    int* list;                   // [batch cols]: this batch's columns whose V is formed
+};
+__host__ __device__ size_t eig_arch_fac_doubles(int nm);
+
 struct EigArgs {
     int ncols;              // batch columns
     int col0;               // global index of the first batch column
@@ -152,6 +172,7 @@ struct EigArgs {
     double* V;              // [batch col][nu_max*nu_max] (row n = Krylov index, col k = eigen index)
     int* status;
     int max_sweeps;         // QR sweeps allowed per column (0: 30 nu; DEV_TIMEOUT beyond)
+    FactorArchive ar;       // the kept factors (several batches), else all null
 };
 __host__ __device__ size_t eig_tri_doubles(int nm);
 __host__ __device__ size_t eig_fac_doubles(int nm);
@@ -163,6 +184,13 @@ size_t eig_smem_max(int nm);   // largest dynamic shared memory of the eigensolv
 void eig_vectors(const EigArgs& a, cudaStream_t st);
 // T[batch col][2 nu_max]: t = V w and t_E = V w_E for the density weights at mu, from the factors
 void eig_density_weights(const EigArgs& a, double mu, const double* mu_dev, double kT, double* T, cudaStream_t st);
+// the batch's factors into the archive (a.ar), then V (at a.V) of its columns the pool cannot hold
+void eig_archive(const EigArgs& a, cudaStream_t st);
+// every column from the archive (a.col0 = 0, a.ncols = M, a.V the stored V): V of the columns
+// kept there; T[M][2 nu_max] for the density weights at mu (from V where it was formed instead)
+void eig_vectors_archived(const EigArgs& a, cudaStream_t st);
+void eig_density_weights_archived(const EigArgs& a, double mu, const double* mu_dev, double kT, double* T,
+                                  cudaStream_t st);
 
 // ---------------------------------------------------------------- a7, a9 (reduce.cu)
 struct BisectState {

@@ -22,6 +22,10 @@
 //                  spectra c, d, g = Q^T z too (instead of k_eig_spectra).
 //   k_eig_weights  one thread per (column, vector): the density needs V only applied to two
 //                  vectors, t = V w = L^-T Q_H (R_1^T .. R_n^T w), taken from the factors.
+//   k_eig_archive  several batches: each batch's factors into the archive of every column
+//                  (reflectors and L packed, rotations in a shared pool), so that the density
+//                  reads them after the last batch instead of V formed per batch; columns the
+//                  pool cannot hold get V (k_eig_vectors_listed).
 #include <algorithm>
 
 #include "internal.h"
@@ -32,8 +36,13 @@ __host__ __device__ size_t eig_tri_doubles(int nm) { return 5 * (size_t)nm; }   
 // reflector k in row k (entries i > k, tau_k at k), then L row-major
 __host__ __device__ size_t eig_fac_doubles(int nm) { return 2 * (size_t)nm * nm; }
 __host__ __device__ size_t eig_rot_cap(int nm) { return 2 * (size_t)nm * nm + 64; }  // Givens rotations per column
+__host__ __device__ size_t eig_arch_fac_doubles(int nm) { return (size_t)nm * (nm + 1); }  // both triangles packed
 constexpr int kRotStage = 128;   // rotations staged in shared memory at a time (k_eig_vectors)
 constexpr int kChaseThreads = 64;  // columns per CTA of k_eig_chase
+// CTAs per SM that the shared memory of the rotation-replay kernels (k_eig_spectra,
+// k_eig_weights) is sized for on grids of many waves: each thread streams its own rotation
+// list, and with more CTAs the L1 left over no longer holds the warps' streams
+constexpr int kStreamCtas = 8;
 
 // The lower-triangle pairs (i, m), lo <= m <= i < hi, in row-major order, 32 at a time from
 // `lane`: f(i, m) for each pair the lane owns. Trailing-block updates spread this way keep all
@@ -379,28 +388,65 @@ __global__ void __launch_bounds__(kSpecThreads) k_eig_spectra(const EigArgs a) {
     for (int k = 0; k < nm; ++k) out[k] = k < nu ? Y[perm[k]] : 0.0;
 }
 
+// ----------------------------------------------------------------------------- factor sources
+// Where a column's factors are read. The batch buffers (batch column c): reflector k in row k of
+// an nm x nm matrix (entries i > k, tau_k at k), L row-major after it, the rotations at
+// c * rot_cap. The archive (global column j): the reflectors' upper triangle and L's lower
+// triangle packed row by row, the rotations in the pool from off[j].
+struct FactorSrc {
+    const double* F;          // reflector k, entry i >= k: F[rrow(k) + i]
+    const double* Lf;         // L row i, entry l <= i: Lf[lrow(i) + l]
+    const int* perm;
+    const double* rc;
+    const double* rs;
+    const unsigned char* rk;
+    int nrot;
+    int nm;
+    bool packed;
+    __device__ __forceinline__ long long rrow(int k) const {
+        return packed ? (long long)k * nm - (long long)k * (k - 1) / 2 - k : (long long)k * nm;
+    }
+    __device__ __forceinline__ long long lrow(int i) const {
+        return packed ? (long long)i * (i + 1) / 2 : (long long)i * nm;
+    }
+};
+
+__device__ __forceinline__ FactorSrc batch_factors(const EigArgs& a, int c) {
+    const int nm = a.nu_max;
+    const size_t o = (size_t)c * eig_rot_cap(nm);
+    const double* F = a.fac + (size_t)c * eig_fac_doubles(nm);
+    return {F, F + (size_t)nm * nm, a.perm + (size_t)c * nm, a.rot_c + o, a.rot_s + o, a.rot_k + o,
+            a.rot_n[c], nm, false};
+}
+
+// only for a column the archive holds (n[j] >= 0)
+__device__ __forceinline__ FactorSrc archived_factors(const EigArgs& a, int j) {
+    const int nm = a.nu_max;
+    const unsigned long long o = a.ar.off[j];
+    const double* F = a.ar.fac + (size_t)j * eig_arch_fac_doubles(nm);
+    return {F, F + (size_t)nm * (nm + 1) / 2, a.ar.perm + (size_t)j * nm, a.ar.rot_c + o, a.ar.rot_s + o,
+            a.ar.rot_k + o, a.ar.n[j], nm, true};
+}
+
 // ----------------------------------------------------------------------------- k_eig_vectors
 // spectra: also write c, d, g = Q^T z in pole order (the batches that form V get them here instead
 // of from k_eig_spectra): z = Q_H y is taken with Q_H once it is accumulated, and after the
 // rotations Q^T z = R_n .. R_1 y.
-__global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a, bool spectra) {
+// One column (batch column c, global column j) by one warp, V written at Vo.
+__device__ void vectors_column(const EigArgs& a, const FactorSrc& f, int c, int j, bool spectra, double* Vo) {
     extern __shared__ __align__(16) double sm[];
-    const int lane = threadIdx.x;
-    const int c = blockIdx.x;
-    if (c >= a.ncols) return;
+    const int lane = threadIdx.x & 31;
     const int nm = a.nu_max, ld = nm + 1;
-    const int j = a.col0 + c;
     const int nu = a.nu_eff[j];
     double* R = sm;                 // reflectors (column k below the diagonal), tau_k on the diagonal
     double* L = R + nm * ld;
     double* Q = L + nm * ld;
     double* inv = Q + nm * ld;
     double* zs = inv + nm;          // [3][nm]: z = Q_H y (spectra only)
-    const double* F = a.fac + (size_t)c * eig_fac_doubles(nm);
-    for (int q = lane; q < nu * nu; q += 32) {
+    for (int q = lane; q < nu * nu; q += 32) {   // the triangles in use; zero elsewhere
         const int i = q / nu, k = q % nu;
-        R[k * ld + i] = F[i * nm + k];
-        L[i * ld + k] = F[nm * nm + i * nm + k];
+        R[k * ld + i] = k >= i ? f.F[f.rrow(i) + k] : 0.0;
+        L[i * ld + k] = k <= i ? f.Lf[f.lrow(i) + k] : 0.0;
         Q[i * ld + k] = (i == k) ? 1.0 : 0.0;
     }
     __syncwarp();
@@ -435,10 +481,10 @@ __global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a, bool spectr
     }
     // Q <- Q R^T for every recorded rotation (columns k, k+1; lanes over rows), the rotation list
     // staged through shared memory 128 at a time with coalesced loads
-    const int nrot = a.rot_n[c];
-    const double* rc = a.rot_c + (size_t)c * eig_rot_cap(nm);
-    const double* rs = a.rot_s + (size_t)c * eig_rot_cap(nm);
-    const unsigned char* rk = a.rot_k + (size_t)c * eig_rot_cap(nm);
+    const int nrot = f.nrot;
+    const double* rc = f.rc;
+    const double* rs = f.rs;
+    const unsigned char* rk = f.rk;
     __shared__ double sc[kRotStage], ss[kRotStage];
     __shared__ int sk[kRotStage];
     for (int r0 = 0; r0 < nrot; r0 += kRotStage) {
@@ -461,7 +507,7 @@ __global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a, bool spectr
         __syncwarp();
     }
     if (spectra) {   // c, d, g = Q^T z in ascending order of the poles (lanes over poles)
-        const int* pm = a.perm + (size_t)c * nm;
+        const int* pm = f.perm;
         for (int k = lane; k < nm; k += 32) {
             double sc = 0.0, sd = 0.0, sg = 0.0;
             if (k < nu) {
@@ -486,11 +532,74 @@ __global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a, bool spectr
             Q[i * ld + m] = s * inv[i];
         }
     __syncwarp();
-    const int* perm = a.perm + (size_t)c * nm;
-    double* Vo = a.V + (size_t)c * nm * nm;
+    const int* perm = f.perm;
     for (int q = lane; q < nu * nu; q += 32) {
         const int n = q / nu, k = q % nu;
         Vo[(size_t)n * nm + k] = Q[n * ld + perm[k]];
+    }
+}
+
+__global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a, bool spectra) {
+    const int c = blockIdx.x;
+    if (c >= a.ncols) return;
+    vectors_column(a, batch_factors(a, c), c, a.col0 + c, spectra, a.V + (size_t)c * a.nu_max * a.nu_max);
+}
+
+// the columns of the batch that k_eig_archive listed (the pool could not hold them)
+__global__ void __launch_bounds__(32) k_eig_vectors_listed(const EigArgs a) {
+    const unsigned long long cnt = a.ar.cnt[2];
+    for (unsigned long long q = blockIdx.x; q < cnt; q += gridDim.x) {
+        const int c = a.ar.list[q];
+        vectors_column(a, batch_factors(a, c), c, a.col0 + c, false, a.V + (size_t)c * a.nu_max * a.nu_max);
+        __syncwarp();
+    }
+}
+
+// every column the archive holds (a.col0 = 0: batch column = global column)
+__global__ void __launch_bounds__(32) k_eig_vectors_archived(const EigArgs a) {
+    const int j = blockIdx.x;
+    if (j >= a.ncols || a.ar.n[j] < 0) return;
+    vectors_column(a, archived_factors(a, j), j, j, false, a.V + (size_t)j * a.nu_max * a.nu_max);
+}
+
+// ----------------------------------------------------------------------------- k_eig_archive
+// One warp per batch column: a run of the pool taken with one atomic (runs land in any order;
+// each column reads only its own), the rotations, the two triangles in use and the eigenvalue
+// order copied. A column past the pool's end is listed instead, and gets n[j] = -1.
+__global__ void __launch_bounds__(128) k_eig_archive(const EigArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (c >= a.ncols) return;
+    const int nm = a.nu_max, j = a.col0 + c, nu = a.nu_eff[j];
+    const FactorSrc f = batch_factors(a, c);
+    const unsigned long long n = (unsigned long long)f.nrot;
+    unsigned long long off = 0;
+    if (lane == 0) off = atomicAdd(a.ar.cnt, n);
+    off = __shfl_sync(0xffffffffu, off, 0);
+    if (off + n > a.ar.cap) {
+        if (lane == 0) {
+            a.ar.n[j] = -1;
+            atomicAdd(a.ar.cnt + 1, 1ull);
+            a.ar.list[atomicAdd(a.ar.cnt + 2, 1ull)] = c;
+        }
+        return;
+    }
+    for (unsigned long long r = lane; r < n; r += 32) {
+        a.ar.rot_c[off + r] = f.rc[r];
+        a.ar.rot_s[off + r] = f.rs[r];
+        a.ar.rot_k[off + r] = f.rk[r];
+    }
+    double* F = a.ar.fac + (size_t)j * eig_arch_fac_doubles(nm);
+    double* Lp = F + (size_t)nm * (nm + 1) / 2;
+    for (int k = 0; k < nu; ++k) {   // rows as archived_factors reads them
+        const long long ru = (long long)k * nm - (long long)k * (k - 1) / 2 - k, rl = (long long)k * (k + 1) / 2;
+        for (int i = k + lane; i < nu; i += 32) F[ru + i] = f.F[f.rrow(k) + i];
+        for (int l = lane; l <= k; l += 32) Lp[rl + l] = f.Lf[f.lrow(k) + l];
+    }
+    for (int k = lane; k < nu; k += 32) a.ar.perm[(size_t)j * nm + k] = f.perm[k];
+    if (lane == 0) {
+        a.ar.n[j] = (int)n;
+        a.ar.off[j] = off;
     }
 }
 
@@ -503,8 +612,10 @@ __global__ void __launch_bounds__(32) k_eig_vectors(const EigArgs a, bool spectr
 //   the back substitution L^T t = x (t_i = x_i / L_ii, then x_l -= L_il t_i for l < i).
 // One thread per (column, vector): a CTA takes 32 columns, warp 0 the vector w, warp 1 w e. No
 // reductions across lanes, so every FP64 instruction carries 32 columns.
-// Out: T[batch col][2 nu_max] = (t, t_E), zero past nu.
+// Out: T[batch col][2 nu_max] = (t, t_E), zero past nu. kArch: every column from the archive
+// (a.col0 = 0), and t = V w from the stored V (a.V) for a column whose V was formed instead.
 constexpr int kWtThreads = 64;
+template <bool kArch>
 __global__ void __launch_bounds__(kWtThreads) k_eig_weights(const EigArgs a, double mu_in, const double* mu_dev,
                                                              double kT, double* T) {
     const double mu = mu_dev ? *mu_dev : mu_in;
@@ -513,27 +624,44 @@ __global__ void __launch_bounds__(kWtThreads) k_eig_weights(const EigArgs a, dou
     const int c0 = blockIdx.x * 32, c = c0 + lane;
     const int nm = a.nu_max;
     const Strided<kWtThreads> X{csm + threadIdx.x};
-    if (c < a.ncols) {
+    if (c < a.ncols && kArch && a.ar.n[a.col0 + c] < 0) {
+        // w in pole order against V's columns; the thread's own slots of T hold t meanwhile
         const int j = a.col0 + c;
         const int nu = a.nu_eff[j];
+        const double* Vj = a.V + (size_t)j * nm * nm;
+        double* Tt = T + (size_t)c * 2 * nm + (size_t)v * nm;
         for (int k = 0; k < nm; ++k) X[k] = 0.0;
-        const int* perm = a.perm + (size_t)c * nm;
+        for (int k = 0; k < nu; ++k) {
+            const double e = a.eps[(size_t)j * nm + k];
+            const double f2 = 2.0 * fermi((e - mu) / kT) * a.c[(size_t)j * nm + k];
+            X[k] = v ? f2 * e : f2;
+        }
+        for (int n = 0; n < nu; ++n) {
+            double t = 0.0;
+            for (int k = 0; k < nu; ++k) t = fma(Vj[(size_t)n * nm + k], X[k], t);
+            Tt[n] = t;
+        }
+        for (int n = 0; n < nu; ++n) X[n] = Tt[n];
+    } else if (c < a.ncols) {
+        const int j = a.col0 + c;
+        const int nu = a.nu_eff[j];
+        const FactorSrc fs = kArch ? archived_factors(a, j) : batch_factors(a, c);
+        for (int k = 0; k < nm; ++k) X[k] = 0.0;
+        const int* perm = fs.perm;
         for (int k = 0; k < nu; ++k) {
             const double e = a.eps[(size_t)j * nm + k];
             const double f2 = 2.0 * fermi((e - mu) / kT) * a.c[(size_t)j * nm + k];
             X[perm[k]] = v ? f2 * e : f2;
         }
-        const RotList R(a, c);
-        for (int r = R.n - 1; r >= 0; --r) {
-            const double cr = __ldg(R.c + r), sr = __ldg(R.s + r);
-            const int k = __ldg(R.k + r);
+        for (int r = fs.nrot - 1; r >= 0; --r) {
+            const double cr = __ldg(fs.rc + r), sr = __ldg(fs.rs + r);
+            const int k = __ldg(fs.rk + r);
             const double p = X[k], w = X[k + 1];
             X[k] = fma(cr, p, -sr * w);
             X[k + 1] = fma(cr, w, sr * p);
         }
-        const double* F = a.fac + (size_t)c * eig_fac_doubles(nm);
         for (int k = nu - 3; k >= 0; --k) {
-            const double* vk = F + (size_t)k * nm;
+            const double* vk = fs.F + fs.rrow(k);
             const double tau = vk[k];
             if (tau == 0.0) continue;
             double s0 = 0.0, s1 = 0.0;           // two partial sums: half the dependent chain
@@ -546,9 +674,8 @@ __global__ void __launch_bounds__(kWtThreads) k_eig_weights(const EigArgs a, dou
             const double sc = tau * (s0 + s1);
             for (int m = k + 1; m < nu; ++m) X[m] = fma(-sc, vk[m], X[m]);
         }
-        const double* L = F + (size_t)nm * nm;
         for (int i = nu - 1; i >= 0; --i) {
-            const double* row = L + (size_t)i * nm;
+            const double* row = fs.Lf + fs.lrow(i);
             const double ti = X[i] / row[i];
             X[i] = ti;
             for (int l = 0; l < i; ++l) X[l] = fma(-row[l], ti, X[l]);
@@ -595,7 +722,7 @@ void projected_eig(const EigArgs& a, cudaStream_t st, bool form_v) {
     }
     const size_t s3 = sizeof(double) * (size_t)a.nu_max * kSpecThreads;
     smem_at_least(k_eig_spectra, s3);
-    carveout_for(k_eig_spectra, s3, (a.ncols + 31) / 32);
+    carveout_for(k_eig_spectra, s3, (a.ncols + 31) / 32, kStreamCtas);
     k_eig_spectra<<<(a.ncols + 31) / 32, kSpecThreads, s3, st>>>(a);
 }
 
@@ -607,9 +734,31 @@ void eig_vectors(const EigArgs& a, cudaStream_t st) {   // the spectra in use ar
 
 void eig_density_weights(const EigArgs& a, double mu, const double* mu_dev, double kT, double* T, cudaStream_t st) {
     const size_t s = sizeof(double) * (size_t)a.nu_max * kWtThreads;
-    smem_at_least(k_eig_weights, s);
-    carveout_for(k_eig_weights, s, (a.ncols + 31) / 32);
-    k_eig_weights<<<(a.ncols + 31) / 32, kWtThreads, s, st>>>(a, mu, mu_dev, kT, T);
+    smem_at_least(k_eig_weights<false>, s);
+    carveout_for(k_eig_weights<false>, s, (a.ncols + 31) / 32, kStreamCtas);
+    k_eig_weights<false><<<(a.ncols + 31) / 32, kWtThreads, s, st>>>(a, mu, mu_dev, kT, T);
+}
+
+void eig_archive(const EigArgs& a, cudaStream_t st) {
+    cudaMemsetAsync(a.ar.cnt + 2, 0, sizeof(unsigned long long), st);
+    k_eig_archive<<<(a.ncols + 3) / 4, 128, 0, st>>>(a);
+    const size_t sv = eig_smem_vectors(a.nu_max);
+    smem_at_least(k_eig_vectors_listed, sv);
+    k_eig_vectors_listed<<<std::max(1, std::min(a.ncols, 2048)), 32, sv, st>>>(a);
+}
+
+void eig_vectors_archived(const EigArgs& a, cudaStream_t st) {
+    const size_t sv = eig_smem_vectors(a.nu_max);
+    smem_at_least(k_eig_vectors_archived, sv);
+    k_eig_vectors_archived<<<a.ncols, 32, sv, st>>>(a);
+}
+
+void eig_density_weights_archived(const EigArgs& a, double mu, const double* mu_dev, double kT, double* T,
+                                  cudaStream_t st) {
+    const size_t s = sizeof(double) * (size_t)a.nu_max * kWtThreads;
+    smem_at_least(k_eig_weights<true>, s);
+    carveout_for(k_eig_weights<true>, s, (a.ncols + 31) / 32, kStreamCtas);
+    k_eig_weights<true><<<(a.ncols + 31) / 32, kWtThreads, s, st>>>(a, mu, mu_dev, kT, T);
 }
 
 }  // namespace elses

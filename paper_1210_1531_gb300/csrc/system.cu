@@ -218,6 +218,65 @@ int prepare_columns(elses_system s) {
             s->use_store = true;
         }
     }
+    // several batches in the stored workflow, keep_factors set: the eigen-factors of every column
+    // are kept (a pool of rotations of at most 60% of the free memory, or keep_factors per
+    // column) so that V need not be formed per batch; too small a pool does not pay, and V is
+    // formed per batch then
+    s->arch = false;
+    s->arch_cap = 0;
+    if (!s->p.two_pass && s->batch_atoms < s->n && s->p.keep_factors > 0) {
+        const size_t fixed = M * (sizeof(double) * (eig_arch_fac_doubles(nm) + 2 * (size_t)nm) +
+                                  sizeof(int) * ((size_t)nm + 1) + sizeof(unsigned long long)) + bc * sizeof(int);
+        const size_t per_rot = 2 * sizeof(double) + 1;
+        size_t cap = 0;
+        if (s->p.keep_factors > 1) {
+            cap = M * (size_t)s->p.keep_factors;
+        } else {
+            // the archive a previous build planned counts as free (a rebuild keeps its plan)
+            size_t free_b = 0, total_b = 0;
+            cudaMemGetInfo(&free_b, &total_b);
+            free_b += sizeof(double) * (s->afac.cap + s->arot_c.cap + s->arot_s.cap + s->ewt_all.cap) +
+                      s->arot_k.cap + sizeof(int) * (s->aperm.cap + s->an.cap + s->alist.cap) +
+                      sizeof(unsigned long long) * (s->aoff.cap + s->acnt.cap);
+            const size_t avail = free_b / 10 * 6;
+            cap = avail > fixed ? (avail - fixed) / per_rot : 0;
+            cap = std::min(cap, M * eig_rot_cap(nm));
+            if (cap < M * (size_t)nm * nm / 2) cap = 0;
+        }
+        if (cap > 0) {
+            const unsigned long long epoch = g_alloc_epoch;
+            TRY(s->afac.ensure(M * eig_arch_fac_doubles(nm)));
+            TRY(s->aperm.ensure(M * nm));
+            TRY(s->an.ensure(M));
+            TRY(s->aoff.ensure(M));
+            TRY(s->arot_c.ensure(cap));
+            TRY(s->arot_s.ensure(cap));
+            TRY(s->arot_k.ensure(cap));
+            TRY(s->acnt.ensure(3));
+            TRY(s->alist.ensure(bc));
+            TRY(s->ewt_all.ensure(M * 2 * nm));
+            if (epoch != g_alloc_epoch || !s->arch_init) {   // new buffers: no column kept yet
+                CUDA_TRY(cudaMemset(s->acnt.p, 0, 3 * sizeof(unsigned long long)));
+                CUDA_TRY(cudaMemset(s->an.p, 0xff, s->an.cap * sizeof(int)));
+                s->arch_init = true;
+            }
+            s->arch = true;
+            s->arch_cap = cap;
+        }
+    }
+    if (!s->arch) {
+        s->arch_init = false;
+        s->afac.release();
+        s->aperm.release();
+        s->an.release();
+        s->aoff.release();
+        s->arot_c.release();
+        s->arot_s.release();
+        s->arot_k.release();
+        s->acnt.release();
+        s->alist.release();
+        s->ewt_all.release();
+    }
     TRY(s->gblock.ensure((size_t)s->nnzb * 3));
     TRY(s->partials.ensure(4 * (size_t)reduce_grid()));
     TRY(s->act.ensure(M * nm));
@@ -231,6 +290,17 @@ int prepare_columns(elses_system s) {
     s->have_mu = false;
     s->have_rho = false;
     s->v_lazy = false;
+    s->v_arch = false;
+    return 0;
+}
+
+// A pass over every column in the archive's form: the pool starts empty, and until a batch is
+// done its columns count as not computed (a pass that stops early leaves them so).
+int reset_archive(elses_system s, cudaStream_t st) {
+    CUDA_TRY(cudaMemsetAsync(s->acnt.p, 0, 2 * sizeof(unsigned long long), st));
+    s->atom_done.assign(s->n, 0);
+    s->atoms_done = 0;
+    s->v_arch = false;
     return 0;
 }
 
@@ -317,32 +387,60 @@ EigArgs eig_args(elses_system s, int b, int e, double* V) {
     ea.V = V;
     ea.status = s->counters.p + 2;
     ea.max_sweeps = s->p.max_qr_sweeps;   // 0: 30 nu of the column
+    if (s->arch) {
+        ea.ar.fac = s->afac.p;
+        ea.ar.perm = s->aperm.p;
+        ea.ar.n = s->an.p;
+        ea.ar.off = s->aoff.p;
+        ea.ar.rot_c = s->arot_c.p;
+        ea.ar.rot_s = s->arot_s.p;
+        ea.ar.rot_k = s->arot_k.p;
+        ea.ar.cap = s->arch_cap;
+        ea.ar.cnt = s->acnt.p;
+        ea.ar.list = s->alist.p;
+    }
     return ea;
 }
 
 // The stored V of every column, from the kept factors, where the energy pass left it unformed
 // (G(z), the spectra on the pattern and the adjoint need V itself).
 int ensure_V(elses_system s, cudaStream_t st) {
-    if (!s->v_lazy) return 0;
-    s->tic(T_EIG, st);
-    eig_vectors(eig_args(s, 0, s->n, s->V.p), st);
-    s->toc(st);
-    s->stats.launches++;
-    s->v_lazy = false;
+    if (s->v_lazy) {
+        s->tic(T_EIG, st);
+        eig_vectors(eig_args(s, 0, s->n, s->V.p), st);
+        s->toc(st);
+        s->stats.launches++;
+        s->v_lazy = false;
+    }
+    if (s->v_arch) {
+        s->tic(T_EIG, st);
+        eig_vectors_archived(eig_args(s, 0, s->n, s->V.p), st);
+        s->toc(st);
+        s->stats.launches++;
+        s->v_arch = false;
+    }
     return 0;
 }
 
 // Krylov build + projected eigenproblem for atoms [b, e). Writes V and UP either to the stored
 // arrays or to the batch buffers (two-pass), returning the pointers used. form_v false leaves V
-// unformed; in the stored workflow that is kept only for a batch of every atom (its factors then
-// stay in the batch buffers until ensure_V or the next batch).
+// unformed; in the stored workflow that holds for a batch of every atom (its factors then stay in
+// the batch buffers until ensure_V or the next batch) and, where the archive is planned, for each
+// of several batches (its factors go to the archive); other batches form V.
 int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_col0,
               double** UP_out, int* up_block0, cudaStream_t st, bool need_rows, bool form_v) {
     const int nm = s->nu_max;
-    if (stored && !form_v && (b != 0 || e != s->n)) form_v = true;
-    // the batch buffers are about to be overwritten: V of the other columns first, unless every
-    // column is recomputed now
-    if (stored && (b != 0 || e != s->n)) TRY(ensure_V(s, st));
+    std::vector<const elses_system_s::K3Launch*> ls;   // the batch's Krylov launches
+    for (const auto& L : s->k3_launches)
+        if (L.batch_begin == b) ls.push_back(&L);
+    if (ls.empty() || e > ls[0]->batch_end)
+        return fail(ELSES_ERR_STATE, "atoms [%d, %d) are not the start of a planned batch", b, e);
+    const bool multi = b != 0 || e != s->n;
+    const bool keep = stored && !form_v && multi && s->arch;
+    if (stored && !form_v && multi && !keep) form_v = true;
+    // the batch buffers are about to be overwritten: V of the columns whose factors are there
+    // first (the archive's stay where they are)
+    if (stored && multi && s->v_lazy) TRY(ensure_V(s, st));
     if (stored) s->v_lazy = false;
     KrylovArgs ka = krylov_args(s, b, e);
     if (stored) {
@@ -354,9 +452,6 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
     }
     if (!need_rows) ka.UP = nullptr;
     s->tic(T_KRYLOV, st);
-    std::vector<const elses_system_s::K3Launch*> ls;
-    for (const auto& L : s->k3_launches)
-        if (L.batch_begin == b) ls.push_back(&L);
     // batched form: the class with the most atoms runs on the caller's stream and the others
     // (few atoms each, partial waves) beside it, one after another, on a second stream
     const bool conc = s->p.schedule == 1 && ls.size() >= 2;
@@ -390,9 +485,17 @@ int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_
     EigArgs ea = eig_args(s, b, e, stored ? s->V.p + (size_t)4 * b * nm * nm : s->Vb.p);
     s->tic(T_EIG, st);
     projected_eig(ea, st, form_v);
+    if (keep) {
+        eig_archive(ea, st);
+        s->stats.launches += 2;
+        s->v_arch = true;
+    } else if (stored && s->v_arch) {
+        // V formed for these columns: the archive's entries give way
+        CUDA_TRY(cudaMemsetAsync(s->an.p + 4 * (size_t)b, 0xff, sizeof(int) * 4 * (size_t)(e - b), st));
+    }
     s->toc(st);
     s->stats.launches += 3;
-    if (stored && !form_v) s->v_lazy = true;
+    if (stored && !form_v && !keep) s->v_lazy = true;
     s->stats.columns += 4LL * (e - b);
     *V_out = ea.V;
     *v_col0 = 4 * b;
@@ -565,12 +668,34 @@ static void density_batch(elses_system s, double mu, double* rho, double* rhoE, 
     s->stats.launches++;
 }
 
+// rho columns of every atom at mu from the archive: t = V w of every column in one launch (from
+// V for the columns the pool could not hold), then the density.
+static void density_archived(elses_system s, double mu, double* rho, double* rhoE, cudaStream_t st,
+                             const double* mu_dev) {
+    DensityArgs d = density_args(s, mu, rho, rhoE);
+    d.mu_dev = mu_dev;
+    d.atom_begin = 0;
+    d.atom_end = s->n;
+    d.V = s->V.p;
+    d.v_col0 = 0;
+    d.UP = s->UP.p;
+    d.up_block0 = 0;
+    s->tic(T_DENSITY, st);
+    eig_density_weights_archived(eig_args(s, 0, s->n, s->V.p), mu, mu_dev, s->p.kT, s->ewt_all.p, st);
+    d.T = s->ewt_all.p;
+    density_columns(d, st);
+    s->toc(st);
+    s->stats.launches += 2;
+}
+
 // mu_dev: when set, mu is read from device memory (the captured step of the graph form).
 int density_impl(elses_system s, double mu, double* rho, double* rhoE, cudaStream_t st,
                  const double* mu_dev) {
     if (s->atoms_done != s->n) return fail(ELSES_ERR_STATE, "density_matrix needs every column");
     if (!mu_dev) TRY(clear_status(s, st));
-    if (!s->p.two_pass) {
+    if (!s->p.two_pass && s->v_arch) {
+        density_archived(s, mu, rho, rhoE, st, mu_dev);
+    } else if (!s->p.two_pass) {
         density_batch(s, mu, rho, rhoE, 0, s->n, s->V.p, 0, s->UP.p, 0, s->v_lazy, st, mu_dev);
     } else {
         // second calculation of G (Eq. 3): recompute every batch, then its rho columns
@@ -703,6 +828,7 @@ int elses_build_clusters(elses_system* sys, int n_atoms, const double* pos_dev,
     if (p.k3_lanes != 0 && p.k3_lanes != 32) return fail(ELSES_ERR_ARG, "k3_lanes must be 0 or 32");
     if (p.max_qr_sweeps < 0) return fail(ELSES_ERR_ARG, "max_qr_sweeps must be >= 0");
     if (p.reorth != 0 && p.reorth != 1) return fail(ELSES_ERR_ARG, "reorth must be 0 or 1");
+    if (p.keep_factors < 0) return fail(ELSES_ERR_ARG, "keep_factors must be 0 or positive");
     if (p.krylov_block) {
         if (p.nu < 4) return fail(ELSES_ERR_ARG, "a block space needs nu >= 4");
         for (int c = 0; c < p.n_classes; ++c)
@@ -936,6 +1062,7 @@ int elses_set_hs(elses_system s, int nnzb, const int* row_ptr_dev, const int* co
     CUDA_TRY(cudaMemcpyAsync(s->S.p, S_dev, sizeof(double) * 16 * s->nnzb, cudaMemcpyDeviceToDevice, st));
     s->have_rho = false;
     s->v_lazy = false;   // every column is recomputed before V is used again
+    s->v_arch = false;
     s->atom_done.assign(s->n, 0);
     s->atoms_done = 0;
     s->have_mu = false;
@@ -957,7 +1084,10 @@ int elses_green_columns(elses_system s, int col_begin, int col_end, int n_z, con
     }
     const int a0 = col_begin / 4, a1 = col_end / 4;
     const bool stored = !s->p.two_pass;
-    for (int b = a0; b < a1; b += s->batch_atoms) {
+    if (stored && s->arch && n_z == 0 && a0 == 0 && a1 == s->n) TRY(reset_archive(s, st));
+    // the batches of the launch plan that meet [a0, a1), each from its first atom (the atoms of
+    // it before a0 are recomputed as well: the same columns again) to the range's end in it
+    for (int b = a0 / s->batch_atoms * s->batch_atoms; b < a1; b += s->batch_atoms) {
         const int e = std::min(a1, b + s->batch_atoms);
         double* V;
         double* UP;
@@ -967,7 +1097,7 @@ int elses_green_columns(elses_system s, int col_begin, int col_end, int n_z, con
         TRY(run_batch(s, b, e, stored, &V, &v0, &UP, &u0, st, stored || n_z > 0, n_z > 0));
         if (n_z > 0) {
             DensityArgs d = density_args(s, 0.0, nullptr, nullptr);
-            d.atom_begin = b;
+            d.atom_begin = std::max(b, a0);
             d.atom_end = e;
             d.V = V;
             d.v_col0 = v0;
@@ -1219,6 +1349,16 @@ int elses_get_stats(elses_system s, elses_stats* out) {
         out->krylov_flops = (double)f[0];
         out->adjoint_flops = (double)f[1];
     }
+    out->batches = s->batch_atoms > 0 ? (s->n + s->batch_atoms - 1) / s->batch_atoms : 0;
+    out->kept_rotations = 0;
+    out->v_formed_columns = 0;
+    if (s->arch) {
+        unsigned long long k[2] = {0, 0};
+        CUDA_TRY(cudaMemcpy(k, s->acnt.p, sizeof k, cudaMemcpyDeviceToHost));
+        out->kept_rotations = (long long)std::min<unsigned long long>(k[0], s->arch_cap);
+        out->v_formed_columns = (long long)k[1];
+    }
+    out->keep_factors = s->arch ? 1 : 0;
     return ELSES_OK;
 }
 

@@ -63,8 +63,11 @@ struct DevBuf {
         ++g_alloc_epoch;
         return 0;
     }
-    void release() {
-        if (p) cudaFree(p);
+    void release() {   // a captured graph that used the buffer is then out of date
+        if (p) {
+            cudaFree(p);
+            ++g_alloc_epoch;
+        }
         p = nullptr;
         cap = 0;
     }
@@ -122,6 +125,15 @@ struct elses_system_s {
     bool use_store = false;
     // the eigen-factors of every column are in the batch buffers and the stored V is not formed
     bool v_lazy = false;
+    // several batches: their eigen-factors kept in an archive of every column (EigArgs::ar) in
+    // place of V formed per batch; arch: the archive is planned, v_arch: the stored V of the
+    // archived columns is not formed (columns the pool could not hold have V)
+    DevBuf<double> afac, arot_c, arot_s, ewt_all;
+    DevBuf<unsigned char> arot_k;
+    DevBuf<int> aperm, an, alist;
+    DevBuf<unsigned long long> aoff, acnt;
+    unsigned long long arch_cap = 0;
+    bool arch = false, v_arch = false, arch_init = false;
     std::vector<int> adj_bps;              // resident adjoint CTAs per SM, by cluster slots
     DevBuf<double> partials, zbuf, gbuf, dosbuf, act_below;
     DevBuf<double2> act;
@@ -189,6 +201,7 @@ struct elses_system_s {
     std::vector<long long> graph_key;
     long long graph_launches = 0, graph_krylov = 0, graph_columns = 0;
     bool graph_v_lazy = false;            // v_lazy as the captured step leaves it
+    bool graph_v_arch = false;            // and v_arch
     void drop_graph() {
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         graph_exec = nullptr;
@@ -233,6 +246,7 @@ int join_side(elses_system s, cudaStream_t st);
 KrylovArgs krylov_args(elses_system s, int b, int e);
 EigArgs eig_args(elses_system s, int b, int e, double* V);
 int ensure_V(elses_system s, cudaStream_t st);
+int reset_archive(elses_system s, cudaStream_t st);
 int run_batch(elses_system s, int b, int e, bool stored, double** V_out, int* v_col0,
               double** UP_out, int* up_block0, cudaStream_t st, bool need_rows = true, bool form_v = true);
 int adjoint_impl(elses_system s, double mu, int lo, int hi, double* gH, double* gS, double s_scale,

@@ -130,15 +130,17 @@ def test_two_pass_equals_stored(eg, d64):
     assert np.array_equal(gu.to_np(rho), d64["rho"]) and np.array_equal(gu.to_np(F), d64["F"])
 
 
-def test_two_pass_equals_stored_in_batches(eg):
+@pytest.mark.parametrize("keep_factors", [1, 0], ids=["kept_factors", "v_per_batch"])
+def test_two_pass_equals_stored_in_batches(eg, keep_factors):
     """The same workflow invariance with the columns streamed in batches (the 4096-atom system in
-    four batches of 1024 atoms, the form the 10^6-atom system runs in). The stored workflow
-    forms V per batch and takes the spectra as Q^T z; the memory-saving one keeps only the
-    spectra in its first calculation of G (the rotation replay) and recomputes each batch for the
-    density. So they agree to rounding, not bit for bit: mu within the bound a rounding
-    difference of N allows (gu.mu_tolerance), energies and rho to 1e-12 relative."""
+    four batches of 1024 atoms, the form the 10^6-atom system runs in). The stored workflow keeps
+    every batch's eigen-factors for the density (keep_factors = 1; or, 0, forms V per batch and
+    takes the spectra as Q^T z); the memory-saving one keeps only the spectra in its first
+    calculation of G and recomputes each batch for the density. So they agree to rounding, not
+    bit for bit: mu within the bound a rounding difference of N allows (gu.mu_tolerance),
+    energies and rho to 1e-12 relative."""
     w = wl.make("diamond_4096")
-    a = eg.system_for(w, batch_atoms=1024)
+    a = eg.system_for(w, batch_atoms=1024, keep_factors=keep_factors)
     b = eg.system_for(w, batch_atoms=1024, two_pass=True)
     ra, rb = a.energy_force(), b.energy_force()
     assert abs(ra[0] - rb[0]) <= gu.mu_tolerance(a, ra[0])
@@ -152,10 +154,10 @@ def test_two_pass_equals_stored_in_batches(eg):
 
 def test_factor_density_equals_formed_V(eg, d64):
     """One batch of every atom leaves V unformed: the spectra come from the rotation replay and
-    t = V w from the eigen-factors (rotations, reflectors, L^-T). Several batches form V, with
-    the spectra as Q^T z. The same results to rounding; the two N(mu) differ by rounding, so mu
-    agrees within the bound that difference allows where N is nearly flat (gu.mu_tolerance),
-    and rho is compared at one mu."""
+    t = V w from the eigen-factors (rotations, reflectors, L^-T). Several batches that form V
+    per batch (keep_factors = 0) take the spectra as Q^T z. The same results to rounding; the
+    two N(mu) differ by rounding, so mu agrees within the bound that difference allows where N
+    is nearly flat (gu.mu_tolerance), and rho is compared at one mu."""
     s2 = eg.system_for(d64["w"], batch_atoms=16)
     mu, e_band, _, F = s2.energy_force()
     assert abs(mu - d64["mu"]) <= gu.mu_tolerance(s2, mu)
