@@ -376,7 +376,25 @@ __global__ void __launch_bounds__(kSpecThreads) k_eig_spectra(const EigArgs a) {
     const double* y = a.tri + (size_t)c * eig_tri_doubles(nm) + (2 + q) * (size_t)nm;
     for (int k = 0; k < nu; ++k) Y[k] = y[k];
     const RotList R(a, c);
-    for (int r = 0; r < R.n; ++r) {
+    int r = 0;   // the loads of four rotations issued before the four are applied
+    for (; r + 3 < R.n; r += 4) {
+        double cq[4], sq[4];
+        int kq[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            cq[q] = __ldg(R.c + r + q);
+            sq[q] = __ldg(R.s + r + q);
+            kq[q] = __ldg(R.k + r + q);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = kq[q];
+            const double p = Y[k], w = Y[k + 1];
+            Y[k] = fma(cq[q], p, sq[q] * w);
+            Y[k + 1] = fma(cq[q], w, -sq[q] * p);
+        }
+    }
+    for (; r < R.n; ++r) {
         const double cr = __ldg(R.c + r), sr = __ldg(R.s + r);
         const int k = __ldg(R.k + r);
         const double p = Y[k], w = Y[k + 1];
@@ -653,7 +671,26 @@ __global__ void __launch_bounds__(kWtThreads) k_eig_weights(const EigArgs a, dou
             const double f2 = 2.0 * fermi((e - mu) / kT) * a.c[(size_t)j * nm + k];
             X[perm[k]] = v ? f2 * e : f2;
         }
-        for (int r = fs.nrot - 1; r >= 0; --r) {
+        // in reverse; the loads of four rotations issued before the four are applied
+        int r = fs.nrot - 1;
+        for (; r >= 3; r -= 4) {
+            double cq[4], sq[4];
+            int kq[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                cq[q] = __ldg(fs.rc + r - q);
+                sq[q] = __ldg(fs.rs + r - q);
+                kq[q] = __ldg(fs.rk + r - q);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = kq[q];
+                const double p = X[k], w = X[k + 1];
+                X[k] = fma(cq[q], p, -sq[q] * w);
+                X[k + 1] = fma(cq[q], w, sq[q] * p);
+            }
+        }
+        for (; r >= 0; --r) {
             const double cr = __ldg(fs.rc + r), sr = __ldg(fs.rs + r);
             const int k = __ldg(fs.rk + r);
             const double p = X[k], w = X[k + 1];

@@ -138,3 +138,14 @@ def test_partial_passes_and_g_of_z(eg, ref):
     rho, _ = s.density_matrix(mu)
     assert np.abs(gu.to_np(rho) - ref["rho"]).max() <= 1e-13 * np.abs(ref["rho"]).max()
 
+
+
+def test_block_spaces_with_kept_factors(eg, ref):
+    """Block-start spaces give every column its own projected problem too: kept across six
+    batches, the results equal one batch's bit for bit."""
+    a = eg.system_for(ref["w"], krylov_block=True)
+    b = eg.system_for(ref["w"], krylov_block=True, batch_atoms=BATCH, keep_factors=1)
+    ra, rb = a.energy_force(), b.energy_force()
+    assert b.stats()["keep_factors"] == 1
+    assert ra[0] == rb[0] and ra[1] == rb[1] and ra[2] == rb[2]
+    assert np.array_equal(gu.to_np(ra[3]), gu.to_np(rb[3]))
