@@ -72,6 +72,9 @@ def parse():
                          "coefficients from the projected overlap S' (one sweep of the basis)")
     ap.add_argument("--no-exact", action="store_true",
                     help="skip the energy + exact-force step (gradient through the truncated Krylov build)")
+    ap.add_argument("--batch-atoms", type=int, default=0,
+                    help="atoms per Krylov -> eigensolver batch of the main system (0: automatic); "
+                         "several batches keep their eigen-factors for the density")
     return ap.parse_args()
 
 
@@ -261,10 +264,10 @@ class Runner:
     """One workload on the current device: Systems of it, and their timed energy + force steps
     (each step: rebuild at the resident positions, then elses_energy_force)."""
 
-    def __init__(self, eg, w, k3_ctas, stream, flush, reorth=0):
+    def __init__(self, eg, w, k3_ctas, stream, flush, reorth=0, batch_atoms=0):
         import torch
         self.eg, self.w, self.k3_ctas, self.stream, self.flush = eg, w, k3_ctas, stream, flush
-        self.reorth = reorth
+        self.reorth, self.batch_atoms = reorth, batch_atoms
         self.pos_dev = torch.tensor(w.pos, dtype=torch.float64, device="cuda")
         self.forces = torch.empty((w.n_atoms, 3), dtype=torch.float64, device="cuda")
 
@@ -274,7 +277,7 @@ class Runner:
                               nu_classes=w.nu_classes, schedule=schedule, timing=True,
                               k3_ctas_per_sm=self.k3_ctas, exact_forces=exact_forces,
                               autotune=autotune and self.k3_ctas == 0, graph=graph,
-                              reorth=self.reorth, keep_factors=1)
+                              reorth=self.reorth, batch_atoms=self.batch_atoms, keep_factors=1)
 
     def step(self, s):
         s.rebuild(self.pos_dev)
@@ -403,7 +406,7 @@ def run_ours(args):
     M = 4 * w.n_atoms
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    r = Runner(eg, w, args.k3_ctas, stream, flush, args.reorth)
+    r = Runner(eg, w, args.k3_ctas, stream, flush, args.reorth, args.batch_atoms)
 
     # the production form: launch shape tuned at build (before timing), the step replayed as a
     # CUDA graph (captured during the warm-up steps)
@@ -485,6 +488,7 @@ def run_ours(args):
         "plain": {"ms_per_step": plain_ms, "value": M / (plain_ms * 1e-3), "unit": "columns/s"},
         "exact_forces": exact,
         "autotuned_shapes": shapes(tuned),
+        "batches": batched_stats["batches"],
         "gram_schmidt": GRAM_SCHMIDT[args.reorth],
         "phases_ms_per_step": {k: stats[k] / args.steps for k in PHASES},
         "e2e": {"value": e2e_value, "unit": "columns/s", "ms_per_step": e2e_ms,
@@ -492,7 +496,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(f_host.numel() * 8 + 3 * 8)},
         "gpu_launches": int(stats["launches"]),
         "roofline": dict(roofline(stats, peak_probe,
-                                  krylov_traffic(args.reorth) if args.workload == WORKLOAD else None),
+                                  krylov_traffic(args.reorth)
+                                  if args.workload == WORKLOAD and batched_stats["batches"] == 1 else None),
                          ctas_per_sm=batched_stats["k3_ctas_per_sm"],
                          launches_per_step=stats["krylov_launches"] / args.steps),
         "clocks": clk.summary(),
@@ -528,11 +533,14 @@ def bench_workload(name, w):
 
 def bench_config(args, w, world):
     """The workload configuration both arms report."""
-    return {"workload": bench_workload(args.workload, w),
-            "columns_per_step": 4 * w.n_atoms,
-            "schedule": "batched (persistent, size-sorted queue, autotuned launch shape, CUDA graph)",
-            "l2": "256 MB buffer written between timed steps",
-            "parallelism": f"replicas x{world}"}
+    cfg = {"workload": bench_workload(args.workload, w),
+           "columns_per_step": 4 * w.n_atoms,
+           "schedule": "batched (persistent, size-sorted queue, autotuned launch shape, CUDA graph)",
+           "l2": "256 MB buffer written between timed steps",
+           "parallelism": f"replicas x{world}"}
+    if getattr(args, "batch_atoms", 0):
+        cfg["batch_atoms"] = args.batch_atoms
+    return cfg
 
 
 def run_reference(args):
