@@ -81,3 +81,33 @@ def test_binding_structs_match_the_header(struct, cls):
     assert [n for n, _ in got] == [n for n, _ in want]
     for (n, a), (_, b) in zip(got, want):
         assert ctypes.sizeof(a) == ctypes.sizeof(b) and getattr(a, "_type_", a) == getattr(b, "_type_", b), n
+
+
+BAD_PARAMS = [("nu", 0, "nu must be"), ("nu", 65, "nu must be"), ("n_classes", 5, "n_classes"),
+              ("kT", 0.0, "kT must be positive"), ("force_mode", 2, "force_mode"),
+              ("krylov_block", 2, "krylov_block"), ("batch_atoms", -1, "batch_atoms"),
+              ("k3_lanes", 16, "k3_lanes"), ("max_qr_sweeps", -1, "max_qr_sweeps"),
+              ("reorth", 2, "reorth"), ("keep_factors", -1, "keep_factors"),
+              ("r_cluster", 1.0, "r_cluster must be >= r_cut")]
+
+
+@pytest.mark.parametrize("field, value, message", BAD_PARAMS, ids=[f"{f}={v}" for f, v, _ in BAD_PARAMS])
+def test_build_rejects_bad_parameters_before_any_device_call(libpath, field, value, message):
+    """elses_build_clusters checks every parameter on the host before it touches the device or
+    the positions (here a host buffer stands in for the device pointer): ELSES_ERR_ARG and a
+    message naming the parameter, no system created."""
+    import paper_1210_1531_gb300 as eg
+    import workloads as wl
+    w = wl.make("diamond_64")
+    p = eg.make_params(6.0, w.nu, w.kT, w.n_electrons)
+    setattr(p, field, value)
+    L = eg.load_library(libpath)
+    L.elses_last_error.restype = ctypes.c_char_p
+    sk = eg.make_sk(w.sk)
+    box = (ctypes.c_double * 3)(20.0, 20.0, 20.0)
+    pos = (ctypes.c_double * (3 * w.n_atoms))()
+    h = ctypes.c_void_p(None)
+    rc = L.elses_build_clusters(ctypes.byref(h), w.n_atoms, ctypes.cast(pos, ctypes.c_void_p), box,
+                                ctypes.byref(sk), ctypes.byref(p), None)
+    assert rc == -1 and h.value is None
+    assert message in L.elses_last_error().decode()
