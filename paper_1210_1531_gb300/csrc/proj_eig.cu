@@ -280,8 +280,9 @@ __global__ void __launch_bounds__(kChaseThreads) k_eig_chase(const EigArgs a) {
     const int max_sweeps = a.max_sweeps > 0 ? a.max_sweeps : 30 * nu;
     // each pass deflates every negligible trailing off-diagonal entry, then makes one sweep:
     // the columns of a warp then reach their sweeps together (a column that deflated would
-    // otherwise sit out the other lanes' sweep), in the same order of operations per column
-    while (ok) {
+    // otherwise sit out the other lanes' sweep), in the same order of operations per column.
+    // A column without a space (nu = 0, flagged by the Krylov build) has nothing to chase.
+    while (ok && hi > 0) {
         while (hi > 0 && fabs(E[hi - 1]) <= eps * (fabs(D[hi - 1]) + fabs(D[hi]))) {
             E[hi - 1] = 0.0;
             --hi;

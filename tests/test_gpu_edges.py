@@ -108,6 +108,27 @@ def test_indefinite_overlap_is_not_spd(eg):
     assert s.green_columns() == 0
 
 
+def test_column_without_a_space_under_a_sweep_cap(eg):
+    """A non-positive diagonal overlap S_jj leaves column j without a Krylov space (nu_eff = 0,
+    ELSES_ERR_ARG); with a QR sweep cap set the eigensolver still has nothing to chase for it
+    (the cap no longer lets an empty column into the sweep loop), the call reports the error and
+    the valid overlap builds again."""
+    w = wl.make("diamond_64")
+    s = eg.system_for(w, max_qr_sweeps=200)             # enough for every nu = 30 column
+    H, S = s.hs()
+    rp, ci = (gu.to_np(t) for t in s.pattern())
+    e33 = int(np.flatnonzero((np.repeat(np.arange(w.n_atoms), np.diff(rp)) == 3) & (ci == 3))[0])
+    Sb = S.clone()
+    Sb[e33, 0, 0] = -1.0
+    s.set_hs(H, Sb)
+    with pytest.raises(eg.ElsesError) as err:
+        s.green_columns()
+    assert err.value.code in (-1, -2)
+    assert int(s.spectra()["nu_eff"][12]) == 0          # column 4 * 3 + 0: no space
+    s.set_hs(H, S)
+    assert s.green_columns() == 0
+
+
 def test_qr_sweep_cap_reports_timeout(eg):
     """The implicit-shift QR chase of the projected eigenproblem is a bounded loop: with its cap
     at one sweep per column (a 30 x 30 tridiagonal needs about two per eigenvalue) the columns
