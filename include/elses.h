@@ -226,8 +226,12 @@ int elses_autotune(elses_system sys, int run, int max_classes, int* classes_out,
  * for columns [col_begin, col_end) (whole atoms: both multiples of 4). Keeps the spectra (and,
  * unless two_pass, what rho needs). If n_z > 0, also writes G_ij(z) for the pattern rows i of
  * each column j into G_dev[(e*16 + a*4 + b)*n_z + iz][2] (re, im) for block e = (I, J) holding
- * G_(I,a),(J,b), z_host[iz] = (re, im). nu_eff_dev: optional int[M] device output.
- * Passage: Eq. 1 and the generation of G column by column. */
+ * G_(I,a),(J,b), z_host[iz] = (re, im). nu_eff_dev: optional int[M] device output. The columns
+ * are computed in the system's batches of atoms (params.batch_atoms): a range that starts
+ * inside a batch recomputes it from its first atom (the same columns again; G is written for
+ * the range only). With keep_factors and several batches, a range of every column (n_z = 0)
+ * starts the pool of kept rotations afresh, and until it returns its columns count as not
+ * computed. Passage: Eq. 1 and the generation of G column by column. */
 int elses_green_columns(elses_system sys, int col_begin, int col_end, int n_z,
                         const double* z_host, double* G_dev, int* nu_eff_dev, void* stream);
 
