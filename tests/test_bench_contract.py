@@ -36,3 +36,22 @@ def test_reference_line_has_the_contract_keys():
 def test_other_ranks_print_nothing():
     res = _run({"RANK": "1"})
     assert res.returncode == 0 and res.stdout.strip() == ""
+
+
+def test_both_arms_name_a_batch_size_set_on_the_command_line():
+    """--batch-atoms changes the workload's batches, so both arms' config says so (and leaves it
+    out when the library chooses them)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as wl
+    w = wl.make("diamond_64")
+    saved = sys.argv
+    try:
+        sys.argv = ["bench.py", "--workload", "diamond_64", "--batch-atoms", "16"]
+        args = bench.parse()
+        assert bench.bench_config(args, w, 1)["batch_atoms"] == 16
+        sys.argv = ["bench.py", "--workload", "diamond_64"]
+        args = bench.parse()
+        assert "batch_atoms" not in bench.bench_config(args, w, 1)
+    finally:
+        sys.argv = saved
