@@ -222,8 +222,8 @@ int prepare_columns(elses_system s) {
     // are kept (a pool of rotations of at most 60% of the free memory, or keep_factors per
     // column) so that V need not be formed per batch; too small a pool does not pay, and V is
     // formed per batch then
+    const bool arch_was = s->arch;
     s->arch = false;
-    s->arch_cap = 0;
     if (!s->p.two_pass && s->batch_atoms < s->n && s->p.keep_factors > 0) {
         const size_t fixed = M * (sizeof(double) * (eig_arch_fac_doubles(nm) + 2 * (size_t)nm) +
                                   sizeof(int) * ((size_t)nm + 1) + sizeof(unsigned long long)) + bc * sizeof(int);
@@ -231,6 +231,8 @@ int prepare_columns(elses_system s) {
         size_t cap = 0;
         if (s->p.keep_factors > 1) {
             cap = M * (size_t)s->p.keep_factors;
+        } else if (arch_was && s->arch_M == M && s->arch_nm == nm) {
+            cap = s->arch_cap;   // a rebuild of the same size keeps the pool it planned
         } else {
             // the archive a previous build planned counts as free (a rebuild keeps its plan)
             size_t free_b = 0, total_b = 0;
@@ -262,10 +264,13 @@ int prepare_columns(elses_system s) {
             }
             s->arch = true;
             s->arch_cap = cap;
+            s->arch_M = M;
+            s->arch_nm = nm;
         }
     }
     if (!s->arch) {
         s->arch_init = false;
+        s->arch_cap = 0;
         s->afac.release();
         s->aperm.release();
         s->an.release();

@@ -133,6 +133,8 @@ struct elses_system_s {
     DevBuf<int> aperm, an, alist;
     DevBuf<unsigned long long> aoff, acnt;
     unsigned long long arch_cap = 0;
+    size_t arch_M = 0;
+    int arch_nm = 0;
     bool arch = false, v_arch = false, arch_init = false;
     std::vector<int> adj_bps;              // resident adjoint CTAs per SM, by cluster slots
     DevBuf<double> partials, zbuf, gbuf, dosbuf, act_below;
