@@ -439,3 +439,20 @@ def test_single_atom_closed_forms():
     assert abs(res["mu"] - (SK.Ep - w.kT * np.log(2.0))) < 1e-12
     assert abs(res["E_band"] - (2 * SK.Es + 2 * SK.Ep)) < 1e-11
     assert np.abs(res["forces"]).max() == 0.0
+
+
+def test_dense_carbon_recipe():
+    """The 10^6-atom input recipe on a seeded sample of the same construction (8 x 8 x 4 cells):
+    3.0 g/cm^3 of carbon, no pair closer than 1.1 A after the redraws, 5 A clusters of 69-89
+    atoms; the full system is 64 x 64 x 32 cells of 8 atoms, 2^20 atoms."""
+    pos, box = wl.amorphous((8, 8, 4))
+    n = len(pos)
+    assert n == 2048
+    rho_gcc = n * 12.011 / 6.02214076e23 / (np.prod(box) * 1e-24)
+    assert abs(rho_gcc - 3.0) < 1e-2
+    tree = cKDTree(pos, boxsize=box)
+    d, _ = tree.query(pos, k=2)
+    assert d[:, 1].min() >= 1.1
+    sizes = np.array([len(x) for x in tree.query_ball_point(pos, 5.0)])
+    assert 75 < sizes.mean() < 85 and sizes.min() >= 60 and sizes.max() <= 100
+    assert 8 * 64 * 64 * 32 == 1 << 20
